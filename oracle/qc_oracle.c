@@ -1,0 +1,245 @@
+/*
+ * Plain CPU oracle for graph Quantum Clustering (arXiv 2305.14641).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg are the only callers.  The CUDA library never
+ * links, loads or calls this file, and this file shares no code with it.
+ *
+ * What it computes, for one undirected unweighted graph in CSR form:
+ *   1. hop distances from a source by a FIFO-queue BFS (Section 3.1: the
+ *      distance between nodes, read as the number of edges on a shortest
+ *      path; an unreachable pair has infinite distance);
+ *   2. the per-node distance histogram h_i(d) = #{j : dist(i, j) = d},
+ *      j running over every node including i itself (Algorithm 1 sums over
+ *      all n nodes);
+ *   3. the potential of Eq. 7 (last line) as Algorithm 1 computes it,
+ *      v(i) = (sum1 / sum2) / (2 sigma^2) with sum1 = sum_j d^2 exp(-d^2/2sigma^2)
+ *      and sum2 = sum_j exp(-d^2/2sigma^2); the terms are grouped by distance
+ *      (canonical form: ascending d, one exp per distance) and, separately,
+ *      summed pair by pair (literal form, one exp per pair);
+ *   4. Graph Gradient Descent (Algorithm 2 and the prose after Algorithm 4):
+ *      each node points at its lowest-potential neighbour (first one in
+ *      ascending index on ties) when that potential is strictly lower than
+ *      its own, else at itself;
+ *   5. cluster centers (Algorithm 3): the root each node's parent chain
+ *      reaches, found iteratively with path compression.
+ *
+ * Readings of the paper taken here (unreachable pairs contribute nothing,
+ * the self term has d = 0, strict descent, lowest-index tie-break, the
+ * root id as the label) are listed with their reasons in the design notes.
+ *
+ * Floating point: IEEE binary64 throughout; compile with -ffp-contract=off so
+ * that no multiply-add is fused.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- 1. hop distances (Section 3.1, hop reading) ------------------------- */
+
+/* dist[j] = hops from src to j, or -1 when j is unreachable.  queue: n ints of
+ * scratch.  Returns the largest finite distance (the eccentricity of src). */
+int32_t qco_bfs(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                int32_t src, int32_t *dist, int32_t *queue)
+{
+    for (int32_t j = 0; j < n; ++j) dist[j] = -1;
+    int32_t head = 0, tail = 0, ecc = 0;
+    dist[src] = 0;
+    queue[tail++] = src;
+    while (head < tail) {
+        int32_t u = queue[head++];
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            int32_t x = col_idx[e];
+            if (dist[x] < 0) {
+                dist[x] = dist[u] + 1;
+                if (dist[x] > ecc) ecc = dist[x];
+                queue[tail++] = x;
+            }
+        }
+    }
+    return ecc;
+}
+
+/* ---- 2. per-node distance histograms (Algorithm 1's sum over j) ---------- */
+
+typedef struct {
+    int32_t n;
+    const int32_t *row_ptr, *col_idx;
+    const int32_t *nodes;
+    int64_t first, last;       /* rows [first, last) of the node list */
+    int32_t cap;
+    int32_t *hist;             /* [n_nodes][cap] */
+    int32_t *ecc;              /* [n_nodes] */
+    int status;
+} qco_hist_job;
+
+static void *qco_hist_worker(void *arg)
+{
+    qco_hist_job *job = (qco_hist_job *)arg;
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)job->n);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)job->n);
+    if (!dist || !queue) {
+        job->status = -2;
+        free(dist);
+        free(queue);
+        return NULL;
+    }
+    for (int64_t k = job->first; k < job->last; ++k) {
+        int32_t *h = job->hist + k * (int64_t)job->cap;
+        memset(h, 0, sizeof(int32_t) * (size_t)job->cap);
+        int32_t e = qco_bfs(job->n, job->row_ptr, job->col_idx, job->nodes[k], dist, queue);
+        job->ecc[k] = e;
+        if (e >= job->cap) {
+            job->status = -1;
+            continue;
+        }
+        for (int32_t j = 0; j < job->n; ++j)
+            if (dist[j] >= 0) h[dist[j]] += 1;
+    }
+    free(dist);
+    free(queue);
+    return NULL;
+}
+
+/* hist[k][d] = #{j : dist(nodes[k], j) = d} for d < cap; ecc[k] = largest finite
+ * distance from nodes[k].  The node list is split into `threads` contiguous parts,
+ * one pthread each.  Returns 0, -1 if some distance is >= cap (that row is then
+ * incomplete; call again with a larger cap), -2 on allocation failure. */
+int qco_histograms(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                   int64_t n_nodes, const int32_t *nodes, int32_t cap,
+                   int32_t *hist, int32_t *ecc, int threads)
+{
+    if (threads < 1) threads = 1;
+    if (threads > n_nodes) threads = (int)(n_nodes > 0 ? n_nodes : 1);
+    qco_hist_job *jobs = (qco_hist_job *)calloc((size_t)threads, sizeof(qco_hist_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    if (!jobs || !tid) {
+        free(jobs);
+        free(tid);
+        return -2;
+    }
+    for (int t = 0; t < threads; ++t) {
+        jobs[t] = (qco_hist_job){n, row_ptr, col_idx, nodes,
+                                 n_nodes * t / threads, n_nodes * (t + 1) / threads,
+                                 cap, hist, ecc, 0};
+    }
+    for (int t = 1; t < threads; ++t) pthread_create(&tid[t], NULL, qco_hist_worker, &jobs[t]);
+    qco_hist_worker(&jobs[0]);
+    for (int t = 1; t < threads; ++t) pthread_join(tid[t], NULL);
+    int status = 0;
+    for (int t = 0; t < threads; ++t)
+        if (jobs[t].status < status) status = jobs[t].status;
+    free(jobs);
+    free(tid);
+    return status;
+}
+
+/* ---- 3. the potential (Eq. 7, Algorithm 1) -------------------------------- */
+
+/* Per-distance factors for one sigma: w[d] = exp(-d^2 / (2 sigma^2)) and
+ * u[d] = d^2 w[d], d = 0..len-1 (the two summands of Algorithm 1 for a node
+ * at distance d). */
+void qco_weights(double sigma, int32_t len, double *w, double *u)
+{
+    for (int32_t d = 0; d < len; ++d) {
+        double d2 = (double)((int64_t)d * d);
+        w[d] = exp(-d2 / (2.0 * (sigma * sigma)));
+        u[d] = d2 * w[d];
+    }
+}
+
+/* Canonical form: for each row k of hist ([rows][cap]),
+ *   sum1 = sum_{d=0..cap-1} h(d) u[d],  sum2 = sum_{d=0..cap-1} h(d) w[d]
+ * accumulated from 0.0 in ascending d, V[k] = (sum1 / sum2) / (2 sigma^2). */
+void qco_potential_hist(const int32_t *hist, int64_t rows, int32_t cap, double sigma,
+                        double *V)
+{
+    double *w = (double *)malloc(sizeof(double) * (size_t)cap);
+    double *u = (double *)malloc(sizeof(double) * (size_t)cap);
+    qco_weights(sigma, cap, w, u);
+    for (int64_t k = 0; k < rows; ++k) {
+        const int32_t *h = hist + k * (int64_t)cap;
+        double sum1 = 0.0, sum2 = 0.0;
+        for (int32_t d = 0; d < cap; ++d) {
+            sum1 = sum1 + (double)h[d] * u[d];
+            sum2 = sum2 + (double)h[d] * w[d];
+        }
+        V[k] = (sum1 / sum2) / (2.0 * (sigma * sigma));
+    }
+    free(w);
+    free(u);
+}
+
+/* Literal form: Algorithm 1 as written, one term per node j with dist = hop
+ * distance from i (dist[j] < 0: unreachable, no term). */
+double qco_potential_literal(const int32_t *dist, int32_t n, double sigma)
+{
+    double sum1 = 0.0, sum2 = 0.0;
+    for (int32_t j = 0; j < n; ++j) {
+        if (dist[j] < 0) continue;
+        double d = (double)dist[j];
+        double e = exp(-(d * d) / (2.0 * sigma * sigma));
+        sum1 = sum1 + d * d * e;
+        sum2 = sum2 + e;
+    }
+    return (1.0 / (2.0 * sigma * sigma)) * (sum1 / sum2);
+}
+
+/* ---- 4. Graph Gradient Descent (Algorithm 2, prose after Algorithm 4) ------ */
+
+/* parent[i] = the first neighbour (ascending index) holding the smallest V among
+ * i's neighbours, if that V is strictly below V[i]; otherwise i.  Returns the
+ * number of nodes whose minimal neighbours tie (two or more share the minimum and
+ * it is below V[i]): the only places where node numbering decides the result. */
+int64_t qco_ggd_parent(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                       const double *V, int32_t *parent)
+{
+    int64_t ties = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t best = -1;
+        int32_t count = 0;
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col_idx[e];
+            if (best < 0 || V[j] < V[best]) {
+                best = j;
+                count = 1;
+            } else if (V[j] == V[best]) {
+                count += 1;
+            }
+        }
+        if (best >= 0 && V[best] < V[i]) {
+            parent[i] = best;
+            if (count > 1) ties += 1;
+        } else {
+            parent[i] = i;
+        }
+    }
+    return ties;
+}
+
+/* ---- 5. cluster centers (Algorithm 3) --------------------------------------- */
+
+/* label[i] = root of i's parent chain.  Iterative find with path compression on a
+ * private copy of parent.  Returns the number of roots (clusters). */
+int32_t qco_find_centers(int32_t n, const int32_t *parent, int32_t *label)
+{
+    int32_t *p = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    memcpy(p, parent, sizeof(int32_t) * (size_t)n);
+    int32_t roots = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t r = i;
+        while (p[r] != r) r = p[r];
+        int32_t x = i;
+        while (p[x] != r) {
+            int32_t next = p[x];
+            p[x] = r;
+            x = next;
+        }
+        label[i] = r;
+        if (r == i) roots += 1;
+    }
+    free(p);
+    return roots;
+}
