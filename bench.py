@@ -1,0 +1,337 @@
+"""Benchmark: graph Quantum Clustering on the DC-SBM N=16384 workload with the
+16-value sigma sweep (one step = all-source BFS + histogram, potentials for 16
+sigma values, descent and roots for each).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is clusterings/s (one clustering = one label
+vector for one (graph, sigma) pair) over all ranks, timed on the device with
+CUDA events, inputs resident in HBM, L2 flushed (256 MiB write) before every
+timed step.  `e2e` is the same metric through the public API with host
+buffers: pinned host CSR -> device, solve, labels back to pinned host memory.
+`--impl reference` times the CPU oracle (test infrastructure, plain C) on the
+same workload instead.  With --gpus N > 1 each rank runs an independent replica
+(the single-graph workload is not sharded) and rank 0 reports the total.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+WORKLOAD = ("dcsbm-16384: degree-corrected SBM, N=16384, 32 equal communities, power-law expected "
+            "degrees (density exponent 2.5, mean 16, max 512), mixing 0.1, seed 1; sigma sweep of 16 "
+            "values log-spaced 0.5-4.0 reusing one histogram")
+METRIC = "clusterings/s"
+PROFILE = os.path.join(ROOT, "profiles", "bfs_level_dcsbm16384.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2305_14641_gb300", "csrc", "bfs.cu")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def gteps_edges(graph) -> float:
+    """sum over sources of the undirected edges in the source's component."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    n = graph.n
+    a = csr_matrix((np.ones(graph.nnz), graph.col_idx, graph.row_ptr), shape=(n, n))
+    _, comp = connected_components(a, directed=False)
+    size = np.bincount(comp)
+    rows = np.repeat(np.arange(n), graph.degrees())
+    edges = np.bincount(comp[rows], minlength=len(size)) / 2.0
+    return float((size * edges).sum())
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def profile_traffic():
+    """dram bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    if not os.path.exists(PROFILE):
+        return None
+    text = open(PROFILE).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
+    if not m or not h:
+        return None
+    if hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest() != h.group(1):
+        return None
+    return float(m.group(1))
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def run_cpu_oracle(graph, sigmas, threads):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.solve(graph, sigmas, threads=threads)
+    return time.perf_counter() - t0
+
+
+def bench_reference(args, graph, sigmas):
+    """The oracle, as it stands, on the host cores: each step one full solve of the workload."""
+    import oracle
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    threads = oracle.default_threads()
+    oracle.build()
+    for _ in range(args.warmup):
+        run_cpu_oracle(graph, sigmas, threads)
+    times = [run_cpu_oracle(graph, sigmas, threads) for _ in range(args.steps)]
+    total = sum(times)
+    value = len(sigmas) * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": graph.n, "nnz": graph.nnz, "sigmas": len(sigmas)},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
+                         "sample": "the full workload per step: queue BFS from all 16384 sources, "
+                                   "histograms, 16 potentials, descent and roots"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_ours(args, graph, sigmas):
+    import torch
+    import paper_2305_14641_gb300 as qc
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ctx = qc.Context(local)
+    S = len(sigmas)
+    n = graph.n
+
+    # device-resident inputs
+    g = qc.Graph.from_graph(ctx, graph)
+    V = torch.empty((S, n), dtype=torch.float64, device=dev)
+    labels = torch.empty((S, n), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        g.drop_histogram()
+        g.solve(sigmas, V_out=V, labels_out=labels, counts=False)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, each bracketed by events after an L2 flush
+    ctx.set_timing(True)
+    ctx.kernel_stats("bfs_level", reset=True)
+    launches0 = ctx.launch_count()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = ctx.launch_count() - launches0
+    kstats = ctx.kernel_stats("bfs_level", reset=True)
+    ctx.set_timing(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * S * args.steps / (total_ms / 1000.0)
+
+    # end to end through the public API with host buffers
+    rp_h = torch.from_numpy(graph.row_ptr).pin_memory()
+    ci_h = torch.from_numpy(graph.col_idx).pin_memory()
+    lab_h = torch.empty((S, n), dtype=torch.int32).pin_memory()
+    h2d = rp_h.numel() * 4 + ci_h.numel() * 4
+    d2h = lab_h.numel() * 4
+
+    def e2e_step():
+        gg_ = qc.Graph(ctx, rp_h.numpy(), ci_h.numpy(), validate=True)
+        _, lab_d, counts = gg_.solve(sigmas, labels_out=labels, counts=False)
+        lab_h.copy_(lab_d, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        gg_.close()
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_times = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_times.append(e0.elapsed_time(e1))
+    e2e_ms = float(sum(e_times))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * S * args.steps / (e2e_ms / 1000.0)
+
+    if rank == 0:
+        peak, peak_kind = measured_peak_gbs()
+        achieved = (kstats["model_bytes"] / (kstats["total_ms"] / 1000.0) / 1e9
+                    if kstats["total_ms"] > 0 else None)
+        traffic = profile_traffic()
+        edges = gteps_edges(graph)
+        bfs_ms = kstats["total_ms"] / args.steps
+        cpu = None
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            threads = oracle.default_threads()
+            t = run_cpu_oracle(graph, sigmas, threads)
+            cpu = {"value": S / t, "unit": METRIC, "cores": threads, "kind": "oracle",
+                   "sample": "one full solve of the workload (queue BFS from all 16384 sources, "
+                             "histograms, 16 potentials, descent, roots)",
+                   "seconds": t}
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64 bitsets / f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "nnz": graph.nnz, "sigmas": S,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "256 MiB buffer written between timed steps"},
+            "gteps": edges * world * args.steps / (total_ms / 1000.0) / 1e9,
+            "bfs_gteps": (edges / (bfs_ms / 1000.0) / 1e9) if bfs_ms > 0 else None,
+            "roofline": {"kernel": "bfs_pull_level", "bound": "hbm", "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": traffic,
+                         "model_bytes_per_launch": (kstats["model_bytes"] / kstats["launches"]
+                                                    if kstats["launches"] else None),
+                         "launches": kstats["launches"],
+                         "avg_launch_ms": (kstats["total_ms"] / kstats["launches"]
+                                           if kstats["launches"] else None)},
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    graph, sigmas = gg.config2()
+    if args.impl == "reference":
+        bench_reference(args, graph, sigmas)
+    else:
+        bench_ours(args, graph, sigmas)
+
+
+if __name__ == "__main__":
+    main()

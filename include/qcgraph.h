@@ -1,0 +1,241 @@
+/*
+ * qcgraph — graph Quantum Clustering on one GB300 (sm_103a).
+ *
+ * C ABI of libqcgraph.so.  Plain pointers and sizes only; every call returns a
+ * qc_status and no exception crosses the boundary.  Details of the last error
+ * of a context are in qc_last_error().
+ *
+ * The method (arXiv 2305.14641, Section 3.1, Algorithms 1-4):
+ *   dist(i, j)  hop distance between nodes i and j of an undirected,
+ *               unweighted graph (infinite when unreachable; such pairs add
+ *               nothing to the sums below);
+ *   V(i)        = (1 / (2 sigma^2)) * sum_j d^2 e^{-d^2/(2 sigma^2)}
+ *                                   / sum_j e^{-d^2/(2 sigma^2)},  d = dist(i, j),
+ *               j over all nodes including i (Eq. 7 last line, Algorithm 1);
+ *   parent(i)   the lowest-potential neighbour of i (smallest node id among
+ *               equal minima) when its V is strictly below V(i), else i
+ *               (Algorithm 2 with the prose that follows Algorithm 4);
+ *   label(i)    the root reached from i by following parents (Algorithm 3),
+ *               reported as that root's node id.
+ *
+ * Conventions for every call:
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls are asynchronous on it unless they write host memory, in
+ *     which case they synchronise that stream before returning.
+ *   - Arrays marked "device" must be device memory of the context's GPU and stay
+ *     valid until the work queued on `stream` has completed.  The caller owns
+ *     every array it passes; the library never frees them.
+ *   - Outputs go into caller-provided buffers.  The library allocates its own
+ *     scratch through the context's allocator (see qc_allocator).
+ *   - There is no CPU fallback: without a usable GPU every call that needs one
+ *     returns QC_ERR_CUDA.
+ */
+#ifndef QCGRAPH_H
+#define QCGRAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QC_OK = 0,
+    QC_ERR_INVALID_ARG = 1,    /* a null pointer, a size out of range, sigma <= 0 or NaN */
+    QC_ERR_INVALID_GRAPH = 2,  /* CSR fails validation (see QC_VALIDATE) */
+    QC_ERR_OOM = 3,            /* the allocator returned no memory */
+    QC_ERR_BUDGET = 4,         /* the request would exceed the context's memory budget */
+    QC_ERR_CUDA = 5,           /* a CUDA runtime error, or no usable GPU */
+    QC_ERR_TIMEOUT = 6,        /* a device-side wait gave up (bounded spin ran out) */
+    QC_ERR_CANCELLED = 7,      /* a served request was cancelled */
+    QC_ERR_NOT_READY = 8       /* a served request has not completed yet */
+} qc_status;
+
+typedef struct qc_ctx qc_ctx;
+typedef struct qc_graph qc_graph;
+typedef struct qc_batch qc_batch;
+typedef struct qc_server qc_server;
+
+/* Device-memory provider.  alloc returns `bytes` of device memory usable on
+ * `stream` (NULL on failure); free returns it.  Both may be called from any
+ * thread that calls into the library, and from the serving thread.  Passing
+ * NULL for the allocator selects cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} qc_allocator;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the scratch
+ * and resident-graph memory the library holds at once (0 = no cap); a call that
+ * would exceed it returns QC_ERR_BUDGET and allocates nothing.  `alloc` is
+ * copied; NULL selects the stream-ordered CUDA allocator.
+ * Errors: QC_ERR_INVALID_ARG (out == NULL, device < 0), QC_ERR_CUDA. */
+qc_status qc_context_create(int device, size_t mem_budget_bytes, const qc_allocator *alloc,
+                            qc_ctx **out);
+/* Destroy a context.  All graphs, batches and servers made from it must have
+ * been destroyed first. */
+void qc_context_destroy(qc_ctx *ctx);
+/* Bytes the context currently holds through its allocator. */
+size_t qc_context_bytes_in_use(const qc_ctx *ctx);
+/* Per-kernel timing, for measurement.  When enabled, the library brackets every
+ * launch of its dominant kernels with CUDA events on the launching stream and
+ * accumulates their durations and the modelled bytes each launch must move
+ * (documented per kernel in the design notes).  Off by default. */
+typedef struct {
+    uint64_t launches;
+    double total_ms;        /* sum of event-measured launch durations */
+    double model_bytes;     /* sum of modelled algorithmic bytes */
+} qc_kernel_stats;
+qc_status qc_context_set_timing(qc_ctx *ctx, int enable);
+/* kernel: "bfs_level" (the bitset BFS level step).  reset != 0 clears the
+ * counters after reading them. */
+qc_status qc_context_kernel_stats(qc_ctx *ctx, const char *kernel, qc_kernel_stats *out, int reset);
+/* Number of kernels the library has launched on this context so far. */
+uint64_t qc_context_launch_count(const qc_ctx *ctx);
+/* Static text for a status code. */
+const char *qc_status_string(qc_status s);
+/* Message of the most recent error on this context ("" if none).  Valid until
+ * the next call on the context. */
+const char *qc_last_error(const qc_ctx *ctx);
+
+/* ---- one graph ------------------------------------------------------------ */
+
+enum {
+    QC_PTR_DEVICE = 1u, /* row_ptr / col_idx are device pointers (else host) */
+    QC_VALIDATE = 2u    /* check the CSR: row_ptr[0] = 0, non-decreasing, row_ptr[n] =
+                           nnz; column ids in [0, n); rows strictly ascending (sorted,
+                           no duplicates); no self-loops; symmetric (undirected) */
+};
+
+/* Upload an undirected, unweighted graph in CSR form (the paper's adjacency
+ * matrix input of Algorithms 1 and 4, held sparse): node v's neighbours are
+ * col_idx[row_ptr[v] .. row_ptr[v+1]-1].  row_ptr: int32[n+1]; col_idx:
+ * int32[nnz], each undirected edge stored in both rows.  The library copies
+ * the arrays into device memory it owns; the copy stays resident until
+ * qc_graph_destroy.  Without QC_VALIDATE the CSR is trusted: an invalid one
+ * gives undefined results (out-of-range ids may fault the GPU).
+ * Errors: QC_ERR_INVALID_ARG (n < 1, nnz < 0, nnz >= 2^31, null pointers),
+ * QC_ERR_INVALID_GRAPH (validation failed), QC_ERR_BUDGET, QC_ERR_OOM,
+ * QC_ERR_CUDA. */
+qc_status qc_graph_create(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                          const int32_t *col_idx, uint32_t flags, void *stream,
+                          qc_graph **out);
+void qc_graph_destroy(qc_graph *g);
+/* Release the cached histogram (the next qc_potential / qc_graph_histogram runs
+ * the BFS again). */
+void qc_graph_drop_histogram(qc_graph *g);
+int32_t qc_graph_num_nodes(const qc_graph *g);
+int64_t qc_graph_num_edges(const qc_graph *g);
+
+/* Per-node hop-distance histogram (Algorithm 1 depends on node i only through
+ * the multiset {dist(i, j)}): hist[d][v] = #{j : dist(v, j) = d} for d = 0..D,
+ * D the largest finite distance in the graph.  Runs the all-source bitset BFS
+ * the first time (the result is cached in the graph and reused by later
+ * qc_potential calls for any sigma).
+ * hist_out: device int32[(D+1) * n] row-major (level-major) or NULL to query D
+ * only.  D_out: host, required.  Synchronises `stream` (D is a host output).
+ * Errors: QC_ERR_INVALID_ARG, QC_ERR_BUDGET, QC_ERR_OOM, QC_ERR_CUDA. */
+qc_status qc_graph_histogram(qc_graph *g, int32_t *hist_out, int32_t *D_out, void *stream);
+
+/* Potential V for every node and every sigma (Eq. 7 last line, Algorithm 1),
+ * in binary64, summed over distances in ascending order from the histogram.
+ * sigmas: host double[n_sigma], each finite and > 0.  V_out: device
+ * double[n_sigma * n], V_out[s * n + v].
+ * Errors: QC_ERR_INVALID_ARG (n_sigma < 1, bad sigma, null), QC_ERR_BUDGET,
+ * QC_ERR_OOM, QC_ERR_CUDA. */
+qc_status qc_potential(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
+                       void *stream);
+
+/* Graph Gradient Descent and cluster centers (Algorithms 2 and 3) for n_sigma
+ * potential vectors.  V: device double[n_sigma * n] (as written by
+ * qc_potential).  labels_out: device int32[n_sigma * n], the root node id each
+ * node descends to.  n_clusters_out: host int32[n_sigma] (number of roots) or
+ * NULL; when given, the call synchronises `stream`.
+ * Errors: QC_ERR_INVALID_ARG, QC_ERR_BUDGET, QC_ERR_OOM, QC_ERR_CUDA. */
+qc_status qc_ggd_labels(qc_graph *g, const double *V, int32_t n_sigma, int32_t *labels_out,
+                        int32_t *n_clusters_out, void *stream);
+
+/* Algorithm 4 in one call: qc_potential then qc_ggd_labels.  V_out may be NULL
+ * (the potentials then live in library scratch).  Same arguments and errors as
+ * those two calls. */
+qc_status qc_solve(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
+                   int32_t *labels_out, int32_t *n_clusters_out, void *stream);
+
+/* ---- many graphs ------------------------------------------------------------ */
+
+/* A batch plan: Algorithm 4 for n_graphs graphs, graph k clustered with
+ * sigma_per_graph[k] (host), its labels written to labels_out + label_offsets[k]
+ * (labels_out: device int32, label_offsets: host int64[n_graphs]; the caller
+ * sizes labels_out so that every graph's n labels fit).  The plan packs the
+ * graphs' descriptors once, picks tile shapes with the context's autotuner,
+ * and captures the whole solve (one persistent kernel over all graphs, then
+ * descent and roots) into a CUDA graph.  The graphs must outlive the plan.
+ * n_clusters_out of qc_batch_run: host int32[n_graphs] or NULL (when given,
+ * the call synchronises `stream`).
+ * Errors: QC_ERR_INVALID_ARG, QC_ERR_BUDGET, QC_ERR_OOM, QC_ERR_CUDA,
+ * QC_ERR_TIMEOUT (a device-side wait gave up). */
+qc_status qc_batch_create(qc_ctx *ctx, int32_t n_graphs, qc_graph *const *graphs,
+                          const double *sigma_per_graph, int32_t *labels_out,
+                          const int64_t *label_offsets, void *stream, qc_batch **out);
+qc_status qc_batch_run(qc_batch *b, int32_t *n_clusters_out, void *stream);
+void qc_batch_destroy(qc_batch *b);
+
+/* One-shot form: create a plan, run it once, destroy it. */
+qc_status qc_solve_batch(qc_ctx *ctx, int32_t n_graphs, qc_graph *const *graphs,
+                         const double *sigma_per_graph, int32_t *labels_out,
+                         const int64_t *label_offsets, void *stream);
+
+/* ---- serving ------------------------------------------------------------------ */
+
+typedef struct {
+    size_t mem_budget_bytes;   /* admission budget for resident requests (0 = the context's) */
+    int32_t max_active;        /* most requests on the GPU at once (0 = 256) */
+} qc_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, failed;
+    uint64_t steps;            /* scheduler iterations that launched GPU work */
+    size_t bytes_resident;     /* admitted requests' bytes right now */
+    size_t peak_bytes_resident;
+    int32_t active, queued;
+} qc_server_stats;
+
+/* A serving loop on its own host thread and CUDA stream: submitted requests
+ * wait in FIFO order until their memory estimate fits the budget and a slot is
+ * free, then join the requests already on the GPU (continuous batching: every
+ * scheduler step advances all active requests by one BFS level in one launch;
+ * requests that finish their BFS get their potential, descent and roots, and
+ * leave).  cfg may be NULL for defaults. */
+qc_status qc_server_create(qc_ctx *ctx, const qc_server_config *cfg, qc_server **out);
+/* Queue one request: a host CSR (copied before the call returns; same layout
+ * and validation as qc_graph_create with QC_VALIDATE) and its sigma.
+ * req_id: host, receives the request id.
+ * Errors: QC_ERR_INVALID_ARG, QC_ERR_INVALID_GRAPH, QC_ERR_BUDGET (the request
+ * alone exceeds the budget). */
+qc_status qc_server_submit(qc_server *s, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                           const int32_t *col_idx, double sigma, uint64_t *req_id);
+/* Non-blocking: *done = 1 and labels_out (host int32[n]) / *n_clusters filled
+ * when the request has completed, else *done = 0.  A completed request's result
+ * is released after it has been read.  Returns the request's own error status
+ * if it failed, QC_ERR_INVALID_ARG for an unknown id. */
+qc_status qc_server_poll(qc_server *s, uint64_t req_id, int32_t *labels_out,
+                         int32_t *n_clusters, int *done);
+/* Blocking form of poll: waits up to timeout_ms (< 0: no limit); returns
+ * QC_ERR_NOT_READY if the time ran out. */
+qc_status qc_server_wait(qc_server *s, uint64_t req_id, int64_t timeout_ms,
+                         int32_t *labels_out, int32_t *n_clusters);
+/* Cancel a queued or active request (its memory is released at the next step). */
+qc_status qc_server_cancel(qc_server *s, uint64_t req_id);
+qc_status qc_server_get_stats(qc_server *s, qc_server_stats *out);
+/* Stop the loop (cancelling what is left) and free everything it holds. */
+void qc_server_destroy(qc_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCGRAPH_H */

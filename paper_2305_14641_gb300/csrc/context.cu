@@ -1,0 +1,271 @@
+// Context, memory accounting, error reporting, graph upload.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+
+#include "qc_internal.h"
+
+void qc_set_error(qc_ctx *ctx, const char *fmt, ...) {
+    if (!ctx) return;
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::lock_guard<std::mutex> lk(ctx->err_mu);
+    ctx->last_error = buf;
+}
+
+qc_status qc_mem_alloc(qc_ctx *ctx, size_t bytes, cudaStream_t stream, void **out) {
+    *out = nullptr;
+    if (bytes == 0) return QC_OK;
+    size_t before = ctx->in_use.fetch_add(bytes);
+    if (ctx->budget && before + bytes > ctx->budget) {
+        ctx->in_use.fetch_sub(bytes);
+        qc_set_error(ctx, "memory budget exceeded: %zu bytes in use + %zu requested > budget %zu",
+                     before, bytes, ctx->budget);
+        return QC_ERR_BUDGET;
+    }
+    void *p = nullptr;
+    if (ctx->custom_alloc) {
+        p = ctx->alloc.alloc(bytes, stream, ctx->alloc.user);
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    if (!p) {
+        ctx->in_use.fetch_sub(bytes);
+        qc_set_error(ctx, "device allocation of %zu bytes failed", bytes);
+        return QC_ERR_OOM;
+    }
+    *out = p;
+    return QC_OK;
+}
+
+void qc_mem_free(qc_ctx *ctx, void *ptr, size_t bytes, cudaStream_t stream) {
+    if (!ptr) return;
+    if (ctx->custom_alloc) ctx->alloc.free(ptr, bytes, stream, ctx->alloc.user);
+    else cudaFreeAsync(ptr, stream);
+    ctx->in_use.fetch_sub(bytes);
+}
+
+void qc_record_kernel(qc_ctx *ctx, const char *kernel, double ms, double model_bytes) {
+    std::lock_guard<std::mutex> lk(ctx->stats_mu);
+    qc_kernel_stats &st = ctx->stats[kernel];
+    st.launches += 1;
+    st.total_ms += ms;
+    st.model_bytes += model_bytes;
+}
+
+extern "C" {
+
+qc_status qc_context_set_timing(qc_ctx *ctx, int enable) {
+    if (!ctx) return QC_ERR_INVALID_ARG;
+    ctx->timing = enable != 0;
+    return QC_OK;
+}
+
+qc_status qc_context_kernel_stats(qc_ctx *ctx, const char *kernel, qc_kernel_stats *out, int reset) {
+    if (!ctx || !kernel || !out) return QC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->stats_mu);
+    auto it = ctx->stats.find(kernel);
+    *out = it == ctx->stats.end() ? qc_kernel_stats{0, 0.0, 0.0} : it->second;
+    if (reset && it != ctx->stats.end()) ctx->stats.erase(it);
+    return QC_OK;
+}
+
+uint64_t qc_context_launch_count(const qc_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
+
+const char *qc_status_string(qc_status s) {
+    switch (s) {
+    case QC_OK: return "ok";
+    case QC_ERR_INVALID_ARG: return "invalid argument";
+    case QC_ERR_INVALID_GRAPH: return "invalid graph";
+    case QC_ERR_OOM: return "out of device memory";
+    case QC_ERR_BUDGET: return "memory budget exceeded";
+    case QC_ERR_CUDA: return "CUDA error";
+    case QC_ERR_TIMEOUT: return "device wait timed out";
+    case QC_ERR_CANCELLED: return "cancelled";
+    case QC_ERR_NOT_READY: return "not ready";
+    }
+    return "unknown status";
+}
+
+const char *qc_last_error(const qc_ctx *ctx) {
+    if (!ctx) return "";
+    std::lock_guard<std::mutex> lk(ctx->err_mu);
+    return ctx->last_error.c_str();
+}
+
+qc_status qc_context_create(int device, size_t mem_budget_bytes, const qc_allocator *alloc,
+                            qc_ctx **out) {
+    if (!out || device < 0) return QC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (alloc && (!alloc->alloc || !alloc->free)) return QC_ERR_INVALID_ARG;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device >= count) {
+        cudaGetLastError();
+        return QC_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return QC_ERR_CUDA;
+    qc_ctx *ctx = new qc_ctx();
+    ctx->device = device;
+    ctx->budget = mem_budget_bytes;
+    if (alloc) {
+        ctx->alloc = *alloc;
+        ctx->custom_alloc = true;
+    }
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    ctx->num_sms = v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, device);
+    ctx->l2_bytes = (size_t)v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    ctx->smem_optin = (size_t)v;
+    *out = ctx;
+    return QC_OK;
+}
+
+void qc_context_destroy(qc_ctx *ctx) { delete ctx; }
+
+size_t qc_context_bytes_in_use(const qc_ctx *ctx) { return ctx ? ctx->in_use.load() : 0; }
+
+qc_status qc_graph_create(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                          const int32_t *col_idx, uint32_t flags, void *stream_, qc_graph **out) {
+    if (!ctx || !out) return QC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 1 || nnz < 0 || nnz >= (int64_t(1) << 31) || !row_ptr || (nnz > 0 && !col_idx)) {
+        qc_set_error(ctx, "qc_graph_create: n=%d nnz=%lld out of range or null CSR", n,
+                     (long long)nnz);
+        return QC_ERR_INVALID_ARG;
+    }
+    cudaStream_t stream = qc_stream(stream_);
+    QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const bool on_device = flags & QC_PTR_DEVICE;
+    if (!on_device && (flags & QC_VALIDATE)) {
+        // row_ptr is checked on the host first: the device checks index through it
+        if (row_ptr[0] != 0 || row_ptr[n] != nnz) {
+            qc_set_error(ctx, "invalid CSR: row_ptr[0]=%d row_ptr[n]=%d nnz=%lld", row_ptr[0],
+                         row_ptr[n], (long long)nnz);
+            return QC_ERR_INVALID_GRAPH;
+        }
+        for (int32_t v = 0; v < n; ++v)
+            if (row_ptr[v + 1] < row_ptr[v]) {
+                qc_set_error(ctx, "invalid CSR: row_ptr decreases at row %d", v);
+                return QC_ERR_INVALID_GRAPH;
+            }
+    }
+    qc_graph *g = new qc_graph();
+    g->ctx = ctx;
+    g->n = n;
+    g->nnz = nnz;
+    qc_status st = g->row_ptr.allocate(ctx, sizeof(int32_t) * (size_t)(n + 1), stream);
+    if (st == QC_OK) st = g->col_idx.allocate(ctx, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1), stream);
+    if (st != QC_OK) {
+        delete g;
+        return st;
+    }
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(g->row_ptr.ptr, row_ptr, sizeof(int32_t) * (size_t)(n + 1), kind, stream);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpyAsync(g->col_idx.ptr, col_idx, sizeof(int32_t) * (size_t)nnz, kind, stream);
+    if (e != cudaSuccess) {
+        qc_set_error(ctx, "qc_graph_create: copy failed: %s", cudaGetErrorString(e));
+        delete g;
+        return QC_ERR_CUDA;
+    }
+    if (flags & QC_VALIDATE) {
+        st = qc_validate_csr(ctx, n, nnz, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(), stream);
+        if (st != QC_OK) {
+            delete g;
+            return st;
+        }
+    }
+    *out = g;
+    return QC_OK;
+}
+
+void qc_graph_destroy(qc_graph *g) { delete g; }
+
+void qc_graph_drop_histogram(qc_graph *g) {
+    if (!g) return;
+    g->hist.release();
+    g->hist_rows = 0;
+    g->hist_valid = false;
+    g->D = 0;
+}
+
+int32_t qc_graph_num_nodes(const qc_graph *g) { return g ? g->n : 0; }
+int64_t qc_graph_num_edges(const qc_graph *g) { return g ? g->nnz : 0; }
+
+qc_status qc_graph_histogram(qc_graph *g, int32_t *hist_out, int32_t *D_out, void *stream_) {
+    if (!g || !D_out) return QC_ERR_INVALID_ARG;
+    cudaStream_t stream = qc_stream(stream_);
+    QC_CUDA_TRY(g->ctx, cudaSetDevice(g->ctx->device));
+    if (!g->hist_valid) QC_TRY(qc_bfs_histogram(g, stream));
+    *D_out = g->D;
+    if (hist_out)
+        QC_CUDA_TRY(g->ctx, cudaMemcpyAsync(hist_out, g->hist.ptr,
+                                            sizeof(int32_t) * (size_t)(g->D + 1) * (size_t)g->n,
+                                            cudaMemcpyDeviceToDevice, stream));
+    QC_CUDA_TRY(g->ctx, cudaStreamSynchronize(stream));
+    return QC_OK;
+}
+
+qc_status qc_potential(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
+                       void *stream_) {
+    if (!g || !sigmas || n_sigma < 1 || !V_out) {
+        if (g) qc_set_error(g->ctx, "qc_potential: null pointer or n_sigma < 1");
+        return QC_ERR_INVALID_ARG;
+    }
+    for (int32_t s = 0; s < n_sigma; ++s)
+        if (!qc_sigma_ok(sigmas[s])) {
+            qc_set_error(g->ctx, "qc_potential: sigma[%d] = %g is not finite and > 0", s, sigmas[s]);
+            return QC_ERR_INVALID_ARG;
+        }
+    cudaStream_t stream = qc_stream(stream_);
+    QC_CUDA_TRY(g->ctx, cudaSetDevice(g->ctx->device));
+    if (!g->hist_valid) QC_TRY(qc_bfs_histogram(g, stream));
+    return qc_potential_from_hist(g, sigmas, n_sigma, V_out, stream);
+}
+
+qc_status qc_ggd_labels(qc_graph *g, const double *V, int32_t n_sigma, int32_t *labels_out,
+                        int32_t *n_clusters_out, void *stream_) {
+    if (!g || !V || n_sigma < 1 || !labels_out) {
+        if (g) qc_set_error(g->ctx, "qc_ggd_labels: null pointer or n_sigma < 1");
+        return QC_ERR_INVALID_ARG;
+    }
+    cudaStream_t stream = qc_stream(stream_);
+    qc_ctx *ctx = g->ctx;
+    QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    qc_buffer roots;
+    QC_TRY(roots.allocate(ctx, sizeof(int32_t) * (size_t)n_sigma, stream));
+    QC_CUDA_TRY(ctx, cudaMemsetAsync(roots.ptr, 0, roots.bytes, stream));
+    QC_TRY(qc_descend(ctx, g->n, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(), V, n_sigma,
+                      labels_out, roots.as<int32_t>(), stream));
+    if (n_clusters_out) {
+        QC_CUDA_TRY(ctx, cudaMemcpyAsync(n_clusters_out, roots.ptr, roots.bytes,
+                                         cudaMemcpyDeviceToHost, stream));
+        QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    }
+    return QC_OK;
+}
+
+qc_status qc_solve(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
+                   int32_t *labels_out, int32_t *n_clusters_out, void *stream_) {
+    if (!g || !sigmas || n_sigma < 1 || !labels_out) return QC_ERR_INVALID_ARG;
+    cudaStream_t stream = qc_stream(stream_);
+    qc_buffer Vtmp;
+    double *V = V_out;
+    if (!V) {
+        QC_TRY(Vtmp.allocate(g->ctx, sizeof(double) * (size_t)n_sigma * (size_t)g->n, stream));
+        V = Vtmp.as<double>();
+    }
+    QC_TRY(qc_potential(g, sigmas, n_sigma, V, stream_));
+    return qc_ggd_labels(g, V, n_sigma, labels_out, n_clusters_out, stream_);
+}
+
+}  // extern "C"

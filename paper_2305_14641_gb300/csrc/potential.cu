@@ -1,0 +1,70 @@
+// The potential of Eq. 7 (last line) / Algorithm 1, evaluated from the distance
+// histogram:
+//     sum1 = sum_d h_v(d) * d^2 e^{-d^2/(2 sigma^2)},  sum2 = sum_d h_v(d) * e^{-d^2/(2 sigma^2)}
+//     V_v  = (sum1 / sum2) / (2 sigma^2)
+// Binary64 throughout.  The factors e^{-d^2/(2 sigma^2)} and d^2 e^{...} are
+// computed once per (sigma, d) on the host with the C library's exp, so the
+// device never evaluates an exponential; the device adds the terms in
+// ascending d starting from 0.0 with explicitly rounded multiplies and adds
+// (no fused multiply-add) and divides with IEEE round-to-nearest.
+#include <cmath>
+#include <vector>
+
+#include "qc_internal.h"
+
+bool qc_sigma_ok(double sigma) { return std::isfinite(sigma) && sigma > 0.0; }
+
+void qc_weight_table(double sigma, int32_t len, double *w, double *u) {
+    for (int32_t d = 0; d < len; ++d) {
+        const double d2 = (double)((int64_t)d * d);
+        w[d] = std::exp(-d2 / (2.0 * (sigma * sigma)));
+        u[d] = d2 * w[d];
+    }
+}
+
+namespace {
+
+// One thread per (sigma, node); hist is level-major so a warp reads 32
+// consecutive counts per level.  tables: w[s][d], u[s][d] for d = 0..D, den[s] = 2 sigma^2.
+__global__ void potential_kernel(int32_t n, int32_t D, const int32_t *__restrict__ hist,
+                                 const double *__restrict__ w, const double *__restrict__ u,
+                                 const double *__restrict__ den, double *__restrict__ V) {
+    const int s = blockIdx.y;
+    const double *ws = w + (size_t)s * (D + 1);
+    const double *us = u + (size_t)s * (D + 1);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        double sum1 = 0.0, sum2 = 0.0;
+        for (int d = 0; d <= D; ++d) {
+            const double h = (double)hist[(size_t)d * n + v];
+            sum1 = __dadd_rn(sum1, __dmul_rn(h, us[d]));
+            sum2 = __dadd_rn(sum2, __dmul_rn(h, ws[d]));
+        }
+        V[(size_t)s * n + v] = __ddiv_rn(__ddiv_rn(sum1, sum2), den[s]);
+    }
+}
+
+}  // namespace
+
+qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V,
+                                 cudaStream_t stream) {
+    qc_ctx *ctx = g->ctx;
+    const int32_t L = g->D + 1;
+    std::vector<double> tab((size_t)n_sigma * (2 * L + 1));
+    double *w = tab.data(), *u = w + (size_t)n_sigma * L, *den = u + (size_t)n_sigma * L;
+    for (int32_t s = 0; s < n_sigma; ++s) {
+        qc_weight_table(sigmas[s], L, w + (size_t)s * L, u + (size_t)s * L);
+        den[s] = 2.0 * (sigmas[s] * sigmas[s]);
+    }
+    qc_buffer dtab;
+    QC_TRY(dtab.allocate(ctx, sizeof(double) * tab.size(), stream));
+    QC_CUDA_TRY(ctx, cudaMemcpyAsync(dtab.ptr, tab.data(), dtab.bytes, cudaMemcpyHostToDevice, stream));
+    // the host table must outlive the asynchronous copy
+    QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    const double *dw = dtab.as<double>();
+    dim3 grid(qc_ceil_div(g->n, 256) < 2 * ctx->num_sms ? qc_ceil_div(g->n, 256) : 2 * ctx->num_sms,
+              n_sigma);
+    potential_kernel<<<grid, 256, 0, stream>>>(g->n, g->D, g->hist.as<int32_t>(), dw,
+                                               dw + (size_t)n_sigma * L, dw + 2 * (size_t)n_sigma * L, V);
+    QC_LAUNCHED(ctx);
+    return QC_OK;
+}

@@ -1,0 +1,151 @@
+// Internal declarations shared by the translation units of libqcgraph.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/qcgraph.h"
+
+// ---- context -------------------------------------------------------------------
+
+struct qc_tune_key {
+    int kind;        // which kernel family
+    int n_bucket;    // log2 bucket of the node count
+    int deg_bucket;  // log2 bucket of the mean degree
+    bool operator<(const qc_tune_key &o) const {
+        if (kind != o.kind) return kind < o.kind;
+        if (n_bucket != o.n_bucket) return n_bucket < o.n_bucket;
+        return deg_bucket < o.deg_bucket;
+    }
+};
+
+struct qc_ctx {
+    int device = 0;
+    size_t budget = 0;                    // 0 = no cap
+    std::atomic<size_t> in_use{0};
+    qc_allocator alloc{};
+    bool custom_alloc = false;
+    int num_sms = 0;
+    size_t l2_bytes = 0;
+    size_t smem_optin = 0;
+    mutable std::mutex err_mu;
+    std::string last_error;
+    std::mutex tune_mu;
+    std::map<qc_tune_key, int> tune;      // autotuned choice per (kind, size bucket)
+    std::atomic<uint64_t> launches{0};    // kernels launched on this context
+    std::atomic<bool> timing{false};
+    std::mutex stats_mu;
+    std::map<std::string, qc_kernel_stats> stats;
+};
+
+// Count one launch (and surface launch-configuration errors).
+#define QC_LAUNCHED(ctx)                                                                \
+    do {                                                                                \
+        (ctx)->launches.fetch_add(1, std::memory_order_relaxed);                        \
+        QC_CUDA_TRY((ctx), cudaGetLastError());                                         \
+    } while (0)
+
+void qc_record_kernel(qc_ctx *ctx, const char *kernel, double ms, double model_bytes);
+
+void qc_set_error(qc_ctx *ctx, const char *fmt, ...);
+
+// Scratch and resident memory go through these so that the budget is honoured.
+qc_status qc_mem_alloc(qc_ctx *ctx, size_t bytes, cudaStream_t stream, void **out);
+void qc_mem_free(qc_ctx *ctx, void *ptr, size_t bytes, cudaStream_t stream);
+
+// A scratch buffer released when it goes out of scope (stream-ordered).
+struct qc_buffer {
+    qc_ctx *ctx = nullptr;
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    qc_buffer() = default;
+    qc_buffer(const qc_buffer &) = delete;
+    qc_buffer &operator=(const qc_buffer &) = delete;
+    qc_buffer(qc_buffer &&o) noexcept { *this = std::move(o); }
+    qc_buffer &operator=(qc_buffer &&o) noexcept {
+        release();
+        ctx = o.ctx; ptr = o.ptr; bytes = o.bytes; stream = o.stream;
+        o.ptr = nullptr; o.bytes = 0;
+        return *this;
+    }
+    ~qc_buffer() { release(); }
+    qc_status allocate(qc_ctx *c, size_t b, cudaStream_t s) {
+        release();
+        ctx = c; stream = s; bytes = b;
+        if (b == 0) return QC_OK;
+        qc_status st = qc_mem_alloc(c, b, s, &ptr);
+        if (st != QC_OK) { ptr = nullptr; bytes = 0; }
+        return st;
+    }
+    void release() {
+        if (ptr) qc_mem_free(ctx, ptr, bytes, stream);
+        ptr = nullptr; bytes = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+#define QC_CUDA_TRY(ctx, expr)                                                          \
+    do {                                                                                \
+        cudaError_t qc_e_ = (expr);                                                     \
+        if (qc_e_ != cudaSuccess) {                                                     \
+            qc_set_error((ctx), "%s:%d: %s: %s", __FILE__, __LINE__, #expr,             \
+                         cudaGetErrorString(qc_e_));                                    \
+            return QC_ERR_CUDA;                                                         \
+        }                                                                               \
+    } while (0)
+
+#define QC_TRY(expr)                                                                    \
+    do {                                                                                \
+        qc_status qc_s_ = (expr);                                                       \
+        if (qc_s_ != QC_OK) return qc_s_;                                               \
+    } while (0)
+
+// ---- graph --------------------------------------------------------------------
+
+struct qc_graph {
+    qc_ctx *ctx = nullptr;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    qc_buffer row_ptr;       // int32[n+1]
+    qc_buffer col_idx;       // int32[nnz]
+    // cached all-source BFS result
+    bool hist_valid = false;
+    int32_t D = 0;           // largest finite hop distance
+    int32_t hist_rows = 0;   // allocated rows of hist
+    qc_buffer hist;          // int32[hist_rows][n], level-major
+};
+
+// ---- entry points implemented per translation unit ---------------------------------
+
+// bfs.cu: all-source bitset BFS + histogram into g->hist (sets D, hist_valid).
+qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream);
+
+// potential.cu: V[s][v] from the cached histogram.
+qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V,
+                                 cudaStream_t stream);
+// Host weight tables for one sigma, d = 0..len-1 (identical expression to the
+// definition: w = exp(-d^2 / (2 sigma^2)), u = d^2 w).
+void qc_weight_table(double sigma, int32_t len, double *w, double *u);
+// Check sigma: finite and > 0.
+bool qc_sigma_ok(double sigma);
+
+// ggd.cu: parents and roots.
+qc_status qc_descend(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                     const double *V, int32_t n_sigma, int32_t *labels, int32_t *n_roots_dev,
+                     cudaStream_t stream);
+
+// validate.cu
+qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
+                          const int32_t *col_idx_dev, cudaStream_t stream);
+
+static inline cudaStream_t qc_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+static inline int qc_ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

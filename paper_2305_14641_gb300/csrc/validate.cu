@@ -1,0 +1,84 @@
+// CSR validation on the device (QC_VALIDATE): the graph must be the sparse form
+// of a symmetric 0/1 adjacency matrix with an empty diagonal, rows sorted.
+#include "qc_internal.h"
+
+namespace {
+
+enum : int32_t {
+    BAD_ROW_PTR = 1,
+    BAD_COLUMN = 2,
+    BAD_ORDER = 4,      // unsorted row or duplicate edge
+    BAD_SELF_LOOP = 8,
+    BAD_ASYMMETRIC = 16,
+};
+
+__global__ void check_row_ptr(int32_t n, int64_t nnz, const int32_t *row_ptr, int32_t *err) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (row_ptr[v + 1] < row_ptr[v]) atomicOr(err, BAD_ROW_PTR);
+        if (v == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz)) atomicOr(err, BAD_ROW_PTR);
+    }
+}
+
+// One warp per row.  Safe to run only after check_row_ptr passed.
+__global__ void check_rows(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    int bad = 0;
+    for (int v = warp; v < n; v += nwarps) {
+        const int beg = row_ptr[v], end = row_ptr[v + 1];
+        for (int e = beg + lane; e < end; e += 32) {
+            const int u = col_idx[e];
+            if (u < 0 || u >= n) { bad |= BAD_COLUMN; continue; }
+            if (u == v) bad |= BAD_SELF_LOOP;
+            if (e > beg && col_idx[e - 1] >= u) bad |= BAD_ORDER;
+            // symmetric: v must appear in row u (binary search; rows may be unsorted
+            // only if BAD_ORDER is also reported)
+            int lo = row_ptr[u], hi = row_ptr[u + 1] - 1;
+            bool found = false;
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const int x = col_idx[mid];
+                if (x == v) { found = true; break; }
+                if (x < v) lo = mid + 1; else hi = mid - 1;
+            }
+            if (!found) bad |= BAD_ASYMMETRIC;
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (lane == 0 && bad) atomicOr(err, bad);
+}
+
+}  // namespace
+
+qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                          const int32_t *col_idx, cudaStream_t stream) {
+    qc_buffer err;
+    QC_TRY(err.allocate(ctx, sizeof(int32_t), stream));
+    QC_CUDA_TRY(ctx, cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), stream));
+    int32_t h_err = 0;
+    const int blocks = qc_ceil_div(n, 256) < 4 * ctx->num_sms ? qc_ceil_div(n, 256) : 4 * ctx->num_sms;
+    check_row_ptr<<<blocks, 256, 0, stream>>>(n, nnz, row_ptr, err.as<int32_t>());
+    QC_LAUNCHED(ctx);
+    QC_CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    if (h_err) {
+        qc_set_error(ctx, "invalid CSR: row_ptr is not 0-based, non-decreasing and ending at nnz");
+        return QC_ERR_INVALID_GRAPH;
+    }
+    if (nnz == 0) return QC_OK;
+    const int wblocks = qc_ceil_div(n, 8) < 8 * ctx->num_sms ? qc_ceil_div(n, 8) : 8 * ctx->num_sms;
+    check_rows<<<wblocks, 256, 0, stream>>>(n, row_ptr, col_idx, err.as<int32_t>());
+    QC_LAUNCHED(ctx);
+    QC_CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    if (h_err) {
+        qc_set_error(ctx, "invalid CSR (flags 0x%x):%s%s%s%s", h_err,
+                     (h_err & BAD_COLUMN) ? " column id out of range;" : "",
+                     (h_err & BAD_ORDER) ? " row not strictly ascending;" : "",
+                     (h_err & BAD_SELF_LOOP) ? " self-loop;" : "",
+                     (h_err & BAD_ASYMMETRIC) ? " not symmetric;" : "");
+        return QC_ERR_INVALID_GRAPH;
+    }
+    return QC_OK;
+}

@@ -1,0 +1,168 @@
+"""CUDA path against the oracle, element by element (needs a GPU).
+
+Histograms and labels must be bit-exact.  Potentials must agree within 1e-12
+relative (the stated tolerance); the design makes them bit-identical, and that
+is asserted too.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def qc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_14641_gb300 as qc
+    return qc
+
+
+@pytest.fixture(scope="module")
+def ctx(qc):
+    c = qc.Context(0)
+    yield c
+    c.close()
+
+
+def assert_solution_matches(qc, ctx, graph, sigmas, threads=None):
+    threads = threads or oracle.default_threads()
+    ref = oracle.solve(graph, sigmas, threads=threads)
+    g = qc.Graph.from_graph(ctx, graph)
+    hist = g.histogram().cpu().numpy()
+    assert hist.shape == (ref.D + 1, graph.n), (graph.name, hist.shape, ref.hist.shape)
+    assert np.array_equal(hist.T, ref.hist), graph.name
+    V = g.potential(sigmas)
+    labels, counts = g.ggd_labels(V)
+    Vh = V.cpu().numpy()
+    rel = np.abs(Vh - ref.V) / np.maximum(np.abs(ref.V), np.finfo(np.float64).tiny)
+    assert np.all(rel <= 1e-12), (graph.name, float(rel.max()))
+    assert np.array_equal(Vh, ref.V), (graph.name, "potential not bit-identical")
+    assert np.array_equal(labels.cpu().numpy(), ref.labels), graph.name
+    assert counts == ref.n_clusters, graph.name
+    g.close()
+    return ref
+
+
+def test_config1(qc, ctx):
+    graph, sigmas = gg.config1()
+    assert_solution_matches(qc, ctx, graph, sigmas + [0.5, 0.8, 2.0, 4.0])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 63, 64, 65, 127, 128, 129, 255, 500, 1000, 2047, 3001])
+def test_random_sizes(qc, ctx, n):
+    """Ragged tails of the 64-source words and of the 16-byte row segments,
+    disconnected graphs and isolated nodes."""
+    g = gg.rng(21, n)
+    for p in (2.0 / max(n, 2), 8.0 / max(n, 2), 0.3):
+        graph = gg.erdos_renyi(n, min(p, 1.0), g) if n <= 3001 else None
+        assert_solution_matches(qc, ctx, graph, [0.6, 1.7])
+
+
+def test_structured(qc, ctx):
+    for graph in [gg.complete(40), gg.path(300), gg.star(70, 5), gg.two_cliques_bridge(9),
+                  gg.path(2), gg.complete(1)]:
+        assert_solution_matches(qc, ctx, graph, [0.5, 1.0, 3.0])
+
+
+def test_no_edges(qc, ctx):
+    graph = gg.Graph(100, np.zeros(101, dtype=np.int32), np.zeros(0, dtype=np.int32), name="empty")
+    ref = assert_solution_matches(qc, ctx, graph, [1.0])
+    assert ref.n_clusters == [100]
+
+
+@pytest.mark.parametrize("chunk", [1, 2, 3, 5])
+def test_forced_source_chunks(qc, ctx, chunk, monkeypatch):
+    """Sources processed a few words at a time: the histogram accumulates across chunks."""
+    monkeypatch.setenv("QCGRAPH_CHUNK_WORDS", str(chunk))
+    graph = gg.planted_partition(700, 5, 0.05, 0.004, gg.rng(22, chunk))
+    assert_solution_matches(qc, ctx, graph, [0.9, 2.2])
+
+
+def test_planted_and_dcsbm_mid(qc, ctx):
+    g1 = gg.planted_partition(4000, 16, 0.02, 0.0005, gg.rng(23))
+    g2 = gg.dcsbm(3000, 8, 2.5, 10.0, 200.0, 0.1, gg.rng(24))
+    for graph in (g1, g2):
+        assert_solution_matches(qc, ctx, graph, gg.config2_sigmas()[::3])
+
+
+def test_config2_full(qc, ctx):
+    """DC-SBM N=16384 with the 16-value sigma sweep, every node checked."""
+    graph, sigmas = gg.config2()
+    assert_solution_matches(qc, ctx, graph, sigmas)
+
+
+def test_sigma_reuse_and_edge_values(qc, ctx):
+    """The cached histogram serves later sigma values; extreme sigmas stay exact."""
+    graph = gg.planted_partition(600, 6, 0.06, 0.003, gg.rng(25))
+    g = qc.Graph.from_graph(ctx, graph)
+    ref = oracle.solve(graph, [0.05, 1.0, 1e3])
+    for k, s in enumerate([0.05, 1.0, 1e3]):
+        V = g.potential([s])
+        assert np.array_equal(V.cpu().numpy()[0], ref.V[k])
+        labels, counts = g.ggd_labels(V)
+        assert np.array_equal(labels.cpu().numpy()[0], ref.labels[k])
+    g.close()
+
+
+def test_invalid_inputs(qc, ctx):
+    graph = gg.path(5)
+    g = qc.Graph.from_graph(ctx, graph)
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(qc.QCError) as e:
+            g.potential([1.0, bad])
+        assert e.value.status_name == "QC_ERR_INVALID_ARG"
+    g.close()
+    rp, ci = graph.row_ptr.copy(), graph.col_idx.copy()
+    cases = {}
+    a = ci.copy(); a[0] = 7; cases["out of range"] = (rp, a)
+    a = ci.copy(); a[1] = 1; cases["self-loop"] = (rp, a)
+    cases["asymmetric"] = (np.array([0, 1, 1], dtype=np.int32), np.array([1], dtype=np.int32))
+    cases["unsorted"] = (np.array([0, 2, 3, 4], dtype=np.int32), np.array([2, 1, 0, 0], dtype=np.int32))
+    cases["duplicate"] = (np.array([0, 2, 4], dtype=np.int32), np.array([1, 1, 0, 0], dtype=np.int32))
+    for name, (r, c) in cases.items():
+        with pytest.raises(qc.QCError) as e:
+            qc.Graph(ctx, r, c)
+        assert e.value.status_name == "QC_ERR_INVALID_GRAPH", name
+    bad_rp = rp.copy(); bad_rp[2] = bad_rp[3] + 1
+    with pytest.raises(qc.QCError) as e:
+        qc.Graph(ctx, bad_rp, ci)
+    assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
+    dev_bad = torch.tensor(bad_rp, device="cuda"), torch.tensor(ci, device="cuda")
+    with pytest.raises(qc.QCError) as e:
+        qc.Graph(ctx, *dev_bad)
+    assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
+
+
+def test_device_input_and_allocators(qc):
+    graph = gg.planted_partition(900, 3, 0.03, 0.003, gg.rng(26))
+    ref = oracle.solve(graph, [1.2])
+    for alloc in ("torch", "cuda"):
+        with qc.Context(0, allocator=alloc) as c:
+            rp = torch.tensor(graph.row_ptr, device="cuda")
+            ci = torch.tensor(graph.col_idx, device="cuda")
+            g = qc.Graph(c, rp, ci)
+            _, labels, counts = g.solve([1.2])
+            assert np.array_equal(labels.cpu().numpy(), ref.labels)
+            g.close()
+            torch.cuda.synchronize()
+            assert c.bytes_in_use() == 0
+
+
+def test_budget(qc):
+    graph = gg.planted_partition(2000, 4, 0.02, 0.001, gg.rng(27))
+    with qc.Context(0, mem_budget_bytes=200_000) as c:
+        g = qc.Graph.from_graph(c, graph)        # CSR alone fits
+        with pytest.raises(qc.QCError) as e:
+            g.potential([1.0])                  # the bitsets do not
+        assert e.value.status_name == "QC_ERR_BUDGET"
+        g.close()
+        torch.cuda.synchronize()
+        assert c.bytes_in_use() == 0
