@@ -234,6 +234,31 @@ qc_status qc_server_get_stats(qc_server *s, qc_server_stats *out);
 /* Stop the loop (cancelling what is left) and free everything it holds. */
 void qc_server_destroy(qc_server *s);
 
+/* ---- histogram without device allocation ---------------------------------------- */
+
+/* The paper has no counterpart to this call; it exists for callers that may not
+ * allocate device memory at all (a host application that fixes its GPU memory
+ * plan at start-up and forbids later cudaMalloc calls, a plugin that may only
+ * use buffers its host hands it, a loop that cannot afford an allocation).
+ *
+ * Same result as qc_graph_histogram, computed with no context and no
+ * allocation: the working bitsets live in a 16 MiB array that is part of the
+ * library (every GPU that loads the library holds it until the process exits).
+ * row_ptr / col_idx: device int32 CSR of an undirected graph, as
+ * qc_graph_create with QC_VALIDATE accepts it (not checked here).  hist_out:
+ * device int32[max_levels * n], level-major; every row is written (rows past D
+ * are zero).  D_out: host, receives D (-1 on failure).  Synchronises `stream`.
+ *
+ * Set-up: the first call on a device (with that device current) looks up the
+ * array's device address; make that first call outside any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (other streams
+ * or threads) race and give wrong results.
+ * Errors: QC_ERR_INVALID_ARG (n < 1 or n > 262144, max_levels < 2 or fewer
+ * rows than D + 1 needs, null pointers), QC_ERR_CUDA. */
+qc_status qc_histogram_static_scratch(int32_t n, int64_t nnz, const int32_t *row_ptr,
+                                      const int32_t *col_idx, int32_t *hist_out,
+                                      int32_t max_levels, int32_t *D_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
