@@ -152,7 +152,7 @@ qc_status qc_potential(qc_graph *g, const double *sigmas, int32_t n_sigma, doubl
 
 /* Graph Gradient Descent and cluster centers (Algorithms 2 and 3) for n_sigma
  * potential vectors.  V: device double[n_sigma * n] (as written by
- * qc_potential).  labels_out: device int32[n_sigma * n], the root node id each
+ * qc_potential), free of NaN (a NaN gives unspecified parents).  labels_out: device int32[n_sigma * n], the root node id each
  * node descends to.  n_clusters_out: host int32[n_sigma] (number of roots) or
  * NULL; when given, the call synchronises `stream`.
  * Errors: QC_ERR_INVALID_ARG, QC_ERR_BUDGET, QC_ERR_OOM, QC_ERR_CUDA. */

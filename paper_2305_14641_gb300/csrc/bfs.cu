@@ -7,24 +7,48 @@
 // node v, how many sources reach v at level d gives v's own histogram h_v(d)
 // without any cross-node reduction.
 //
-// Layout: sources are packed 64 to a uint64 word; the BFS handles a chunk of
-// `wn` consecutive words (64*wn sources) at a time.  vis[v] is a row of
-// `stride` words (stride even, so a row is whole 16-byte segments) holding the
-// sources already known to be within the current level of v.  Two rows per node
-// (vis_in, vis_out) ping-pong between levels.
+// Layout: sources are packed 64 to a uint64 word; a chunk of `wn` consecutive
+// words is processed at a time.  Node v owns a row of R 16-byte segments
+// (2R >= wn words, node-major) in each of two buffers: the row holds the
+// sources known to be within the current level of v.  Level l lives in
+// buf[l & 1].
 //
-// Level step (pull): a source s first reaches v at level l+1 exactly when s is
-// within level l of some neighbour u and not within level l of v:
-//     next[v] = (OR_{u in N(v)} vis_l[u]) & ~vis_l[v],   vis_{l+1}[v] = vis_l[v] | next[v]
-//     hist[l+1][v] += popcount(next[v])
-// Bits of sources >= n (the tail of the last word) and the padding word of an
-// odd-length row start set, so they never count and a row that has met every
-// source reads as all ones ("saturated").  A saturated row never changes again:
-// sat[v] records the level at which v's row saturated and later levels skip v
-// without touching its row.
+// Level 1 (set-up): v's row is {v} + N(v) restricted to the chunk, written
+// straight from the CSR.
+// Levels l >= 2 (pull): a source s first reaches v at level l exactly when s is
+// within level l-1 of a neighbour u and not within level l-1 of v:
+//     next[v] = (OR_{u in N(v)} vis_{l-1}[u]) & ~vis_{l-1}[v],   vis_l[v] = vis_{l-1}[v] | next[v]
+//     hist[l][v] += popcount(next[v])
+// Bits that can never become new start set: sources >= n, the padding word of
+// an odd-length row, and sources in another connected component than v (they
+// never reach v).  So a row is "all ones" exactly when every source that can
+// reach v has, and a saturated row never changes again: sat records the level
+// at which each (node, tile) saturated and later levels skip it.
+//
+// Work: items are (node, tile of 32 segments) taken in the graph's order
+// (heaviest degree bucket first; sat is indexed in that order).  Items of rows
+// with degree >= 63 are heavy: all warps of a block share one, splitting its
+// neighbour list.  Other items go one warp each, GRAB list positions per counter
+// update: the first pull level lists every light item, and each level appends
+// the items it pulled (still open, or saturated just now and owed one copy of
+// ones) to the next level's worklist, so late levels touch only what is left.
+// A warp reads its positions' sat words with one load per lane and runs the
+// items a ballot marks.  Rows of 32 segments or more are split into tiles
+// (lane = segment, G = 32); shorter rows are one tile of G = pow2 >= R lanes and
+// the warp reads 32/G neighbours at once.  Neighbour ids are read 32 at a time
+// with one coalesced load and broadcast by shuffle; each lane keeps min(4, G)
+// loads in flight and stops once its segment has found every missing source.
+//
+// One persistent cooperative launch runs the set-up and every level of a
+// chunk, separated by a grid barrier whose spin is bounded (on expiry the kernel
+// records a timeout and returns).  If the histogram runs out of rows the kernel
+// stops at a level boundary and the host grows it and relaunches from that
+// level.
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
+#include "qc_device.cuh"
 #include "qc_internal.h"
 
 namespace {
@@ -32,178 +56,350 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint64_t ONES = ~0ull;
 constexpr int NOT_SAT = 0x7fffffff;
+constexpr int WARPS = 8;               // warps per block
+constexpr int GRAB = 4;                // light list positions taken per counter update
+using qcdev::ST_DONE;
+using qcdev::ST_NEED_ROWS;
+using qcdev::ST_TIMEOUT;
+using qcdev::grid_barrier;
 
-struct LevelArgs {
+struct BfsParams {
     int32_t n;
     const int32_t *row_ptr;
     const int32_t *col_idx;
-    const ulonglong2 *vis_in;   // [n][R]
-    ulonglong2 *vis_out;        // [n][R]
-    int32_t R;                  // 16-byte segments per row (= stride / 2)
-    int32_t *sat;               // [n] level at which the row saturated, NOT_SAT if not yet
-    int32_t level;              // the level being produced (>= 2)
-    int32_t *hist_row;          // hist[level][*]
-    int32_t *level_new;         // set to 1 when any node gained a source at this level
+    const int32_t *order;       // nodes, heaviest degree bucket first; order[n] = heavy count
+    const int32_t *comp;        // component (smallest node id) of each node
+    const int32_t *wcomp;       // component shared by a whole source word, or -1
+    ulonglong2 *buf[2];         // vis_l in buf[l & 1], [n][R]
+    int32_t R;                  // 16-byte segments per row in this chunk
+    int32_t T;                  // tiles per row
+    int32_t w0, wn, W;          // chunk = words [w0, w0 + wn) of W
+    uint64_t last_mask;         // bits of sources >= n in word W - 1
+    int32_t *sat;               // [n * T], indexed by order position * T + tile
+    int32_t *hist;              // [rows][n]
+    int32_t rows;
+    int32_t first_chunk;        // write hist rows 0 and 1
+    int32_t start_level;        // 2: fresh chunk, run the level-1 set-up first
+    int32_t *level_new;         // [rows]
+    int32_t *light_ctr;         // [rows] light list positions taken so far at each level
+    int32_t *heavy_ctr;         // [rows] block items taken so far at each level
+    int32_t *wl[2];             // worklists of light items: level l reads wl[l & 1]
+    int32_t *wl_count;          // [rows] length of each level's worklist
+    int32_t *status;            // [0] state, [1] level reached
+    unsigned *bar;              // [0] arrivals, [1] generation
+    unsigned long long *stamp;  // [rows] globaltimer when each level's barrier opened (timing only)
 };
 
-__device__ __forceinline__ bool seg_full(ulonglong2 a) { return (a.x & a.y) == ONES; }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
-// One warp per node (grid-stride).  Lanes are split into 32/G neighbour slots of
-// G lanes; lane (slot, q) reads segment q + k*G (k < SPL) of every neighbour the
-// slot takes.  G = 32 for rows of 32 segments or more (one neighbour at a time,
-// each lane SPL segments); smaller rows read 32/G neighbours at once.
-template <int G, int SPL>
-__global__ void __launch_bounds__(256, (SPL >= 8 ? 1 : (SPL >= 4 ? 2 : 4))) bfs_pull_level(const LevelArgs a) {
-    constexpr int SLOTS = 32 / G;
+__device__ __forceinline__ bool seg_full(const ulonglong2 a) { return (a.x & a.y) == ONES; }
+
+// Bits of one chunk word that start set for node v (other components, sources >= n).
+__device__ __forceinline__ uint64_t preset_word(const BfsParams &p, int gw, int cv) {
+    uint64_t m;
+    const int wc = p.wcomp[gw];
+    if (wc >= 0) {
+        m = (wc == cv) ? 0ull : ONES;
+    } else {
+        m = 0ull;
+        const int s0 = 64 * gw;
+        const int cnt = min(64, p.n - s0);
+        for (int b = 0; b < cnt; ++b)
+            if (p.comp[s0 + b] != cv) m |= 1ull << b;
+    }
+    if (gw == p.W - 1) m |= p.last_mask;
+    return m;
+}
+
+// ---- level 1 -----------------------------------------------------------------------
+
+// Two passes.  Fill: every row segment gets its preset bits, in node-major
+// order so the stores stream; sat starts "not saturated" (level 2 finds the rows
+// that are already complete); hist rows 0 and 1 are written for the first chunk.
+// Bits: one warp per node sets the bits of v and of its neighbours with
+// fire-and-forget atomic ORs (only v's own row is touched, so they never
+// contend across warps).
+__device__ void init_fill(const BfsParams &p) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    ulonglong2 *out = p.buf[1];
+    const long long segs = (long long)p.n * p.R;
+    for (long long s = tid; s < segs; s += nthreads) {
+        const int v = (int)(s / p.R);
+        const int q = (int)(s - (long long)v * p.R);
+        const int cv = p.comp[v];
+        uint64_t w[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * q + h;
+            w[h] = (k < p.wn) ? preset_word(p, p.w0 + k, cv) : ONES;
+        }
+        out[s] = make_ulonglong2(w[0], w[1]);
+    }
+    for (int i = tid; i < p.n * p.T; i += nthreads) p.sat[i] = NOT_SAT;
+    if (p.first_chunk)
+        for (int v = tid; v < p.n; v += nthreads) {
+            p.hist[v] = 1;
+            p.hist[(size_t)p.n + v] = p.row_ptr[v + 1] - p.row_ptr[v];
+        }
+}
+
+__device__ void init_bits(const BfsParams &p) {
     const int lane = threadIdx.x & 31;
-    const int slot = lane / G;
-    const int q0 = lane % G;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    bool any_new = false;
-    for (int v = warp; v < a.n; v += nwarps) {
-        const int sv = a.sat[v];
-        if (sv <= a.level - 2) continue;                 // saturated in both buffers
-        ulonglong2 *out_row = a.vis_out + (size_t)v * a.R;
-        if (sv == a.level - 1) {                          // saturated last level: copy ones
-            if (slot == 0) {
+    unsigned long long *words = reinterpret_cast<unsigned long long *>(p.buf[1]);
+    const int stride = 2 * p.R;
+    for (int v = warp; v < p.n; v += nwarps) {
+        unsigned long long *row = words + (size_t)v * stride;
+        const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
+        for (int e = beg + lane; e <= end; e += 32) {
+            const int u = (e == end) ? v : p.col_idx[e];
+            const int k = (u >> 6) - p.w0;
+            if (k >= 0 && k < p.wn) atomicOr(row + k, 1ull << (u & 63));
+        }
+    }
+}
+
+// ---- levels >= 2: pull ------------------------------------------------------------
+
+// OR of the rows of neighbours [j_first, end) of one node, taking 32-neighbour
+// chunks j_first, j_first + stride, ... (stride = 32 x the warps sharing the row).
+// Lane (slot, q) accumulates segment q; it stops once acc | own is all ones.
+template <int G>
+__device__ __forceinline__ ulonglong2 gather_or(const BfsParams &p, const ulonglong2 *vin, int j_first,
+                                                int end, int stride, int q, bool qok, ulonglong2 own) {
+    constexpr int SLOTS = 32 / G;
+    constexpr int U = G < 4 ? G : 4;
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / G;
+    const ulonglong2 zero = make_ulonglong2(0ull, 0ull);
+    ulonglong2 acc = zero;
+    bool act = !seg_full(own);
+    for (int j0 = j_first; j0 < end; j0 += stride) {
+        if (!__any_sync(FULL, act)) break;
+        const int cnt = min(32, end - j0);
+        const int myu = (lane < cnt) ? p.col_idx[j0 + lane] : 0;
+        for (int m = 0; m < cnt; m += SLOTS * U) {
+            ulonglong2 x[U];
 #pragma unroll
-                for (int k = 0; k < SPL; ++k) {
-                    const int q = q0 + k * G;
-                    if (q < a.R) out_row[q] = make_ulonglong2(ONES, ONES);
-                }
+            for (int k = 0; k < U; ++k) {
+                const int tt = m + k * SLOTS + slot;
+                const int u = __shfl_sync(FULL, myu, tt & 31);
+                x[k] = (act && qok && tt < cnt) ? vin[(size_t)u * p.R + q] : zero;
             }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                acc.x |= x[k].x;
+                acc.y |= x[k].y;
+            }
+            act = act && !seg_full(make_ulonglong2(acc.x | own.x, acc.y | own.y));
+            if (!__any_sync(FULL, act)) break;
+        }
+    }
+    return acc;
+}
+
+// Finish one item: combine the slots, write the row segment, count, mark saturation.
+template <int G>
+__device__ __forceinline__ void finish_item(const BfsParams &p, ulonglong2 acc, const ulonglong2 own,
+                                            ulonglong2 *orow, int q, bool qok, int v, int sidx,
+                                            int32_t *hrow, int level, bool &any_new) {
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / G;
+#pragma unroll
+    for (int off = G; off < 32; off <<= 1) {
+        acc.x |= __shfl_xor_sync(FULL, acc.x, off);
+        acc.y |= __shfl_xor_sync(FULL, acc.y, off);
+    }
+    int count = 0;
+    bool full = true;
+    if (slot == 0 && qok) {
+        const ulonglong2 nw = make_ulonglong2(acc.x & ~own.x, acc.y & ~own.y);
+        const ulonglong2 o = make_ulonglong2(own.x | nw.x, own.y | nw.y);
+        orow[q] = o;
+        count = __popcll(nw.x) + __popcll(nw.y);
+        full = seg_full(o);
+    }
+    count = __reduce_add_sync(FULL, count);
+    full = __all_sync(FULL, full);
+    if (lane == 0) {
+        if (count) {
+            if (p.T > 1) atomicAdd(hrow + v, count);
+            else hrow[v] += count;
+            any_new = true;
+        }
+        if (full) p.sat[sidx] = level;
+    }
+}
+
+// Heavy rows (the first order[n] nodes, rows of 32 segments or more): one block
+// per (node, tile) item; warp w takes neighbour chunks w, w + 8, ...; the
+// partial ORs meet in shared memory and warp 0 finishes.
+__device__ void heavy_items(const BfsParams &p, const int level, bool &any_new, ulonglong2 (*red)[32]) {
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const ulonglong2 *vin = p.buf[(level - 1) & 1];
+    ulonglong2 *vout = p.buf[level & 1];
+    int32_t *hrow = p.hist + (size_t)level * p.n;
+    const int items = p.order[p.n] * p.T;
+    __shared__ int grab;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) grab = atomicAdd(p.heavy_ctr + level, 1);
+        __syncthreads();
+        const int it = grab;
+        if (it >= items) break;
+        const int sv = p.sat[it];
+        if (sv <= level - 2) continue;
+        const int oi = it / p.T;
+        const int t = it - oi * p.T;
+        const int v = p.order[oi];
+        const int q = t * 32 + lane;
+        const bool qok = q < p.R;
+        ulonglong2 *orow = vout + (size_t)v * p.R;
+        if (sv == level - 1) {
+            if (wib == 0 && qok) orow[q] = make_ulonglong2(ONES, ONES);
             continue;
         }
-        const ulonglong2 *in_row = a.vis_in + (size_t)v * a.R;
-        ulonglong2 own[SPL], acc[SPL];
-        bool act[SPL];
-#pragma unroll
-        for (int k = 0; k < SPL; ++k) {
-            const int q = q0 + k * G;
-            own[k] = (q < a.R) ? in_row[q] : make_ulonglong2(ONES, ONES);
-            acc[k] = make_ulonglong2(0, 0);
-            act[k] = !seg_full(own[k]);
-        }
-        const int beg = a.row_ptr[v], end = a.row_ptr[v + 1];
-        for (int j0 = beg; j0 < end; j0 += 32) {
-            const int cnt = min(32, end - j0);
-            const int myu = (lane < cnt) ? a.col_idx[j0 + lane] : 0;
-            const int rounds = (cnt + SLOTS - 1) / SLOTS;
-            for (int m = 0; m < rounds; ++m) {
-                const int t = m * SLOTS + slot;
-                const int u = __shfl_sync(FULL, myu, t < 32 ? t : 31);
-                if (t < cnt) {
-                    const ulonglong2 *nrow = a.vis_in + (size_t)u * a.R;
-#pragma unroll
-                    for (int k = 0; k < SPL; ++k) {
-                        const int q = q0 + k * G;
-                        if (act[k] && q < a.R) {
-                            const ulonglong2 x = nrow[q];
-                            acc[k].x |= x.x;
-                            acc[k].y |= x.y;
-                        }
-                    }
-                }
+        const ulonglong2 own = qok ? vin[(size_t)v * p.R + q] : make_ulonglong2(ONES, ONES);
+        const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
+        red[wib][lane] = gather_or<32>(p, vin, beg + 32 * wib, end, 32 * WARPS, q, qok, own);
+        __syncthreads();
+        if (wib == 0) {
+            ulonglong2 acc = red[0][lane];
+            for (int w = 1; w < WARPS; ++w) {
+                acc.x |= red[w][lane].x;
+                acc.y |= red[w][lane].y;
             }
-            // stop once every segment of this slot has found all its missing sources
-            bool more = false;
-#pragma unroll
-            for (int k = 0; k < SPL; ++k) {
-                act[k] = act[k] && !seg_full(make_ulonglong2(acc[k].x | own[k].x, acc[k].y | own[k].y));
-                more |= act[k];
-            }
-            if (!__any_sync(FULL, more)) break;
+            finish_item<32>(p, acc, own, orow, q, qok, v, it, hrow, level, any_new);
         }
-        // combine the slots' partial ORs
-#pragma unroll
-        for (int k = 0; k < SPL; ++k) {
-#pragma unroll
-            for (int off = G; off < 32; off <<= 1) {
-                acc[k].x |= __shfl_xor_sync(FULL, acc[k].x, off);
-                acc[k].y |= __shfl_xor_sync(FULL, acc[k].y, off);
-            }
-        }
-        int count = 0;
-        bool full = true;
-        if (slot == 0) {
-#pragma unroll
-            for (int k = 0; k < SPL; ++k) {
-                const int q = q0 + k * G;
-                if (q < a.R) {
-                    const ulonglong2 nw = make_ulonglong2(acc[k].x & ~own[k].x, acc[k].y & ~own[k].y);
-                    const ulonglong2 o = make_ulonglong2(own[k].x | nw.x, own[k].y | nw.y);
-                    out_row[q] = o;
-                    count += __popcll(nw.x) + __popcll(nw.y);
-                    full = full && seg_full(o);
-                }
-            }
-        }
-        count = __reduce_add_sync(FULL, count);
-        full = __all_sync(FULL, full);
-        if (lane == 0) {
-            if (count) {
-                a.hist_row[v] += count;
-                any_new = true;
-            }
-            if (full) a.sat[v] = a.level;
-        }
-    }
-    if (__syncthreads_or(any_new) && threadIdx.x == 0) *a.level_new = 1;
-}
-
-// Level 1 straight from the CSR: v's row holds v itself and its neighbours that
-// fall in the chunk, plus the always-set bits (sources >= n, padding word).
-// One thread per node; only that thread touches the row.
-__global__ void bfs_init_chunk(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
-                               int32_t w0, int32_t wn, int32_t stride, int32_t last_word,
-                               uint64_t last_mask, uint64_t *vis, int32_t *sat) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        uint64_t *row = vis + (size_t)v * stride;
-        for (int k = 0; k < stride; ++k) row[k] = (k < wn) ? 0ull : ONES;
-        if (last_word >= w0 && last_word < w0 + wn) row[last_word - w0] |= last_mask;
-        int k = (v >> 6) - w0;
-        if (k >= 0 && k < wn) row[k] |= 1ull << (v & 63);
-        for (int e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
-            const int u = col_idx[e];
-            k = (u >> 6) - w0;
-            if (k >= 0 && k < wn) row[k] |= 1ull << (u & 63);
-        }
-        bool full = true;
-        for (int q = 0; q < stride; ++q) full = full && (row[q] == ONES);
-        sat[v] = full ? 1 : NOT_SAT;
     }
 }
 
-// hist[0][v] = 1 (v itself), hist[1][v] = deg(v).
-__global__ void bfs_hist_first_rows(int32_t n, const int32_t *row_ptr, int32_t *hist) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        hist[v] = 1;
-        hist[(size_t)n + v] = row_ptr[v + 1] - row_ptr[v];
+// Light items: a warp takes GRAB list positions, one sat word per lane, and
+// runs the items a ballot marks (copy-ones items first, then pull items); the
+// pull items go to the next level's worklist.  The first pull level of a
+// launch lists every light item in order; later levels read the worklist.
+template <int G>
+__device__ __forceinline__ void light_items(const BfsParams &p, const int level, const bool from_list,
+                                            bool &any_new) {
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / G;
+    const int ql = lane % G;
+    const ulonglong2 *vin = p.buf[(level - 1) & 1];
+    ulonglong2 *vout = p.buf[level & 1];
+    int32_t *hrow = p.hist + (size_t)level * p.n;
+    const int first = (G == 32) ? p.order[p.n] * p.T : 0;   // heavy items go to heavy_items
+    const int32_t *src = p.wl[level & 1];
+    int32_t *dst = p.wl[(level + 1) & 1];
+    const int count = from_list ? *(volatile int32_t *)(p.wl_count + level) : p.n * p.T - first;
+    int32_t *ctr = p.light_ctr + level;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(ctr, GRAB);
+    base = __shfl_sync(FULL, base, 0);
+    while (base < count) {
+        int next = 0;
+        if (lane == 0) next = atomicAdd(ctr, GRAB);
+        const int pos = base + lane;
+        const bool has = lane < GRAB && pos < count;
+        const int it = has ? (from_list ? src[pos] : first + pos) : 0;
+        const int sv = has ? p.sat[it] : 0;
+        const bool ones = has && sv == level - 1;
+        const bool pull = has && sv > level - 1;
+        const int oi = it / p.T;
+        const int v_l = (ones || pull) ? p.order[oi] : 0;
+        const int t_l = it - oi * p.T;
+        const int beg_l = pull ? p.row_ptr[v_l] : 0;
+        const int end_l = pull ? p.row_ptr[v_l + 1] : 0;
+        unsigned mask = __ballot_sync(FULL, ones);
+        while (mask) {
+            const int b = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int v = __shfl_sync(FULL, v_l, b);
+            const int t = __shfl_sync(FULL, t_l, b);
+            const int q = t * 32 + ql;
+            if (slot == 0 && q < p.R) vout[(size_t)v * p.R + q] = make_ulonglong2(ONES, ONES);
+        }
+        const unsigned pulls = __ballot_sync(FULL, pull);
+        mask = pulls;
+        while (mask) {
+            const int b = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int v = __shfl_sync(FULL, v_l, b);
+            const int t = __shfl_sync(FULL, t_l, b);
+            const int sidx = __shfl_sync(FULL, it, b);
+            const int q = t * 32 + ql;
+            const bool qok = q < p.R;
+            const ulonglong2 own = qok ? vin[(size_t)v * p.R + q] : make_ulonglong2(ONES, ONES);
+            const int beg = __shfl_sync(FULL, beg_l, b), end = __shfl_sync(FULL, end_l, b);
+            const ulonglong2 acc = gather_or<G>(p, vin, beg, end, 32, q, qok, own);
+            finish_item<G>(p, acc, own, vout + (size_t)v * p.R, q, qok, v, sidx, hrow, level, any_new);
+        }
+        if (pulls) {
+            int at = 0;
+            if (lane == 0) at = atomicAdd(p.wl_count + level + 1, __popc(pulls));
+            at = __shfl_sync(FULL, at, 0);
+            if (pull) dst[at + __popc(pulls & ((1u << lane) - 1))] = it;
+        }
+        base = __shfl_sync(FULL, next, 0);
     }
 }
 
-typedef void (*pull_fn)(const LevelArgs);
-
-pull_fn pick_pull(int R, int *G_out) {
-    if (R <= 1) { *G_out = 1; return bfs_pull_level<1, 1>; }
-    if (R <= 2) { *G_out = 2; return bfs_pull_level<2, 1>; }
-    if (R <= 4) { *G_out = 4; return bfs_pull_level<4, 1>; }
-    if (R <= 8) { *G_out = 8; return bfs_pull_level<8, 1>; }
-    if (R <= 16) { *G_out = 16; return bfs_pull_level<16, 1>; }
-    *G_out = 32;
-    if (R <= 32) return bfs_pull_level<32, 1>;
-    if (R <= 64) return bfs_pull_level<32, 2>;
-    if (R <= 128) return bfs_pull_level<32, 4>;
-    return bfs_pull_level<32, 8>;
+template <int G>
+__global__ void __launch_bounds__(256) bfs_persistent(const BfsParams p) {
+    __shared__ ulonglong2 red[WARPS][32];
+    int level = p.start_level;
+    const bool stamp = p.stamp && blockIdx.x == 0 && threadIdx.x == 0;
+    if (stamp) p.stamp[level - 1] = global_ns();
+    if (level == 2) {
+        init_fill(p);
+        if (!grid_barrier(p.bar, p.status)) return;
+        init_bits(p);
+        if (!grid_barrier(p.bar, p.status)) return;
+        if (stamp) p.stamp[2] = global_ns();
+    }
+    for (;; ++level) {
+        if (level >= p.rows) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                p.status[1] = level;
+                atomicCAS(p.status, ST_DONE, ST_NEED_ROWS);
+            }
+            return;
+        }
+        bool any_new = false;
+        if (G == 32) heavy_items(p, level, any_new, red);
+        light_items<G>(p, level, level > p.start_level, any_new);
+        if (__syncthreads_or(any_new) && threadIdx.x == 0) p.level_new[level] = 1;
+        if (!grid_barrier(p.bar, p.status)) return;
+        if (stamp) p.stamp[level + 1] = global_ns();
+        if (*(volatile int32_t *)(p.level_new + level) == 0) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.status[1] = level;
 }
 
-// Grow hist to hold at least `rows` levels (new rows zeroed), keeping the old rows.
+typedef void (*bfs_fn)(const BfsParams);
+
+bfs_fn pick(int R, int *G) {
+    if (R <= 1) { *G = 1; return bfs_persistent<1>; }
+    if (R <= 2) { *G = 2; return bfs_persistent<2>; }
+    if (R <= 4) { *G = 4; return bfs_persistent<4>; }
+    if (R <= 8) { *G = 8; return bfs_persistent<8>; }
+    if (R <= 16) { *G = 16; return bfs_persistent<16>; }
+    *G = 32;
+    return bfs_persistent<32>;
+}
+
+// Grow hist to at least `rows` levels (new rows zeroed), keeping the old rows.
 qc_status ensure_hist_rows(qc_graph *g, int32_t rows, cudaStream_t stream) {
     if (rows <= g->hist_rows) return QC_OK;
     int32_t want = g->hist_rows ? g->hist_rows : 16;
     while (want < rows) want *= 2;
-    if (want > g->n + 1) want = g->n + 1 > rows ? g->n + 1 : rows;
+    if (want > g->n + 1) want = (g->n + 1 > rows) ? g->n + 1 : rows;
     qc_buffer nb;
     const size_t row_bytes = sizeof(int32_t) * (size_t)g->n;
     QC_TRY(nb.allocate(g->ctx, row_bytes * (size_t)want, stream));
@@ -218,28 +414,31 @@ qc_status ensure_hist_rows(qc_graph *g, int32_t rows, cudaStream_t stream) {
 
 }  // namespace
 
-// Modelled algorithmic bytes of one level launch over a chunk of wn source words
+// Modelled algorithmic bytes of one level pass over a chunk of wn source words
 // (pull over every node): per node and word, gather the row word of each
 // neighbour, read the node's own word and write it back, plus one write of the
 // next-frontier word (8 wn (E + 3N)); the CSR once (4(N+1) + 4E); one histogram
 // row (4N).
-static double bfs_level_model_bytes(int64_t n, int64_t nnz, int64_t wn) {
+double qc_bfs_level_model_bytes(int64_t n, int64_t nnz, int64_t wn) {
     return 8.0 * (double)wn * (double)(nnz + 3 * n) + 4.0 * (double)(n + 1) + 4.0 * (double)nnz +
            4.0 * (double)n;
 }
 
-// Words of sources handled per chunk: as many as keep both bitset buffers within
-// about half of L2 (they are re-read once per neighbour per level), at most 512.
+// Words of sources per chunk: as many as keep both bitset buffers within about
+// half of L2 (they are re-read once per neighbour per level), at most 512.
 // QCGRAPH_CHUNK_WORDS overrides the choice (tests use it to force many chunks).
-static int32_t choose_chunk_words(const qc_graph *g) {
-    const int64_t W = (g->n + 63) / 64;
+int32_t qc_bfs_chunk_words(const qc_ctx *ctx, int32_t n) {
+    const int64_t W = (n + 63) / 64;
+    int64_t wc;
     if (const char *env = getenv("QCGRAPH_CHUNK_WORDS")) {
-        int64_t forced = atoll(env);
-        if (forced >= 1) return (int32_t)(forced < W ? forced : W);
+        wc = atoll(env);
+        if (wc < 1) wc = 1;
+    } else {
+        const size_t target = ctx->l2_bytes ? ctx->l2_bytes / 2 : (size_t)48 << 20;
+        wc = (int64_t)(target / (2 * 8 * (size_t)n));
+        if (wc > 2) wc &= ~int64_t(1);
+        if (wc < 2) wc = 2;
     }
-    const size_t target = g->ctx->l2_bytes ? g->ctx->l2_bytes / 2 : (size_t)48 << 20;
-    int64_t wc = (int64_t)(target / (2 * 8 * (size_t)g->n));
-    if (wc < 2) wc = 2;
     if (wc > 512) wc = 512;
     if (wc > W) wc = W;
     return (int32_t)wc;
@@ -248,96 +447,130 @@ static int32_t choose_chunk_words(const qc_graph *g) {
 qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
     qc_ctx *ctx = g->ctx;
     const int32_t n = g->n;
-    const int64_t W = (n + 63) / 64;
-    const int32_t wc = choose_chunk_words(g);
-    const int32_t R_max = (wc + 1) / 2;
+    const int32_t W = (n + 63) / 64;
     g->hist_valid = false;
     g->D = g->nnz > 0 ? 1 : 0;
-    QC_TRY(ensure_hist_rows(g, 2, stream));
-    const int threads = 256;
-    const int node_blocks = qc_ceil_div(n, threads) < 4 * ctx->num_sms ? qc_ceil_div(n, threads)
-                                                                         : 4 * ctx->num_sms;
-    bfs_hist_first_rows<<<node_blocks, threads, 0, stream>>>(n, g->row_ptr.as<int32_t>(),
-                                                           g->hist.as<int32_t>());
-    QC_LAUNCHED(ctx);
+    QC_TRY(qc_graph_prepare(g, stream));
+    QC_TRY(ensure_hist_rows(g, g->nnz > 0 ? 32 : 2, stream));
     if (g->nnz == 0) {
+        // no edges: h(0) = 1 for every node, nothing else
+        QC_TRY(qc_fill_first_rows(g, stream));
         g->hist_valid = true;
         return QC_OK;
     }
-    qc_buffer visA, visB, sat, flags;
+    const int32_t wc = qc_bfs_chunk_words(ctx, n);
+    const int32_t R_max = (wc + 1) / 2;
+    const int32_t T_max = R_max >= 32 ? (R_max + 31) / 32 : 1;
+    qc_buffer visA, visB, sat, ctl, wl;
     const size_t vis_bytes = sizeof(ulonglong2) * (size_t)R_max * (size_t)n;
     QC_TRY(visA.allocate(ctx, vis_bytes, stream));
     QC_TRY(visB.allocate(ctx, vis_bytes, stream));
-    QC_TRY(sat.allocate(ctx, sizeof(int32_t) * (size_t)n, stream));
-    const int32_t max_levels = n + 2;
-    QC_TRY(flags.allocate(ctx, sizeof(int32_t) * (size_t)max_levels, stream));
-    int32_t *h_flag = nullptr;
-    QC_CUDA_TRY(ctx, cudaMallocHost(&h_flag, sizeof(int32_t)));
-    struct PinnedGuard { int32_t *p; ~PinnedGuard() { cudaFreeHost(p); } } guard{h_flag};
+    QC_TRY(sat.allocate(ctx, sizeof(int32_t) * (size_t)n * T_max, stream));
+    QC_TRY(wl.allocate(ctx, 2 * sizeof(int32_t) * (size_t)n * T_max, stream));
+    // control block: status (2 ints), barrier (2 uints), pad, then level_new, the
+    // per-level work counters (light, heavy) and worklist lengths, each with room for
+    // any depth (<= n + 1)
+    const size_t ctl_ints = 8 + 4 * ((size_t)n + 2);
+    QC_TRY(ctl.allocate(ctx, sizeof(int32_t) * ctl_ints, stream));
+    qc_pinned pin(ctx);
+    QC_TRY(pin.acquire());
+    int32_t *h_status = static_cast<int32_t *>(pin.ptr);
 
     const bool timing = ctx->timing.load();
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    struct EventGuard {
-        cudaEvent_t *e;
-        ~EventGuard() { for (int i = 0; i < 2; ++i) if (e[i]) cudaEventDestroy(e[i]); }
-    } ev_guard{ev};
+    qc_event_pair ev;
+    qc_buffer stamps;
     if (timing) {
-        QC_CUDA_TRY(ctx, cudaEventCreate(&ev[0]));
-        QC_CUDA_TRY(ctx, cudaEventCreate(&ev[1]));
+        QC_TRY(ev.create(ctx));
+        QC_TRY(stamps.allocate(ctx, sizeof(unsigned long long) * ((size_t)n + 3), stream));
     }
-    const int32_t last_word = (int32_t)(W - 1);
+
     const uint64_t last_mask = (n % 64) ? (ONES << (n % 64)) : 0ull;
-    int dev_blocks_per_sm = 0;
-    for (int64_t w0 = 0; w0 < W; w0 += wc) {
-        const int32_t wn = (int32_t)((W - w0) < wc ? (W - w0) : wc);
+    for (int32_t w0 = 0; w0 < W; w0 += wc) {
+        const int32_t wn = (W - w0) < wc ? (W - w0) : wc;
         const int32_t R = (wn + 1) / 2;
-        bfs_init_chunk<<<qc_ceil_div(n, 128), 128, 0, stream>>>(
-            n, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(), (int32_t)w0, wn, 2 * R,
-            last_word, last_mask, visA.as<uint64_t>(), sat.as<int32_t>());
-        QC_LAUNCHED(ctx);
-        QC_CUDA_TRY(ctx, cudaMemsetAsync(flags.ptr, 0, flags.bytes, stream));
+        const int32_t T = R >= 32 ? (R + 31) / 32 : 1;
         int G = 32;
-        pull_fn fn = pick_pull(R, &G);
-        if (!dev_blocks_per_sm) {
-            QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&dev_blocks_per_sm,
-                                                                           (const void *)fn, 256, 0));
-            if (dev_blocks_per_sm < 1) dev_blocks_per_sm = 1;
+        bfs_fn fn = pick(R, &G);
+        int per_sm = 0;
+        QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, 256, 0));
+        if (per_sm < 1) {
+            qc_set_error(ctx, "BFS kernel cannot be resident on an SM");
+            return QC_ERR_CUDA;
         }
-        const int warps_needed = n;
-        int blocks = qc_ceil_div(warps_needed, 8);
-        const int cap_blocks = dev_blocks_per_sm * ctx->num_sms;
-        if (blocks > cap_blocks) blocks = cap_blocks;
-        ulonglong2 *in = visA.as<ulonglong2>(), *out = visB.as<ulonglong2>();
-        for (int32_t level = 2; level <= n; ++level) {
-            QC_TRY(ensure_hist_rows(g, level + 1, stream));
-            LevelArgs a;
-            a.n = n;
-            a.row_ptr = g->row_ptr.as<int32_t>();
-            a.col_idx = g->col_idx.as<int32_t>();
-            a.vis_in = in;
-            a.vis_out = out;
-            a.R = R;
-            a.sat = sat.as<int32_t>();
-            a.level = level;
-            a.hist_row = g->hist.as<int32_t>() + (size_t)level * n;
-            a.level_new = flags.as<int32_t>() + level;
-            if (timing) QC_CUDA_TRY(ctx, cudaEventRecord(ev[0], stream));
-            fn<<<blocks, 256, 0, stream>>>(a);
+        const int items = n * T;
+        int blocks = per_sm * ctx->num_sms;
+        if (blocks > qc_ceil_div(items, 8)) blocks = qc_ceil_div(items, 8);
+        if (blocks < 1) blocks = 1;
+        int32_t start = 2;
+        while (true) {
+            BfsParams p;
+            p.n = n;
+            p.row_ptr = g->row_ptr.as<int32_t>();
+            p.col_idx = g->col_idx.as<int32_t>();
+            p.order = g->order.as<int32_t>();
+            p.comp = g->comp.as<int32_t>();
+            p.wcomp = g->wcomp.as<int32_t>();
+            p.buf[0] = visB.as<ulonglong2>();
+            p.buf[1] = visA.as<ulonglong2>();
+            p.R = R;
+            p.T = T;
+            p.w0 = w0;
+            p.wn = wn;
+            p.W = W;
+            p.last_mask = last_mask;
+            p.sat = sat.as<int32_t>();
+            p.hist = g->hist.as<int32_t>();
+            p.rows = g->hist_rows;
+            p.first_chunk = (w0 == 0);
+            p.start_level = start;
+            p.status = ctl.as<int32_t>();
+            p.bar = reinterpret_cast<unsigned *>(ctl.as<int32_t>() + 2);
+            p.level_new = ctl.as<int32_t>() + 8;
+            p.light_ctr = p.level_new + (n + 2);
+            p.heavy_ctr = p.light_ctr + (n + 2);
+            p.wl_count = p.heavy_ctr + (n + 2);
+            p.wl[0] = wl.as<int32_t>();
+            p.wl[1] = wl.as<int32_t>() + (size_t)n * T_max;
+            p.stamp = timing ? stamps.as<unsigned long long>() : nullptr;
+            QC_CUDA_TRY(ctx, cudaMemsetAsync(ctl.ptr, 0, ctl.bytes, stream));
+            void *args[] = {(void *)&p};
+            if (timing) QC_CUDA_TRY(ctx, cudaEventRecord(ev.a, stream));
+            QC_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(256), args,
+                                                         0, stream));
             QC_LAUNCHED(ctx);
-            if (timing) QC_CUDA_TRY(ctx, cudaEventRecord(ev[1], stream));
-            QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_flag, a.level_new, sizeof(int32_t),
+            if (timing) QC_CUDA_TRY(ctx, cudaEventRecord(ev.b, stream));
+            QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_status, ctl.ptr, 2 * sizeof(int32_t),
                                              cudaMemcpyDeviceToHost, stream));
             QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+            const int32_t st = h_status[0], reached = h_status[1];
             if (timing) {
                 float ms = 0.f;
-                QC_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ev[0], ev[1]));
-                qc_record_kernel(ctx, "bfs_level", ms, bfs_level_model_bytes(n, g->nnz, wn));
+                QC_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ev.a, ev.b));
+                const int passes = reached - start + 1 + (start == 2 ? 1 : 0);
+                const double per_pass = qc_bfs_level_model_bytes(n, g->nnz, wn);
+                qc_record_kernel(ctx, "bfs_level", ms, passes * per_pass);
+                // stamp[l] opens level l (stamp[1] = launch start; the set-up covers levels 1-2)
+                std::vector<unsigned long long> h((size_t)reached + 2);
+                QC_CUDA_TRY(ctx, cudaMemcpy(h.data(), stamps.ptr, sizeof(unsigned long long) * h.size(),
+                                            cudaMemcpyDeviceToHost));
+                for (int l = start - 1; l <= reached && l + 1 < (int)h.size(); ++l) {
+                    if (!h[l] || !h[l + 1] || h[l + 1] < h[l]) continue;
+                    char name[32];
+                    snprintf(name, sizeof name, "bfs_pass_%d", l);
+                    qc_record_kernel(ctx, name, (double)(h[l + 1] - h[l]) * 1e-6, per_pass);
+                }
             }
-            if (!*h_flag) break;
-            if (level > g->D) g->D = level;
-            ulonglong2 *t = in;
-            in = out;
-            out = t;
+            if (st == ST_TIMEOUT) {
+                qc_set_error(ctx, "BFS grid barrier timed out (chunk at word %d)", w0);
+                return QC_ERR_TIMEOUT;
+            }
+            if (st == ST_NEED_ROWS) {
+                QC_TRY(ensure_hist_rows(g, reached + 1, stream));
+                start = reached;
+                continue;
+            }
+            if (reached - 1 > g->D) g->D = reached - 1;
+            break;
         }
     }
     g->hist_valid = true;

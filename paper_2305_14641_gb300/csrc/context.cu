@@ -52,6 +52,35 @@ void qc_mem_free(qc_ctx *ctx, void *ptr, size_t bytes, cudaStream_t stream) {
     ctx->in_use.fetch_sub(bytes);
 }
 
+qc_ctx::~qc_ctx() {
+    for (void *p : pinned_free) cudaFreeHost(p);
+}
+
+qc_status qc_pinned::acquire() {
+    {
+        std::lock_guard<std::mutex> lk(ctx->pinned_mu);
+        if (!ctx->pinned_free.empty()) {
+            ptr = ctx->pinned_free.back();
+            ctx->pinned_free.pop_back();
+            return QC_OK;
+        }
+    }
+    QC_CUDA_TRY(ctx, cudaMallocHost(&ptr, QC_PINNED_BYTES));
+    return QC_OK;
+}
+
+qc_pinned::~qc_pinned() {
+    if (!ptr) return;
+    std::lock_guard<std::mutex> lk(ctx->pinned_mu);
+    ctx->pinned_free.push_back(ptr);
+}
+
+qc_status qc_event_pair::create(qc_ctx *ctx) {
+    QC_CUDA_TRY(ctx, cudaEventCreate(&a));
+    QC_CUDA_TRY(ctx, cudaEventCreate(&b));
+    return QC_OK;
+}
+
 void qc_record_kernel(qc_ctx *ctx, const char *kernel, double ms, double model_bytes) {
     std::lock_guard<std::mutex> lk(ctx->stats_mu);
     qc_kernel_stats &st = ctx->stats[kernel];
@@ -125,6 +154,16 @@ qc_status qc_context_create(int device, size_t mem_budget_bytes, const qc_alloca
     ctx->l2_bytes = (size_t)v;
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     ctx->smem_optin = (size_t)v;
+    if (!alloc) {
+        // keep freed blocks in the stream-ordered pool instead of returning them to
+        // the driver at every synchronisation (a process-local pool setting)
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
     *out = ctx;
     return QC_OK;
 }

@@ -6,6 +6,16 @@
 // its own center.  Strict descent makes every parent chain strictly decreasing
 // in V, so chains end at roots (parent(r) = r) and never cycle.
 //
+// Comparisons run on order-preserving 64-bit integer keys of the doubles
+// (IEEE order, -0 and +0 equal), which the integer pipe compares far faster
+// than GB300's binary64 pipe; for NaN-free V the outcome of every comparison
+// is the same as comparing the doubles.  Keys are laid out node-major,
+// K[v * S + s], so one neighbour's S keys are one contiguous run.
+//
+// Parents: one warp per node; lane j scans neighbours j, j + 32, ... keeping
+// the best (key, id) for up to 16 sigma values, then a butterfly over the 32
+// lanes combines them (the result does not depend on the scan order).
+//
 // Roots: every (sigma, node) thread walks its chain with path halving
 // (parent[x] <- parent[parent[x]]) in a scratch parent array; concurrent walkers
 // only ever replace a pointer by another ancestor of the same node, so any
@@ -16,25 +26,86 @@
 
 namespace {
 
-__global__ void ggd_parent_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
-                                  const int32_t *__restrict__ col_idx, const double *__restrict__ V,
-                                  int32_t *__restrict__ parent) {
-    const int s = blockIdx.y;
-    const double *Vs = V + (size_t)s * n;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const double vv = Vs[v];
-        int best = -1;
-        double bv = 0.0;
-        const int end = row_ptr[v + 1];
-        for (int e = row_ptr[v]; e < end; ++e) {
-            const int u = col_idx[e];
-            const double x = Vs[u];
-            if (best < 0 || x < bv || (x == bv && u < best)) {
-                best = u;
-                bv = x;
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ long long order_key(double x) {
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ull) b = 0;          // -0 compares equal to +0
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+
+// K[v * S + s] = key(V[s * n + v]) through 32 x 32 shared-memory tiles.
+__global__ void key_transpose(int32_t n, int32_t S, const double *__restrict__ V, long long *__restrict__ K) {
+    __shared__ long long tile[32][33];
+    const int v0 = blockIdx.x * 32, s0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int s = s0 + r, v = v0 + threadIdx.x;
+        if (s < S && v < n) tile[r][threadIdx.x] = order_key(V[(size_t)s * n + v]);
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int v = v0 + r, s = s0 + threadIdx.x;
+        if (s < S && v < n) K[(size_t)v * S + s] = tile[threadIdx.x][r];
+    }
+}
+
+// (k, u) precedes (bk, best): smaller key, then smaller id; best < 0 = none yet.
+__device__ __forceinline__ bool better(long long k, int u, long long bk, int best) {
+    return best < 0 || k < bk || (k == bk && u < best);
+}
+
+// Sigma values s0 .. s0 + sn - 1 (sn <= SB).
+template <int SB>
+__global__ void __launch_bounds__(256) ggd_parent_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
+                                                         const int32_t *__restrict__ col_idx,
+                                                         const long long *__restrict__ K, int32_t S,
+                                                         int32_t s0, int32_t sn,
+                                                         int32_t *__restrict__ parent) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int v = warp; v < n; v += nwarps) {
+        const int beg = row_ptr[v], end = row_ptr[v + 1];
+        long long bk[SB];
+        int best[SB];
+#pragma unroll
+        for (int k = 0; k < SB; ++k) {
+            bk[k] = 0;
+            best[k] = -1;
+        }
+        for (int j = beg + lane; j < end; j += 32) {
+            const int u = col_idx[j];
+            const long long *row = K + (size_t)u * S + s0;
+#pragma unroll
+            for (int k = 0; k < SB; ++k) {
+                if (k < sn) {
+                    const long long x = row[k];
+                    if (better(x, u, bk[k], best[k])) {
+                        bk[k] = x;
+                        best[k] = u;
+                    }
+                }
             }
         }
-        parent[(size_t)s * n + v] = (best >= 0 && bv < vv) ? best : v;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+            for (int k = 0; k < SB; ++k) {
+                const long long ok = __shfl_xor_sync(FULL, bk[k], off);
+                const int ob = __shfl_xor_sync(FULL, best[k], off);
+                if (ob >= 0 && better(ok, ob, bk[k], best[k])) {
+                    bk[k] = ok;
+                    best[k] = ob;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < SB; ++k) {
+            if (lane == k && k < sn) {
+                const long long own = K[(size_t)v * S + s0 + k];
+                parent[(size_t)(s0 + k) * n + v] = (best[k] >= 0 && bk[k] < own) ? best[k] : v;
+            }
+        }
     }
 }
 
@@ -55,8 +126,19 @@ __global__ void find_roots_kernel(int32_t n, int32_t *parent, int32_t *__restric
         if (x == v) ++roots;
         labels[(size_t)s * n + v] = x;
     }
-    roots = __reduce_add_sync(0xffffffffu, roots);
+    roots = __reduce_add_sync(FULL, roots);
     if ((threadIdx.x & 31) == 0 && roots) atomicAdd(n_roots + s, roots);
+}
+
+typedef void (*parent_fn)(int32_t, const int32_t *, const int32_t *, const long long *, int32_t,
+                          int32_t, int32_t, int32_t *);
+
+parent_fn pick_parent(int sn) {
+    if (sn <= 1) return ggd_parent_kernel<1>;
+    if (sn <= 2) return ggd_parent_kernel<2>;
+    if (sn <= 4) return ggd_parent_kernel<4>;
+    if (sn <= 8) return ggd_parent_kernel<8>;
+    return ggd_parent_kernel<16>;
 }
 
 }  // namespace
@@ -64,13 +146,22 @@ __global__ void find_roots_kernel(int32_t n, int32_t *parent, int32_t *__restric
 qc_status qc_descend(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                      const double *V, int32_t n_sigma, int32_t *labels, int32_t *n_roots_dev,
                      cudaStream_t stream) {
-    const int blocks = qc_ceil_div(n, 256) < 2 * ctx->num_sms ? qc_ceil_div(n, 256) : 2 * ctx->num_sms;
-    dim3 grid(blocks, n_sigma);
-    qc_buffer parent;
+    qc_buffer parent, keys;
     QC_TRY(parent.allocate(ctx, sizeof(int32_t) * (size_t)n * (size_t)n_sigma, stream));
-    ggd_parent_kernel<<<grid, 256, 0, stream>>>(n, row_ptr, col_idx, V, parent.as<int32_t>());
+    QC_TRY(keys.allocate(ctx, sizeof(long long) * (size_t)n * (size_t)n_sigma, stream));
+    key_transpose<<<dim3(qc_ceil_div(n, 32), qc_ceil_div(n_sigma, 32)), dim3(32, 8), 0, stream>>>(
+        n, n_sigma, V, keys.as<long long>());
     QC_LAUNCHED(ctx);
-    find_roots_kernel<<<grid, 256, 0, stream>>>(n, parent.as<int32_t>(), labels, n_roots_dev);
+    const int wblocks = qc_ceil_div(n, 8) < 16 * ctx->num_sms ? qc_ceil_div(n, 8) : 16 * ctx->num_sms;
+    for (int32_t s0 = 0; s0 < n_sigma; s0 += 16) {
+        const int32_t sn = (n_sigma - s0) < 16 ? (n_sigma - s0) : 16;
+        pick_parent(sn)<<<wblocks, 256, 0, stream>>>(n, row_ptr, col_idx, keys.as<long long>(), n_sigma,
+                                                     s0, sn, parent.as<int32_t>());
+        QC_LAUNCHED(ctx);
+    }
+    const int blocks = qc_ceil_div(n, 256) < 2 * ctx->num_sms ? qc_ceil_div(n, 256) : 2 * ctx->num_sms;
+    find_roots_kernel<<<dim3(blocks, n_sigma), 256, 0, stream>>>(n, parent.as<int32_t>(), labels,
+                                                                 n_roots_dev);
     QC_LAUNCHED(ctx);
     return QC_OK;
 }

@@ -35,7 +35,9 @@ __global__ void potential_kernel(int32_t n, int32_t D, const int32_t *__restrict
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         double sum1 = 0.0, sum2 = 0.0;
         for (int d = 0; d <= D; ++d) {
-            const double h = (double)hist[(size_t)d * n + v];
+            const int c = hist[(size_t)d * n + v];
+            if (c == 0) continue;          // adds +0.0 to non-negative sums: no change
+            const double h = (double)c;
             sum1 = __dadd_rn(sum1, __dmul_rn(h, us[d]));
             sum2 = __dadd_rn(sum2, __dmul_rn(h, ws[d]));
         }

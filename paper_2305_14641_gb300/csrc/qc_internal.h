@@ -43,6 +43,32 @@ struct qc_ctx {
     std::atomic<bool> timing{false};
     std::mutex stats_mu;
     std::map<std::string, qc_kernel_stats> stats;
+    std::mutex pinned_mu;
+    std::vector<void *> pinned_free;       // 64 KiB pinned host blocks ready for reuse
+    ~qc_ctx();
+};
+
+// A pinned host block of QC_PINNED_BYTES for small device<->host transfers,
+// taken from the context's pool and given back on destruction.
+#define QC_PINNED_BYTES (64u << 10)
+struct qc_pinned {
+    qc_ctx *ctx;
+    void *ptr = nullptr;
+    explicit qc_pinned(qc_ctx *c) : ctx(c) {}
+    qc_pinned(const qc_pinned &) = delete;
+    qc_pinned &operator=(const qc_pinned &) = delete;
+    qc_status acquire();
+    ~qc_pinned();
+};
+
+// Two CUDA events for timing one launch.
+struct qc_event_pair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    qc_status create(qc_ctx *ctx);
+    ~qc_event_pair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
 };
 
 // Count one launch (and surface launch-configuration errors).
@@ -121,7 +147,23 @@ struct qc_graph {
     int32_t D = 0;           // largest finite hop distance
     int32_t hist_rows = 0;   // allocated rows of hist
     qc_buffer hist;          // int32[hist_rows][n], level-major
+    // preparation (see prep.cu), computed once
+    bool prepared = false;
+    qc_buffer comp;          // int32[n] component = smallest node id in it
+    qc_buffer wcomp;         // int32[W] component of a whole 64-source word, or -1
+    qc_buffer order;         // int32[n] nodes, heaviest degree bucket first
 };
+
+// prep.cu
+// Degree bucket (floor(log2(deg + 1))) from which a row counts as heavy: its BFS
+// item is shared by all warps of a block instead of one warp.
+#define QC_HEAVY_BUCKET 6
+qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream);
+// hist[0][v] = 1, hist[1][v] = deg(v)
+qc_status qc_fill_first_rows(qc_graph *g, cudaStream_t stream);
+// bfs.cu helpers shared with the batched paths
+double qc_bfs_level_model_bytes(int64_t n, int64_t nnz, int64_t wn);
+int32_t qc_bfs_chunk_words(const qc_ctx *ctx, int32_t n);
 
 // ---- entry points implemented per translation unit ---------------------------------
 

@@ -166,3 +166,33 @@ def test_budget(qc):
         g.close()
         torch.cuda.synchronize()
         assert c.bytes_in_use() == 0
+
+
+def test_descent_on_given_potentials(qc, ctx):
+    """GGD and roots alone, on seeded potentials with negatives, many exact ties,
+    and -0.0 next to +0.0 (equal under IEEE comparison)."""
+    g = gg.rng(28)
+    for graph in [gg.planted_partition(3000, 8, 0.01, 0.001, g), gg.erdos_renyi(500, 0.05, g),
+                  gg.star(40, 7), gg.complete(30)]:
+        G = qc.Graph.from_graph(ctx, graph)
+        S = 5
+        V = np.round(g.normal(size=(S, graph.n)), 1)          # heavy ties
+        V[1] = np.abs(V[1])
+        V[2] = np.where(g.random(graph.n) < 0.5, -0.0, 0.0)    # only signed zeros
+        V[3] = g.integers(0, 3, size=graph.n).astype(np.float64)
+        Vd = torch.tensor(V, device="cuda")
+        labels, counts = G.ggd_labels(Vd)
+        labels = labels.cpu().numpy()
+        for s in range(S):
+            p, _ = oracle.ggd_parent(graph, V[s])
+            lab, k = oracle.find_centers(p)
+            assert np.array_equal(labels[s], lab), (graph.name, s)
+            assert counts[s] == k
+        G.close()
+
+
+def test_many_sigmas_in_groups(qc, ctx):
+    """More sigma values than one descent launch handles (groups of 16)."""
+    graph = gg.planted_partition(1200, 6, 0.03, 0.002, gg.rng(29))
+    sigmas = [0.4 + 0.1 * k for k in range(37)]
+    assert_solution_matches(qc, ctx, graph, sigmas)
