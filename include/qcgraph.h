@@ -192,24 +192,40 @@ qc_status qc_solve_batch(qc_ctx *ctx, int32_t n_graphs, qc_graph *const *graphs,
 /* ---- serving ------------------------------------------------------------------ */
 
 typedef struct {
-    size_t mem_budget_bytes;   /* admission budget for resident requests (0 = the context's) */
+    size_t mem_budget_bytes;   /* admission budget for resident requests (0 = the context's,
+                                  or 100 GB if the context has none) */
     int32_t max_active;        /* most requests on the GPU at once (0 = 256) */
+    int32_t streams;           /* batched launches in flight at once (0 = 4) */
 } qc_server_config;
 
 typedef struct {
     uint64_t submitted, completed, cancelled, failed;
-    uint64_t steps;            /* scheduler iterations that launched GPU work */
-    size_t bytes_resident;     /* admitted requests' bytes right now */
+    uint64_t steps;            /* batched launches the scheduler issued */
+    uint64_t large_solved;     /* requests solved one by one on the large-graph worker */
+    size_t bytes_resident;     /* admitted requests' estimated bytes right now */
     size_t peak_bytes_resident;
     int32_t active, queued;
+    int32_t peak_in_flight;    /* most batched launches on the GPU at once */
 } qc_server_stats;
 
-/* A serving loop on its own host thread and CUDA stream: submitted requests
- * wait in FIFO order until their memory estimate fits the budget and a slot is
- * free, then join the requests already on the GPU (continuous batching: every
- * scheduler step advances all active requests by one BFS level in one launch;
- * requests that finish their BFS get their potential, descent and roots, and
- * leave).  cfg may be NULL for defaults. */
+/* Per-request times on the host clock (milliseconds from submission). */
+typedef struct {
+    double admit_ms;           /* admitted to the GPU */
+    double done_ms;            /* result available (the request's latency) */
+    int32_t n;
+    int64_t nnz;
+    int32_t batch_size;        /* requests in the launch that carried it (0: large-graph worker) */
+} qc_request_info;
+
+/* A serving loop on its own host threads: submitted requests wait in FIFO
+ * order until their memory estimate fits the budget and a slot is free.
+ * Admitted requests up to qc's graph-per-CTA limit (8192 nodes) are grouped
+ * into one launch of the batched kernel per scheduler step; several such
+ * launches run at once on separate streams, so requests that arrive while
+ * others are on the GPU start without waiting for them (continuous batching).
+ * Larger requests go to a worker thread that runs the single-graph path.
+ * A request's result does not depend on what it shares the GPU with.
+ * cfg may be NULL for defaults. */
 qc_status qc_server_create(qc_ctx *ctx, const qc_server_config *cfg, qc_server **out);
 /* Queue one request: a host CSR (copied before the call returns; same layout
  * and validation as qc_graph_create with QC_VALIDATE) and its sigma.
@@ -218,16 +234,17 @@ qc_status qc_server_create(qc_ctx *ctx, const qc_server_config *cfg, qc_server *
  * alone exceeds the budget). */
 qc_status qc_server_submit(qc_server *s, int32_t n, int64_t nnz, const int32_t *row_ptr,
                            const int32_t *col_idx, double sigma, uint64_t *req_id);
-/* Non-blocking: *done = 1 and labels_out (host int32[n]) / *n_clusters filled
- * when the request has completed, else *done = 0.  A completed request's result
- * is released after it has been read.  Returns the request's own error status
- * if it failed, QC_ERR_INVALID_ARG for an unknown id. */
+/* Non-blocking: *done = 1 and labels_out (host int32[n], root node ids),
+ * *n_clusters and *info filled when the request has completed, else *done = 0.
+ * labels_out, n_clusters and info may each be NULL.  A completed request's
+ * result is released after it has been read.  Returns the request's own error
+ * status if it failed, QC_ERR_INVALID_ARG for an unknown id. */
 qc_status qc_server_poll(qc_server *s, uint64_t req_id, int32_t *labels_out,
-                         int32_t *n_clusters, int *done);
+                         int32_t *n_clusters, qc_request_info *info, int *done);
 /* Blocking form of poll: waits up to timeout_ms (< 0: no limit); returns
  * QC_ERR_NOT_READY if the time ran out. */
 qc_status qc_server_wait(qc_server *s, uint64_t req_id, int64_t timeout_ms,
-                         int32_t *labels_out, int32_t *n_clusters);
+                         int32_t *labels_out, int32_t *n_clusters, qc_request_info *info);
 /* Cancel a queued or active request (its memory is released at the next step). */
 qc_status qc_server_cancel(qc_server *s, uint64_t req_id);
 qc_status qc_server_get_stats(qc_server *s, qc_server_stats *out);

@@ -197,3 +197,136 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class BatchPlan:
+    """Algorithm 4 for many graphs at once (one sigma per graph), planned once and
+    replayed: one persistent graph-per-CTA kernel captured in a CUDA graph.
+
+    labels: int32 tensor [sum of n] on the GPU; graph k's labels (root node ids,
+    local to graph k) are labels[offsets[k] : offsets[k] + n_k].
+    """
+
+    def __init__(self, ctx: Context, graphs: Sequence[Graph], sigmas: Sequence[float], stream=None):
+        torch = _torch()
+        if len(graphs) != len(sigmas) or not graphs:
+            raise ValueError("need one sigma per graph and at least one graph")
+        self.ctx = ctx
+        self.graphs = list(graphs)
+        sizes = [g.n for g in graphs]
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+        self.labels = torch.empty(int(sum(sizes)), dtype=torch.int32, device=f"cuda:{ctx.device}")
+        arr = (ctypes.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+        sig = (ctypes.c_double * len(graphs))(*[float(s) for s in sigmas])
+        off = (ctypes.c_int64 * len(graphs))(*[int(o) for o in self.offsets])
+        h = ctypes.c_void_p()
+        ctx.check(ctx._lib.qc_batch_create(ctx.handle, len(graphs), arr, sig, self.labels.data_ptr(), off,
+                                           _stream_handle(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None, counts: bool = True):
+        """Run the plan; returns the clusters per graph (host ints) or None."""
+        nc = (ctypes.c_int32 * len(self.graphs))() if counts else None
+        self.ctx.check(self.ctx._lib.qc_batch_run(self.handle, nc, _stream_handle(stream)))
+        return list(nc) if counts else None
+
+    def labels_of(self, k: int):
+        o = int(self.offsets[k])
+        return self.labels[o:o + self.graphs[k].n]
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            self.ctx._lib.qc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(ctx: Context, graphs: Sequence[Graph], sigmas: Sequence[float], stream=None):
+    """One-shot batched solve: (labels tensor, offsets)."""
+    plan = BatchPlan(ctx, graphs, sigmas, stream)
+    plan.run(stream, counts=False)
+    labels, offsets = plan.labels, plan.offsets
+    plan.close()
+    return labels, offsets
+
+
+class Server:
+    """A serving loop (host threads inside the library): submit CSR graphs with a
+    sigma each, collect labels.  Uses its own context with the stream-ordered CUDA
+    allocator so that the library's threads never call back into Python."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 100 << 30, max_active: int = 256,
+                 streams: int = 4):
+        self.ctx = Context(device, allocator="cuda")
+        cfg = native.qc_server_config(int(mem_budget_bytes), int(max_active), int(streams))
+        h = ctypes.c_void_p()
+        self.ctx.check(self.ctx._lib.qc_server_create(self.ctx.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._n = {}
+
+    def submit(self, row_ptr, col_idx, sigma: float) -> int:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        rid = ctypes.c_uint64()
+        self.ctx.check(self.ctx._lib.qc_server_submit(self.handle, len(rp) - 1, len(ci), rp.ctypes.data,
+                                                      ci.ctypes.data if len(ci) else None, float(sigma),
+                                                      ctypes.byref(rid)))
+        self._n[rid.value] = len(rp) - 1
+        return rid.value
+
+    def _result(self, rid, labels, nc, info):
+        return {"labels": labels, "n_clusters": nc.value, "admit_ms": info.admit_ms,
+                "latency_ms": info.done_ms, "batch_size": info.batch_size}
+
+    def poll(self, rid: int):
+        """The result dict if the request has completed, else None."""
+        n = self._n[rid]
+        labels = np.empty(n, dtype=np.int32)
+        nc = ctypes.c_int32()
+        info = native.qc_request_info()
+        done = ctypes.c_int()
+        st = self.ctx._lib.qc_server_poll(self.handle, rid, labels.ctypes.data, ctypes.byref(nc),
+                                          ctypes.byref(info), ctypes.byref(done))
+        if not done.value:
+            self.ctx.check(st)
+            return None
+        self._n.pop(rid, None)
+        self.ctx.check(st)
+        return self._result(rid, labels, nc, info)
+
+    def wait(self, rid: int, timeout_ms: int = -1):
+        n = self._n[rid]
+        labels = np.empty(n, dtype=np.int32)
+        nc = ctypes.c_int32()
+        info = native.qc_request_info()
+        st = self.ctx._lib.qc_server_wait(self.handle, rid, int(timeout_ms), labels.ctypes.data,
+                                          ctypes.byref(nc), ctypes.byref(info))
+        if st != 8:
+            self._n.pop(rid, None)
+        self.ctx.check(st)
+        return self._result(rid, labels, nc, info)
+
+    def cancel(self, rid: int) -> None:
+        self.ctx.check(self.ctx._lib.qc_server_cancel(self.handle, rid))
+
+    def stats(self) -> dict:
+        s = native.qc_server_stats()
+        self.ctx.check(self.ctx._lib.qc_server_get_stats(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            self.ctx._lib.qc_server_destroy(self.handle)
+            self.handle = None
+            self.ctx.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

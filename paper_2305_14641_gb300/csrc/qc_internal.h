@@ -184,6 +184,17 @@ qc_status qc_descend(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32
                      const double *V, int32_t n_sigma, int32_t *labels, int32_t *n_roots_dev,
                      cudaStream_t stream);
 
+// batch.cu: the graph-per-CTA kernel without a plan (used by the serving loop)
+struct qc_cta_launch;
+int32_t qc_cta_max_nodes();
+size_t qc_cta_bytes_per_node();
+qc_status qc_cta_launch_async(qc_ctx *ctx, int32_t m, qc_graph *const *graphs, const double *sigmas,
+                              int32_t *const *labels, cudaStream_t stream, qc_cta_launch **out);
+// counts: device int32[m]; flags: device int32[m + 1] (see batch.cu)
+int32_t *qc_cta_counts(qc_cta_launch *L);
+int32_t *qc_cta_flags(qc_cta_launch *L);
+void qc_cta_launch_free(qc_cta_launch *L);
+
 // validate.cu
 qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
                           const int32_t *col_idx_dev, cudaStream_t stream);

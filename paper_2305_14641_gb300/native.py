@@ -27,15 +27,22 @@ class qc_allocator(ctypes.Structure):
 
 
 class qc_server_config(ctypes.Structure):
-    _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int32)]
+    _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int32),
+                ("streams", ctypes.c_int32)]
 
 
 class qc_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("cancelled", ctypes.c_uint64), ("failed", ctypes.c_uint64),
-                ("steps", ctypes.c_uint64), ("bytes_resident", ctypes.c_size_t),
-                ("peak_bytes_resident", ctypes.c_size_t), ("active", ctypes.c_int32),
-                ("queued", ctypes.c_int32)]
+                ("steps", ctypes.c_uint64), ("large_solved", ctypes.c_uint64),
+                ("bytes_resident", ctypes.c_size_t), ("peak_bytes_resident", ctypes.c_size_t),
+                ("active", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("peak_in_flight", ctypes.c_int32)]
+
+
+class qc_request_info(ctypes.Structure):
+    _fields_ = [("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double), ("n", ctypes.c_int32),
+                ("nnz", ctypes.c_int64), ("batch_size", ctypes.c_int32)]
 
 
 class qc_kernel_stats(ctypes.Structure):
@@ -83,9 +90,9 @@ SIGNATURES = [
     ("qc_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]),
     ("qc_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, c_int32_p,
-                                      ctypes.POINTER(ctypes.c_int)]),
+                                      ctypes.POINTER(qc_request_info), ctypes.POINTER(ctypes.c_int)]),
     ("qc_server_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
-                                      c_int32_p]),
+                                      c_int32_p, ctypes.POINTER(qc_request_info)]),
     ("qc_server_cancel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     ("qc_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qc_server_stats)]),
     ("qc_server_destroy", None, [ctypes.c_void_p]),
@@ -104,9 +111,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         raise OSError(f"{path} is not built: run __graft_entry__.build() (needs nvcc)")
     lib = ctypes.CDLL(path)
     for name, res, args in SIGNATURES:
-        fn = getattr(lib, name, None)
-        if fn is None:
-            continue
+        fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
     return lib

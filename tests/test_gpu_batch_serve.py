@@ -1,0 +1,132 @@
+"""Batched and served forms against the oracle (needs a GPU).
+
+Every graph of a batch, and every served request, must give exactly the
+oracle's labels and cluster count; a served request must give the same labels
+alone and in a mix.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def qc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_14641_gb300 as qc
+    return qc
+
+
+@pytest.fixture(scope="module")
+def ctx(qc):
+    c = qc.Context(0)
+    yield c
+    c.close()
+
+
+def edge_cases():
+    one = gg.Graph(1, np.array([0, 0], np.int32), np.zeros(0, np.int32), name="one")
+    empty = gg.Graph(50, np.zeros(51, np.int32), np.zeros(0, np.int32), name="empty")
+    return [one, empty, gg.path(2), gg.complete(65), gg.star(130, 64), gg.two_cliques_bridge(40),
+            gg.erdos_renyi(700, 0.003, gg.rng(41))]
+
+
+def check_batch(qc, ctx, graphs, sigmas, runs=2):
+    Gs = [qc.Graph.from_graph(ctx, g) for g in graphs]
+    plan = qc.BatchPlan(ctx, Gs, sigmas)
+    for _ in range(runs):
+        plan.labels.fill_(-1)
+        counts = plan.run()
+        for k, (g, s) in enumerate(zip(graphs, sigmas)):
+            ref = oracle.solve(g, [s])
+            got = plan.labels_of(k).cpu().numpy()
+            assert np.array_equal(got, ref.labels[0]), (g.name, s)
+            assert counts[k] == ref.n_clusters[0], g.name
+    plan.close()
+    for G in Gs:
+        G.close()
+
+
+def test_batch_planted(qc, ctx):
+    graphs, sigmas = gg.config4_batch(160)
+    check_batch(qc, ctx, graphs, sigmas)
+
+
+def test_batch_edge_cases_and_deep_graph(qc, ctx):
+    """Single nodes, no edges, cliques, a path too deep for the batched kernel's
+    histogram (finished by the single-graph path) and a graph above the CTA limit."""
+    graphs = edge_cases() + [gg.path(300), gg.planted_partition(9000, 12, 0.01, 0.0004, gg.rng(42))]
+    sigmas = [0.5 + 0.25 * k for k in range(len(graphs))]
+    check_batch(qc, ctx, graphs, sigmas, runs=1)
+
+
+def test_solve_batch_one_shot(qc, ctx):
+    graphs, sigmas = gg.config4_batch(20, seed=9)
+    Gs = [qc.Graph.from_graph(ctx, g) for g in graphs]
+    labels, offsets = qc.solve_batch(ctx, Gs, sigmas)
+    lab = labels.cpu().numpy()
+    for k, g in enumerate(graphs):
+        ref = oracle.solve(g, [sigmas[k]])
+        assert np.array_equal(lab[offsets[k]:offsets[k] + g.n], ref.labels[0])
+
+
+def serve_requests(count, seed=4):
+    reqs = gg.config5_requests(count, seed=seed, n_max=12000)
+    return [(r.graph(), r.sigma) for r in reqs]
+
+
+def test_server_mixed_equals_alone_and_oracle(qc):
+    reqs = serve_requests(40)
+    with qc.Server(0, streams=3) as srv:
+        ids = [srv.submit(g.row_ptr, g.col_idx, s) for g, s in reqs]
+        mixed = [srv.wait(i, timeout_ms=120000) for i in ids]
+        alone = []
+        for g, s in reqs[:12]:
+            alone.append(srv.wait(srv.submit(g.row_ptr, g.col_idx, s), timeout_ms=120000))
+        st = srv.stats()
+    for (g, s), res in zip(reqs, mixed):
+        ref = oracle.solve(g, [s])
+        assert np.array_equal(res["labels"], ref.labels[0]), g.name
+        assert res["n_clusters"] == ref.n_clusters[0]
+        assert res["latency_ms"] >= res["admit_ms"] >= 0
+    for a, m in zip(alone, mixed):
+        assert np.array_equal(a["labels"], m["labels"])
+    assert st["completed"] == 52 and st["failed"] == 0
+    assert st["large_solved"] >= 1            # requests above the CTA limit took the worker
+
+
+def test_server_budget_and_cancel(qc):
+    g = gg.planted_partition(12000, 6, 0.002, 0.0001, gg.rng(43))
+    with qc.Server(0, mem_budget_bytes=1 << 20) as srv:
+        with pytest.raises(qc.QCError) as e:
+            srv.submit(g.row_ptr, g.col_idx, 1.0)           # alone exceeds the budget
+        assert e.value.status_name == "QC_ERR_BUDGET"
+        small = [gg.erdos_renyi(200, 0.03, gg.rng(44, k)) for k in range(30)]
+        ids = [srv.submit(x.row_ptr, x.col_idx, 1.2) for x in small]
+        srv.cancel(ids[-1])
+        results = []
+        for i in ids[:-1]:
+            results.append(srv.wait(i, timeout_ms=60000))
+        with pytest.raises(qc.QCError) as e:
+            srv.wait(ids[-1], timeout_ms=60000)
+        assert e.value.status_name == "QC_ERR_CANCELLED"
+        st = srv.stats()
+        assert st["peak_bytes_resident"] <= 1 << 20
+    for x, res in zip(small, results):
+        assert np.array_equal(res["labels"], oracle.solve(x, [1.2]).labels[0])
+
+
+def test_server_rejects_invalid(qc):
+    with qc.Server(0) as srv:
+        with pytest.raises(qc.QCError) as e:
+            srv.submit(np.array([0, 1, 1], np.int32), np.array([1], np.int32), 1.0)
+        assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
+        with pytest.raises(qc.QCError) as e:
+            srv.submit(np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), -1.0)
+        assert e.value.status_name == "QC_ERR_INVALID_ARG"
