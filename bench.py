@@ -318,6 +318,134 @@ def bench_ours(args, graph, sigmas):
         torch.distributed.destroy_process_group()
 
 
+BATCH_WORKLOAD = ("batch4096: 4096 planted-partition graphs, N log-uniform in [32, 2048], 2-16 blocks, "
+                  "p_in U(0.1, 0.5), p_out 0.02, sigma U(0.5, 3.0), seed 3; one persistent launch under a "
+                  "captured CUDA graph")
+SERVE_WORKLOAD = ("serve: Poisson arrivals at 200 requests/s of SBM graphs, N log-uniform in [64, 65536], "
+                  "mean degree 12, 4-64 blocks, mixing 0.1, sigma U(0.5, 3.0), seed 4, 100 GB admission budget")
+
+
+def bench_batch(args):
+    """Batched plan vs the plain form (one graph at a time through qc_solve)."""
+    import torch
+    import paper_2305_14641_gb300 as qc
+    graphs, sigmas = gg.config4_batch(args.batch_graphs)
+    ctx = qc.Context(0)
+    Gs = [qc.Graph.from_graph(ctx, g, validate=False) for g in graphs]
+    t0 = time.perf_counter()
+    plan = qc.BatchPlan(ctx, Gs, sigmas)
+    plan_s = time.perf_counter() - t0
+    for _ in range(max(args.warmup, 3)):
+        plan.run(counts=False)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    times = []
+    with ClockSampler(0) as clocks:
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.run(counts=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    batched = len(graphs) * args.steps / (sum(times) / 1000.0)
+    # plain form: every graph through the single-graph path, one after another
+    m = min(len(graphs), args.plain_graphs)
+    for G, s in zip(Gs[:8], sigmas[:8]):
+        G.solve([s], counts=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for G, s in zip(Gs[:m], sigmas[:m]):
+        G.drop_histogram()
+        G.solve([s], counts=False)
+    torch.cuda.synchronize()
+    plain = m / (time.perf_counter() - t0)
+    line = {"metric": "clusterings/s", "workload": BATCH_WORKLOAD, "graphs": len(graphs),
+            "nodes": int(sum(g.n for g in graphs)), "directed_edges": int(sum(g.nnz for g in graphs)),
+            "batched": batched, "ms_per_batch": sum(times) / len(times), "plain": plain,
+            "plain_sample_graphs": m, "batched_over_plain": batched / plain, "plan_seconds": plan_s,
+            "steps": args.steps, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def bench_serve(args):
+    """Open-loop Poisson stream through the server (p50/p99 latency), closed-loop
+    throughput, and the same requests solved serially with the plain form."""
+    import threading as th
+    import torch
+    import paper_2305_14641_gb300 as qc
+    reqs = gg.config5_requests(args.requests)
+    graphs = [r.graph() for r in reqs]
+    lat, results = {}, {}
+    with qc.Server(0, large_workers=args.large_workers, large_sm_share=args.large_sm_share) as srv:
+        # warm up: a few requests of each kind
+        for g, r in list(zip(graphs, reqs))[:8]:
+            srv.wait(srv.submit(g.row_ptr, g.col_idx, r.sigma))
+        t_start = time.perf_counter()
+        ids = []
+
+        def collector():
+            for i in range(len(reqs)):
+                while len(ids) <= i:
+                    time.sleep(0.0005)
+                res = srv.wait(ids[i])
+                lat[i] = res["latency_ms"]
+                results[i] = (res["n_clusters"], res["admit_ms"], res["batch_size"])
+
+        col = th.Thread(target=collector)
+        col.start()
+        with ClockSampler(0) as clocks:
+            for i, (g, r) in enumerate(zip(graphs, reqs)):
+                delay = r.arrival_s - (time.perf_counter() - t_start)
+                if delay > 0:
+                    time.sleep(delay)
+                ids.append(srv.submit(g.row_ptr, g.col_idx, r.sigma))
+            col.join()
+        open_wall = time.perf_counter() - t_start
+        st_open = srv.stats()
+        # closed loop: everything submitted at once
+        t0 = time.perf_counter()
+        cids = [srv.submit(g.row_ptr, g.col_idx, r.sigma) for g, r in zip(graphs, reqs)]
+        for i in cids:
+            srv.wait(i)
+        closed = len(reqs) / (time.perf_counter() - t0)
+    # serial plain solves of the same requests (FIFO), device-resident after upload
+    ctx = qc.Context(0)
+    t0 = time.perf_counter()
+    service = []
+    for g, r in zip(graphs, reqs):
+        s0 = time.perf_counter()
+        G = qc.Graph.from_graph(ctx, g)
+        G.solve([r.sigma], counts=True)
+        G.close()
+        service.append(time.perf_counter() - s0)
+    serial = len(reqs) / (time.perf_counter() - t0)
+    # latency of the serial plain form under the same arrivals (FIFO queue simulation)
+    free_at, serial_lat = 0.0, []
+    for r, sv in zip(reqs, service):
+        start = max(r.arrival_s, free_at)
+        free_at = start + sv
+        serial_lat.append(1000.0 * (free_at - r.arrival_s))
+    L = np.array([lat[i] for i in range(len(reqs))])
+    line = {"metric": "clusterings/s", "workload": SERVE_WORKLOAD, "requests": len(reqs),
+            "large_workers": args.large_workers, "large_sm_share": args.large_sm_share,
+            "served_open_loop_per_s": len(reqs) / open_wall,
+            "p50_ms": float(np.percentile(L, 50)), "p99_ms": float(np.percentile(L, 99)),
+            "served_closed_loop_per_s": closed, "serial_plain_per_s": serial,
+            "served_over_serial_plain": closed / serial,
+            "serial_plain_p50_ms": float(np.percentile(serial_lat, 50)),
+            "serial_plain_p99_ms": float(np.percentile(serial_lat, 99)),
+            "server_stats": {k: int(v) for k, v in st_open.items()}, "clocks": clocks.summary(),
+            "slowest": [{"n": reqs[i].n, "latency_ms": round(float(L[i]), 3),
+                         "admit_ms": round(results[i][1], 3), "batch_size": results[i][2],
+                         "serial_service_ms": round(1000 * service[i], 3)}
+                        for i in np.argsort(-L)[:12]]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -325,7 +453,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["dcsbm16384", "batch4096", "serve"], default="dcsbm16384")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--plain-graphs", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--large-workers", type=int, default=4)
+    ap.add_argument("--large-sm-share", type=float, default=0.4)
     args = ap.parse_args()
+    if args.workload == "batch4096":
+        return bench_batch(args)
+    if args.workload == "serve":
+        return bench_serve(args)
     graph, sigmas = gg.config2()
     if args.impl == "reference":
         bench_reference(args, graph, sigmas)

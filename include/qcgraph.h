@@ -196,6 +196,10 @@ typedef struct {
                                   or 100 GB if the context has none) */
     int32_t max_active;        /* most requests on the GPU at once (0 = 256) */
     int32_t streams;           /* batched launches in flight at once (0 = 4) */
+    int32_t large_workers;     /* threads running the single-graph path (0 = 4) */
+    float large_sm_share;      /* share of the SMs the single-graph path's persistent
+                                  kernels may fill, leaving the rest to batched launches
+                                  (0 = 0.4); applies to the whole context */
 } qc_server_config;
 
 typedef struct {
@@ -219,19 +223,24 @@ typedef struct {
 
 /* A serving loop on its own host threads: submitted requests wait in FIFO
  * order until their memory estimate fits the budget and a slot is free.
- * Admitted requests up to qc's graph-per-CTA limit (8192 nodes) are grouped
+ * Admitted requests up to the graph-per-CTA limit (2048 nodes) are grouped
  * into one launch of the batched kernel per scheduler step; several such
  * launches run at once on separate streams, so requests that arrive while
  * others are on the GPU start without waiting for them (continuous batching).
- * Larger requests go to a worker thread that runs the single-graph path.
+ * Larger requests go to worker threads that run the single-graph path on
+ * low-priority streams, their persistent kernels limited to a share of the SMs
+ * so that batched launches keep running beside them.
  * A request's result does not depend on what it shares the GPU with.
  * cfg may be NULL for defaults. */
 qc_status qc_server_create(qc_ctx *ctx, const qc_server_config *cfg, qc_server **out);
 /* Queue one request: a host CSR (copied before the call returns; same layout
- * and validation as qc_graph_create with QC_VALIDATE) and its sigma.
+ * and checks as qc_graph_create with QC_VALIDATE) and its sigma.
  * req_id: host, receives the request id.
  * Errors: QC_ERR_INVALID_ARG, QC_ERR_INVALID_GRAPH, QC_ERR_BUDGET (the request
- * alone exceeds the budget). */
+ * alone exceeds the budget).  The full CSR check runs here for graphs of up to
+ * 2048 nodes; larger graphs get row_ptr checked here and the rest checked on
+ * the GPU when they are admitted, in which case an invalid graph is reported
+ * as the request's own status (QC_ERR_INVALID_GRAPH from poll / wait). */
 qc_status qc_server_submit(qc_server *s, int32_t n, int64_t nnz, const int32_t *row_ptr,
                            const int32_t *col_idx, double sigma, uint64_t *req_id);
 /* Non-blocking: *done = 1 and labels_out (host int32[n], root node ids),

@@ -261,9 +261,10 @@ class Server:
     allocator so that the library's threads never call back into Python."""
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 100 << 30, max_active: int = 256,
-                 streams: int = 4):
+                 streams: int = 4, large_workers: int = 4, large_sm_share: float = 0.4):
         self.ctx = Context(device, allocator="cuda")
-        cfg = native.qc_server_config(int(mem_budget_bytes), int(max_active), int(streams))
+        cfg = native.qc_server_config(int(mem_budget_bytes), int(max_active), int(streams),
+                                      int(large_workers), float(large_sm_share))
         h = ctypes.c_void_p()
         self.ctx.check(self.ctx._lib.qc_server_create(self.ctx.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h

@@ -38,7 +38,11 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint64_t ONES = ~0ull;
 constexpr int MAXC = 8;            // most source words per chunk (held per lane in registers)
 constexpr int L_CAP = 32;          // histogram rows per graph in the batched kernel
-constexpr int CTA_MAX_N = 8192;    // larger graphs take the single-graph path
+constexpr int SPARSE_DEGREE = 24;  // below this mean degree a thread, not a warp, takes a node
+// Larger graphs take the single-graph path: one CTA walks all n/64 source words
+// of its graph, so its time grows as n^2 x degree while the multi-CTA path
+// spreads a large graph over the whole GPU.
+constexpr int CTA_MAX_N = 2048;
 
 struct CtaGraph {
     const int32_t *row_ptr;
@@ -141,6 +145,7 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
     __syncthreads();
 
     // 2. BFS, chunk by chunk
+    const bool sparse = rp[n] < SPARSE_DEGREE * n;   // short rows: a thread per node
     int rows_ready = 2;       // hist rows zeroed / written so far
     int D = (rp[n] > 0) ? 1 : 0;
     bool overflow = false;
@@ -175,6 +180,40 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
             const uint64_t *in = (level & 1) ? colB : colA;
             uint64_t *out = (level & 1) ? colA : colB;
             bool any_new = false;
+            if (sparse) {
+                // one thread per node: no cross-lane reductions for short rows
+                for (int v = tid; v < n; v += nthr) {
+                    uint64_t own[MAXC], acc[MAXC];
+                    bool full = true;
+#pragma unroll
+                    for (int k = 0; k < MAXC; ++k) {
+                        own[k] = (k < cw) ? in[(size_t)v * P.c + k] : ONES;
+                        acc[k] = 0ull;
+                        full = full && own[k] == ONES;
+                    }
+                    if (!full) {
+                        for (int e = rp[v]; e < rp[v + 1]; ++e) {
+                            const uint64_t *nrow = in + (size_t)ci[e] * P.c;
+#pragma unroll
+                            for (int k = 0; k < MAXC; ++k)
+                                if (k < cw) acc[k] |= nrow[k];
+                        }
+                    }
+                    int cnt = 0;
+#pragma unroll
+                    for (int k = 0; k < MAXC; ++k) {
+                        if (k < cw) {
+                            const uint64_t nwd = acc[k] & ~own[k];
+                            out[(size_t)v * P.c + k] = own[k] | nwd;
+                            cnt += __popcll(nwd);
+                        }
+                    }
+                    if (cnt) {
+                        hist[(size_t)level * n + v] += cnt;
+                        any_new = true;
+                    }
+                }
+            } else
             for (int v = wid; v < n; v += nw) {
                 uint64_t own[MAXC], acc[MAXC];
                 bool full = true;
@@ -242,6 +281,21 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
     }
     __syncthreads();
     // 4. descent and roots
+    if (sparse) {
+        for (int v = tid; v < n; v += nthr) {
+            long long bk = 0;
+            int best = -1;
+            for (int e = rp[v]; e < rp[v + 1]; ++e) {
+                const int x = ci[e];
+                const long long k = key[x];
+                if (best < 0 || k < bk || (k == bk && x < best)) {
+                    bk = k;
+                    best = x;
+                }
+            }
+            parent[v] = (best >= 0 && bk < key[v]) ? best : v;
+        }
+    } else
     for (int v = wid; v < n; v += nw) {
         long long bk = 0;
         int best = -1;
@@ -377,9 +431,10 @@ size_t qc_cta_bytes_per_node() { return sizeof(int32_t) * L_CAP; }
 // `stream`.  labels[i]: device int32[n_i].  The returned record owns the
 // launch's device buffers; keep it until the stream has passed the launch.
 // Per graph, counts[i] and flags[i] (1 = needs the single-graph path) are in
-// L->counts / L->flags.
+// L->counts / L->flags.  max_sms caps the SMs' worth of CTAs the launch may
+// fill (0 = all).
 qc_status qc_cta_launch_async(qc_ctx *ctx, int32_t m, qc_graph *const *graphs, const double *sigmas,
-                              int32_t *const *labels, cudaStream_t stream, qc_cta_launch **out) {
+                              int32_t *const *labels, int max_sms, cudaStream_t stream, qc_cta_launch **out) {
     auto *L = new qc_cta_launch();
     std::unique_ptr<qc_cta_launch> guard(L);
     L->m = m;
@@ -408,7 +463,8 @@ qc_status qc_cta_launch_async(qc_ctx *ctx, int32_t m, qc_graph *const *graphs, c
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)batch_kernel, 256, smem));
-    int grid = std::max(1, std::min(per_sm * ctx->num_sms, m));
+    const int sms = (max_sms > 0 && max_sms < ctx->num_sms) ? max_sms : ctx->num_sms;
+    int grid = std::max(1, std::min(per_sm * sms, m));
     QC_TRY(L->descs.allocate(ctx, sizeof(CtaGraph) * m, stream));
     QC_TRY(L->tables.allocate(ctx, sizeof(double) * tab.size(), stream));
     QC_TRY(L->order.allocate(ctx, sizeof(int32_t) * m, stream));

@@ -498,7 +498,7 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
             return QC_ERR_CUDA;
         }
         const int items = n * T;
-        int blocks = per_sm * ctx->num_sms;
+        int blocks = per_sm * qc_coop_sms(ctx);
         if (blocks > qc_ceil_div(items, 8)) blocks = qc_ceil_div(items, 8);
         if (blocks < 1) blocks = 1;
         int32_t start = 2;

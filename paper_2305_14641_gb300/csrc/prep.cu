@@ -165,7 +165,7 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
         int per_sm = 0;
         QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)cc_persistent,
                                                                        256, 0));
-        int blocks = per_sm * ctx->num_sms;
+        int blocks = per_sm * qc_coop_sms(ctx);
         if (blocks > wb) blocks = wb;
         if (blocks < 1) blocks = 1;
         qc_buffer ctl;

@@ -45,6 +45,7 @@ struct qc_ctx {
     std::map<std::string, qc_kernel_stats> stats;
     std::mutex pinned_mu;
     std::vector<void *> pinned_free;       // 64 KiB pinned host blocks ready for reuse
+    std::atomic<float> coop_sm_share{1.0f};  // share of SMs the cooperative kernels fill
     ~qc_ctx();
 };
 
@@ -189,7 +190,7 @@ struct qc_cta_launch;
 int32_t qc_cta_max_nodes();
 size_t qc_cta_bytes_per_node();
 qc_status qc_cta_launch_async(qc_ctx *ctx, int32_t m, qc_graph *const *graphs, const double *sigmas,
-                              int32_t *const *labels, cudaStream_t stream, qc_cta_launch **out);
+                              int32_t *const *labels, int max_sms, cudaStream_t stream, qc_cta_launch **out);
 // counts: device int32[m]; flags: device int32[m + 1] (see batch.cu)
 int32_t *qc_cta_counts(qc_cta_launch *L);
 int32_t *qc_cta_flags(qc_cta_launch *L);
@@ -202,3 +203,9 @@ qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *ro
 static inline cudaStream_t qc_stream(void *s) { return static_cast<cudaStream_t>(s); }
 
 static inline int qc_ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// SMs' worth of blocks a cooperative (persistent) kernel may fill.
+static inline int qc_coop_sms(const qc_ctx *ctx) {
+    const int s = (int)(ctx->coop_sm_share.load() * (float)ctx->num_sms);
+    return s < 1 ? 1 : (s > ctx->num_sms ? ctx->num_sms : s);
+}

@@ -4,18 +4,23 @@
 // Threads:
 //   scheduler  admits queued requests in FIFO order while their byte estimate
 //              fits the budget and fewer than max_active are on the GPU; groups
-//              the admitted requests that fit a CTA (n <= 8192) into one launch
+//              the admitted requests that fit a CTA (n <= 2048) into one launch
 //              of the batched graph-per-CTA kernel on a free stream slot (up to
 //              `streams` launches in flight, so newly arrived requests start
 //              while earlier ones are still running: continuous batching); a
 //              host callback on the stream wakes it when a launch has finished,
 //              and it hands the results out;
-//   large      runs the single-graph path for larger requests (and for any
-//              request whose BFS needed more histogram rows than the batched
-//              kernel keeps), one at a time on its own stream.
+//   large      worker threads (four by default) run the single-graph path for
+//              larger requests (and for any request whose BFS needed more
+//              histogram rows than the batched kernel keeps), one request at a
+//              time each, on low-priority streams; their persistent kernels
+//              fill only a share of the SMs (40% each by default) so that batched
+//              launches of small requests, on high-priority streams, keep
+//              running beside a large request instead of waiting for it.
 // Every request gets its own device copy of its CSR and its own label buffer,
 // and every kernel that touches it reads only that request's data, so a result
 // does not depend on which other requests shared the launch or the GPU.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -105,8 +110,9 @@ struct qc_server {
     int32_t active = 0;
     int32_t in_flight = 0;
     qc_server_stats st{};
-    std::thread sched, large;
-    cudaStream_t large_stream = nullptr;
+    std::thread sched;
+    std::vector<std::thread> large;
+    std::vector<cudaStream_t> large_streams;
 
     size_t estimate(int32_t n, int64_t nnz, bool is_large) const {
         const size_t csr = 4 * ((size_t)n + 1) + 4 * (size_t)nnz;
@@ -172,8 +178,11 @@ struct qc_server {
             QC_CUDA_TRY(ctx, cudaMallocHost(&s.pinned, sizeof(int32_t) * need * 2));
             s.pinned_ints = need * 2;
         }
-        QC_TRY(qc_cta_launch_async(ctx, (int32_t)rs.size(), graphs.data(), sig.data(), lab.data(), s.stream,
-                                   &s.launch));
+        // the SMs the large requests' persistent kernels leave free, split among the slots
+        const int spare = ctx->num_sms - qc_coop_sms(ctx);
+        const int max_sms = spare > 0 ? std::max(1, spare / (int)slots.size()) : 0;
+        QC_TRY(qc_cta_launch_async(ctx, (int32_t)rs.size(), graphs.data(), sig.data(), lab.data(), max_sms,
+                                   s.stream, &s.launch));
         for (size_t i = 0; i < rs.size(); ++i)
             QC_CUDA_TRY(ctx, cudaMemcpyAsync(s.pinned + s.offs[i], lab[i], sizeof(int32_t) * rs[i]->n,
                                              cudaMemcpyDeviceToHost, s.stream));
@@ -286,7 +295,8 @@ struct qc_server {
         }
     }
 
-    void large_worker() {
+    void large_worker(int idx) {
+        cudaStream_t large_stream = large_streams[idx];
         cudaSetDevice(ctx->device);
         std::unique_lock<std::mutex> lk(mu);
         while (true) {
@@ -307,8 +317,9 @@ struct qc_server {
                 qc_graph_destroy(r->g);
                 r->g = nullptr;
             }
-            status = qc_graph_create(ctx, r->n, r->nnz, r->rp.data(), r->nnz ? r->ci.data() : nullptr, 0,
-                                     large_stream, &r->g);
+            // large requests are validated here, on the device (see qc_server_submit)
+            status = qc_graph_create(ctx, r->n, r->nnz, r->rp.data(), r->nnz ? r->ci.data() : nullptr,
+                                     QC_VALIDATE, large_stream, &r->g);
             if (status == QC_OK && !r->labels_dev.ptr)
                 status = r->labels_dev.allocate(ctx, sizeof(int32_t) * (size_t)r->n, large_stream);
             int32_t nc = 0;
@@ -360,13 +371,27 @@ qc_status qc_server_create(qc_ctx *ctx, const qc_server_config *cfg, qc_server *
                                                : (ctx->budget ? ctx->budget : (size_t)100 << 30);
     s->max_active = (cfg && cfg->max_active > 0) ? cfg->max_active : 256;
     const int ns = (cfg && cfg->streams > 0) ? cfg->streams : 4;
+    // defaults from measurement on the Poisson mix of 64..65536-node graphs: four
+    // workers at 40% of the SMs each beat one worker on the whole GPU (a large
+    // request is bound by its per-level steps, not by SMs)
+    const int nl = (cfg && cfg->large_workers > 0) ? cfg->large_workers : 4;
+    const float share = (cfg && cfg->large_sm_share > 0.f && cfg->large_sm_share <= 1.f) ? cfg->large_sm_share
+                                                                                          : 0.4f;
+    ctx->coop_sm_share = share;
     QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    // batched launches of small requests first: highest stream priority
+    int prio_low = 0, prio_high = 0;
+    QC_CUDA_TRY(ctx, cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
     s->slots.resize(ns);
-    for (Slot &sl : s->slots) QC_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
-    QC_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&s->large_stream, cudaStreamNonBlocking));
+    for (Slot &sl : s->slots)
+        QC_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, prio_high));
+    s->large_streams.resize(nl);
+    for (cudaStream_t &ls : s->large_streams)
+        QC_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&ls, cudaStreamNonBlocking, prio_low));
     qc_server *raw = s.get();
     s->sched = std::thread([raw] { raw->scheduler(); });
-    s->large = std::thread([raw] { raw->large_worker(); });
+    for (int i = 0; i < (int)s->large_streams.size(); ++i)
+        s->large.emplace_back([raw, i] { raw->large_worker(i); });
     *out = s.release();
     return QC_OK;
 }
@@ -376,7 +401,12 @@ qc_status qc_server_submit(qc_server *s, int32_t n, int64_t nnz, const int32_t *
     if (!s || !req_id || n < 1 || nnz < 0 || nnz >= (int64_t(1) << 31) || !row_ptr || (nnz > 0 && !col_idx) ||
         !qc_sigma_ok(sigma))
         return QC_ERR_INVALID_ARG;
-    QC_TRY(validate_host_csr(n, nnz, row_ptr, col_idx));
+    // row_ptr on the host always; the whole CSR on the host for requests the
+    // batched kernel takes, on the device (by the worker) for the others
+    if (row_ptr[0] != 0 || row_ptr[n] != nnz) return QC_ERR_INVALID_GRAPH;
+    for (int32_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] < row_ptr[v]) return QC_ERR_INVALID_GRAPH;
+    if (n <= qc_cta_max_nodes()) QC_TRY(validate_host_csr(n, nnz, row_ptr, col_idx));
     auto r = std::make_unique<Req>();
     r->n = n;
     r->nnz = nnz;
@@ -465,7 +495,8 @@ void qc_server_destroy(qc_server *s) {
         s->cv_large.notify_all();
     }
     if (s->sched.joinable()) s->sched.join();
-    if (s->large.joinable()) s->large.join();
+    for (std::thread &t : s->large)
+        if (t.joinable()) t.join();
     for (Slot &sl : s->slots) {
         if (sl.stream) {
             cudaStreamSynchronize(sl.stream);
@@ -474,7 +505,8 @@ void qc_server_destroy(qc_server *s) {
         if (sl.launch) qc_cta_launch_free(sl.launch);
         if (sl.pinned) cudaFreeHost(sl.pinned);
     }
-    if (s->large_stream) cudaStreamDestroy(s->large_stream);
+    for (cudaStream_t ls : s->large_streams)
+        if (ls) cudaStreamDestroy(ls);
     for (auto &kv : s->reqs) {
         Req *r = kv.second.get();
         if (r->g) qc_graph_destroy(r->g);

@@ -28,7 +28,8 @@ class qc_allocator(ctypes.Structure):
 
 class qc_server_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int32),
-                ("streams", ctypes.c_int32)]
+                ("streams", ctypes.c_int32), ("large_workers", ctypes.c_int32),
+                ("large_sm_share", ctypes.c_float)]
 
 
 class qc_server_stats(ctypes.Structure):

@@ -123,7 +123,14 @@ def test_server_budget_and_cancel(qc):
 
 
 def test_server_rejects_invalid(qc):
+    big = gg.planted_partition(3000, 4, 0.005, 0.0005, gg.rng(45))
+    ci = big.col_idx.copy()
+    ci[10] = ci[11]                       # a duplicate edge in a large request: found on the GPU
     with qc.Server(0) as srv:
+        rid = srv.submit(big.row_ptr, ci, 1.0)
+        with pytest.raises(qc.QCError) as e:
+            srv.wait(rid, timeout_ms=60000)
+        assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
         with pytest.raises(qc.QCError) as e:
             srv.submit(np.array([0, 1, 1], np.int32), np.array([1], np.int32), 1.0)
         assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
