@@ -58,6 +58,7 @@ constexpr uint64_t ONES = ~0ull;
 constexpr int NOT_SAT = 0x7fffffff;
 constexpr int WARPS = 8;               // warps per block
 constexpr int GRAB = 4;                // light list positions taken per counter update
+constexpr int LIST_AFTER = 2;          // pull levels of a launch that scan every item
 using qcdev::ST_DONE;
 using qcdev::ST_NEED_ROWS;
 using qcdev::ST_TIMEOUT;
@@ -170,9 +171,11 @@ __device__ void init_bits(const BfsParams &p) {
 // OR of the rows of neighbours [j_first, end) of one node, taking 32-neighbour
 // chunks j_first, j_first + stride, ... (stride = 32 x the warps sharing the row).
 // Lane (slot, q) accumulates segment q; it stops once acc | own is all ones.
+// When `have0` is set, myu0 already holds the first chunk's ids (prefetched).
 template <int G>
 __device__ __forceinline__ ulonglong2 gather_or(const BfsParams &p, const ulonglong2 *vin, int j_first,
-                                                int end, int stride, int q, bool qok, ulonglong2 own) {
+                                                int end, int stride, int q, bool qok, ulonglong2 own,
+                                                bool have0 = false, int myu0 = 0) {
     constexpr int SLOTS = 32 / G;
     constexpr int U = G < 4 ? G : 4;
     const int lane = threadIdx.x & 31;
@@ -183,7 +186,7 @@ __device__ __forceinline__ ulonglong2 gather_or(const BfsParams &p, const ulongl
     for (int j0 = j_first; j0 < end; j0 += stride) {
         if (!__any_sync(FULL, act)) break;
         const int cnt = min(32, end - j0);
-        const int myu = (lane < cnt) ? p.col_idx[j0 + lane] : 0;
+        const int myu = (have0 && j0 == j_first) ? myu0 : ((lane < cnt) ? p.col_idx[j0 + lane] : 0);
         for (int m = 0; m < cnt; m += SLOTS * U) {
             ulonglong2 x[U];
 #pragma unroll
@@ -287,7 +290,7 @@ __device__ void heavy_items(const BfsParams &p, const int level, bool &any_new, 
 // launch lists every light item in order; later levels read the worklist.
 template <int G>
 __device__ __forceinline__ void light_items(const BfsParams &p, const int level, const bool from_list,
-                                            bool &any_new) {
+                                            const bool make_list, bool &any_new) {
     const int lane = threadIdx.x & 31;
     const int slot = lane / G;
     const int ql = lane % G;
@@ -327,20 +330,35 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
         }
         const unsigned pulls = __ballot_sync(FULL, pull);
         mask = pulls;
+        // item state; the next item's own segment and first neighbour ids are
+        // requested before the current item's gathers, so the two overlap
+        struct Item {
+            int v, t, sidx, beg, end, myu;
+            ulonglong2 own;
+        };
+        auto fetch = [&](int b, Item &x) {
+            x.v = __shfl_sync(FULL, v_l, b);
+            x.t = __shfl_sync(FULL, t_l, b);
+            x.sidx = __shfl_sync(FULL, it, b);
+            x.beg = __shfl_sync(FULL, beg_l, b);
+            x.end = __shfl_sync(FULL, end_l, b);
+            const int q = x.t * 32 + ql;
+            x.own = (q < p.R) ? vin[(size_t)x.v * p.R + q] : make_ulonglong2(ONES, ONES);
+            x.myu = (lane < x.end - x.beg) ? p.col_idx[x.beg + lane] : 0;
+        };
+        Item cur, nxt;
+        if (mask) fetch(__ffs(mask) - 1, cur);
         while (mask) {
-            const int b = __ffs(mask) - 1;
             mask &= mask - 1;
-            const int v = __shfl_sync(FULL, v_l, b);
-            const int t = __shfl_sync(FULL, t_l, b);
-            const int sidx = __shfl_sync(FULL, it, b);
-            const int q = t * 32 + ql;
+            if (mask) fetch(__ffs(mask) - 1, nxt);
+            const int q = cur.t * 32 + ql;
             const bool qok = q < p.R;
-            const ulonglong2 own = qok ? vin[(size_t)v * p.R + q] : make_ulonglong2(ONES, ONES);
-            const int beg = __shfl_sync(FULL, beg_l, b), end = __shfl_sync(FULL, end_l, b);
-            const ulonglong2 acc = gather_or<G>(p, vin, beg, end, 32, q, qok, own);
-            finish_item<G>(p, acc, own, vout + (size_t)v * p.R, q, qok, v, sidx, hrow, level, any_new);
+            const ulonglong2 acc = gather_or<G>(p, vin, cur.beg, cur.end, 32, q, qok, cur.own, true, cur.myu);
+            finish_item<G>(p, acc, cur.own, vout + (size_t)cur.v * p.R, q, qok, cur.v, cur.sidx, hrow, level,
+                           any_new);
+            cur = nxt;
         }
-        if (pulls) {
+        if (make_list && pulls) {
             int at = 0;
             if (lane == 0) at = atomicAdd(p.wl_count + level + 1, __popc(pulls));
             at = __shfl_sync(FULL, at, 0);
@@ -351,7 +369,7 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
 }
 
 template <int G>
-__global__ void __launch_bounds__(256) bfs_persistent(const BfsParams p) {
+__global__ void __launch_bounds__(256, G == 32 ? 1 : 4) bfs_persistent(const BfsParams p) {
     __shared__ ulonglong2 red[WARPS][32];
     int level = p.start_level;
     const bool stamp = p.stamp && blockIdx.x == 0 && threadIdx.x == 0;
@@ -373,7 +391,10 @@ __global__ void __launch_bounds__(256) bfs_persistent(const BfsParams p) {
         }
         bool any_new = false;
         if (G == 32) heavy_items(p, level, any_new, red);
-        light_items<G>(p, level, level > p.start_level, any_new);
+        // the first pull levels touch nearly every item: scan them all; from the
+        // third on, each level lists what it pulled for the next
+        light_items<G>(p, level, level >= p.start_level + LIST_AFTER + 1, level >= p.start_level + LIST_AFTER,
+                       any_new);
         if (__syncthreads_or(any_new) && threadIdx.x == 0) p.level_new[level] = 1;
         if (!grid_barrier(p.bar, p.status)) return;
         if (stamp) p.stamp[level + 1] = global_ns();

@@ -283,7 +283,8 @@ qc_status qc_ggd_labels(qc_graph *g, const double *V, int32_t n_sigma, int32_t *
     qc_buffer roots;
     QC_TRY(roots.allocate(ctx, sizeof(int32_t) * (size_t)n_sigma, stream));
     QC_CUDA_TRY(ctx, cudaMemsetAsync(roots.ptr, 0, roots.bytes, stream));
-    QC_TRY(qc_descend(ctx, g->n, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(), V, n_sigma,
+    QC_TRY(qc_descend(ctx, g->n, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(),
+                      g->prepared ? g->order.as<int32_t>() : nullptr, V, n_sigma,
                       labels_out, roots.as<int32_t>(), stream));
     if (n_clusters_out) {
         QC_CUDA_TRY(ctx, cudaMemcpyAsync(n_clusters_out, roots.ptr, roots.bytes,

@@ -54,57 +54,67 @@ __device__ __forceinline__ bool better(long long k, int u, long long bk, int bes
     return best < 0 || k < bk || (k == bk && u < best);
 }
 
-// Sigma values s0 .. s0 + sn - 1 (sn <= SB).
-template <int SB>
+// Sigma values s0 .. s0 + sn - 1 (sn <= SG).  Lane = (slot, sigma): SG lanes
+// per slot, one sigma each; the 32/SG slots take every (32/SG)-th neighbour.
+// Neighbour ids come 32 at a time from one coalesced load and are broadcast by
+// shuffle; each lane keeps U key loads in flight.  log2(32/SG) butterfly steps
+// combine the slots.  Nodes go in `order` (heaviest first) when given, so the
+// longest rows start first.
+template <int SG>
 __global__ void __launch_bounds__(256) ggd_parent_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
                                                          const int32_t *__restrict__ col_idx,
                                                          const long long *__restrict__ K, int32_t S,
                                                          int32_t s0, int32_t sn,
+                                                         const int32_t *__restrict__ order,
                                                          int32_t *__restrict__ parent) {
+    constexpr int SLOTS = 32 / SG;
+    constexpr int U = 8;
     const int lane = threadIdx.x & 31;
+    const int slot = lane / SG;
+    const int sl = lane % SG;
+    const bool sok = sl < sn;
+    const int s = s0 + sl;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int v = warp; v < n; v += nwarps) {
+    for (int i = warp; i < n; i += nwarps) {
+        const int v = order ? order[i] : i;
         const int beg = row_ptr[v], end = row_ptr[v + 1];
-        long long bk[SB];
-        int best[SB];
+        long long bk = 0;
+        int best = -1;
+        for (int j0 = beg; j0 < end; j0 += 32) {
+            const int cnt = min(32, end - j0);
+            const int myu = (lane < cnt) ? col_idx[j0 + lane] : 0;
+            for (int m = 0; m < cnt; m += SLOTS * U) {
+                long long x[U];
+                int uu[U];
 #pragma unroll
-        for (int k = 0; k < SB; ++k) {
-            bk[k] = 0;
-            best[k] = -1;
-        }
-        for (int j = beg + lane; j < end; j += 32) {
-            const int u = col_idx[j];
-            const long long *row = K + (size_t)u * S + s0;
+                for (int k = 0; k < U; ++k) {
+                    const int t = m + k * SLOTS + slot;
+                    uu[k] = __shfl_sync(FULL, myu, t & 31);
+                    x[k] = (sok && t < cnt) ? K[(size_t)uu[k] * S + s] : 0;
+                }
 #pragma unroll
-            for (int k = 0; k < SB; ++k) {
-                if (k < sn) {
-                    const long long x = row[k];
-                    if (better(x, u, bk[k], best[k])) {
-                        bk[k] = x;
-                        best[k] = u;
+                for (int k = 0; k < U; ++k) {
+                    const int t = m + k * SLOTS + slot;
+                    if (sok && t < cnt && better(x[k], uu[k], bk, best)) {
+                        bk = x[k];
+                        best = uu[k];
                     }
                 }
             }
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-            for (int k = 0; k < SB; ++k) {
-                const long long ok = __shfl_xor_sync(FULL, bk[k], off);
-                const int ob = __shfl_xor_sync(FULL, best[k], off);
-                if (ob >= 0 && better(ok, ob, bk[k], best[k])) {
-                    bk[k] = ok;
-                    best[k] = ob;
-                }
+        for (int off = SG; off < 32; off <<= 1) {
+            const long long ok = __shfl_xor_sync(FULL, bk, off);
+            const int ob = __shfl_xor_sync(FULL, best, off);
+            if (ob >= 0 && better(ok, ob, bk, best)) {
+                bk = ok;
+                best = ob;
             }
         }
-#pragma unroll
-        for (int k = 0; k < SB; ++k) {
-            if (lane == k && k < sn) {
-                const long long own = K[(size_t)v * S + s0 + k];
-                parent[(size_t)(s0 + k) * n + v] = (best[k] >= 0 && bk[k] < own) ? best[k] : v;
-            }
+        if (slot == 0 && sok) {
+            const long long own = K[(size_t)v * S + s];
+            parent[(size_t)s * n + v] = (best >= 0 && bk < own) ? best : v;
         }
     }
 }
@@ -131,7 +141,7 @@ __global__ void find_roots_kernel(int32_t n, int32_t *parent, int32_t *__restric
 }
 
 typedef void (*parent_fn)(int32_t, const int32_t *, const int32_t *, const long long *, int32_t,
-                          int32_t, int32_t, int32_t *);
+                          int32_t, int32_t, const int32_t *, int32_t *);
 
 parent_fn pick_parent(int sn) {
     if (sn <= 1) return ggd_parent_kernel<1>;
@@ -144,8 +154,8 @@ parent_fn pick_parent(int sn) {
 }  // namespace
 
 qc_status qc_descend(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
-                     const double *V, int32_t n_sigma, int32_t *labels, int32_t *n_roots_dev,
-                     cudaStream_t stream) {
+                     const int32_t *order, const double *V, int32_t n_sigma, int32_t *labels,
+                     int32_t *n_roots_dev, cudaStream_t stream) {
     qc_buffer parent, keys;
     QC_TRY(parent.allocate(ctx, sizeof(int32_t) * (size_t)n * (size_t)n_sigma, stream));
     QC_TRY(keys.allocate(ctx, sizeof(long long) * (size_t)n * (size_t)n_sigma, stream));
@@ -156,7 +166,7 @@ qc_status qc_descend(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32
     for (int32_t s0 = 0; s0 < n_sigma; s0 += 16) {
         const int32_t sn = (n_sigma - s0) < 16 ? (n_sigma - s0) : 16;
         pick_parent(sn)<<<wblocks, 256, 0, stream>>>(n, row_ptr, col_idx, keys.as<long long>(), n_sigma,
-                                                     s0, sn, parent.as<int32_t>());
+                                                     s0, sn, order, parent.as<int32_t>());
         QC_LAUNCHED(ctx);
     }
     const int blocks = qc_ceil_div(n, 256) < 2 * ctx->num_sms ? qc_ceil_div(n, 256) : 2 * ctx->num_sms;

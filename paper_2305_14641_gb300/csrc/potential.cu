@@ -45,6 +45,32 @@ __global__ void potential_kernel(int32_t n, int32_t D, const int32_t *__restrict
     }
 }
 
+// Small tables travel as a kernel parameter (no copy, no synchronisation).
+constexpr int INLINE_DOUBLES = 448;
+struct InlineTables {
+    double t[INLINE_DOUBLES];      // w[s][d], then u[s][d], then den[s]
+};
+
+__global__ void potential_kernel_inline(int32_t n, int32_t D, int32_t S, const int32_t *__restrict__ hist,
+                                        const __grid_constant__ InlineTables tab, double *__restrict__ V) {
+    const int s = blockIdx.y;
+    const int L = D + 1;
+    const double *ws = tab.t + s * L;
+    const double *us = tab.t + S * L + s * L;
+    const double den = tab.t[2 * S * L + s];
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        double sum1 = 0.0, sum2 = 0.0;
+        for (int d = 0; d <= D; ++d) {
+            const int c = hist[(size_t)d * n + v];
+            if (c == 0) continue;
+            const double h = (double)c;
+            sum1 = __dadd_rn(sum1, __dmul_rn(h, us[d]));
+            sum2 = __dadd_rn(sum2, __dmul_rn(h, ws[d]));
+        }
+        V[(size_t)s * n + v] = __ddiv_rn(__ddiv_rn(sum1, sum2), den);
+    }
+}
+
 }  // namespace
 
 qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V,
@@ -57,14 +83,21 @@ qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_si
         qc_weight_table(sigmas[s], L, w + (size_t)s * L, u + (size_t)s * L);
         den[s] = 2.0 * (sigmas[s] * sigmas[s]);
     }
+    dim3 grid(qc_ceil_div(g->n, 256) < 2 * ctx->num_sms ? qc_ceil_div(g->n, 256) : 2 * ctx->num_sms,
+              n_sigma);
+    if (tab.size() <= (size_t)INLINE_DOUBLES) {
+        InlineTables it;
+        std::copy(tab.begin(), tab.end(), it.t);
+        potential_kernel_inline<<<grid, 256, 0, stream>>>(g->n, g->D, n_sigma, g->hist.as<int32_t>(), it, V);
+        QC_LAUNCHED(ctx);
+        return QC_OK;
+    }
     qc_buffer dtab;
     QC_TRY(dtab.allocate(ctx, sizeof(double) * tab.size(), stream));
     QC_CUDA_TRY(ctx, cudaMemcpyAsync(dtab.ptr, tab.data(), dtab.bytes, cudaMemcpyHostToDevice, stream));
     // the host table must outlive the asynchronous copy
     QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
     const double *dw = dtab.as<double>();
-    dim3 grid(qc_ceil_div(g->n, 256) < 2 * ctx->num_sms ? qc_ceil_div(g->n, 256) : 2 * ctx->num_sms,
-              n_sigma);
     potential_kernel<<<grid, 256, 0, stream>>>(g->n, g->D, g->hist.as<int32_t>(), dw,
                                                dw + (size_t)n_sigma * L, dw + 2 * (size_t)n_sigma * L, V);
     QC_LAUNCHED(ctx);

@@ -181,9 +181,10 @@ void qc_weight_table(double sigma, int32_t len, double *w, double *u);
 bool qc_sigma_ok(double sigma);
 
 // ggd.cu: parents and roots.
+// order: nodes heaviest first (the graph's preparation) or NULL for 0..n-1.
 qc_status qc_descend(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
-                     const double *V, int32_t n_sigma, int32_t *labels, int32_t *n_roots_dev,
-                     cudaStream_t stream);
+                     const int32_t *order, const double *V, int32_t n_sigma, int32_t *labels,
+                     int32_t *n_roots_dev, cudaStream_t stream);
 
 // batch.cu: the graph-per-CTA kernel without a plan (used by the serving loop)
 struct qc_cta_launch;
