@@ -48,6 +48,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over all ranks of the process group (x itself when there is none)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: float, steps: int, world: int, max_total_ms: float) -> float:
+    """Units per second for the whole job: every rank runs `steps` steps of
+    `units_per_step` (replicas), timed by the slowest rank."""
+    return world * units_per_step * steps / (max_total_ms / 1000.0)
+
+
 def gteps_edges(graph) -> float:
     """sum over sources of the undirected edges in the source's component."""
     from scipy.sparse import csr_matrix
@@ -227,13 +244,9 @@ def bench_ours(args, graph, sigmas):
     kstats = ctx.kernel_stats("bfs_level", reset=True)
     ctx.set_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), dev)
     ms_per_step = total_ms / args.steps
-    value = world * S * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(S, args.steps, world, total_ms)
 
     # end to end through the public API with host buffers
     rp_h = torch.from_numpy(graph.row_ptr).pin_memory()
@@ -262,12 +275,8 @@ def bench_ours(args, graph, sigmas):
         e1.record(stream)
         torch.cuda.synchronize()
         e_times.append(e0.elapsed_time(e1))
-    e2e_ms = float(sum(e_times))
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * S * args.steps / (e2e_ms / 1000.0)
+    e2e_ms = max_over_ranks(float(sum(e_times)), dev)
+    e2e_value = whole_job_rate(S, args.steps, world, e2e_ms)
 
     if rank == 0:
         peak, peak_kind = measured_peak_gbs()

@@ -150,6 +150,16 @@ qc_status qc_graph_histogram(qc_graph *g, int32_t *hist_out, int32_t *D_out, voi
 qc_status qc_potential(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
                        void *stream);
 
+/* The potential with the distance of Section 3.1 taken literally from the
+ * adjacency matrix instead of hop counts: 0 from a node to itself, the edge
+ * weight (1 here) to a neighbour, and M, a value above every weight that the
+ * paper does not fix, to every other node, connected or not.  Node v then has
+ * deg(v) terms at distance 1 and n - 1 - deg(v) at distance M; no BFS runs.
+ * Same arithmetic, layout and errors as qc_potential; M must be finite and > 1
+ * (QC_ERR_INVALID_ARG otherwise). */
+qc_status qc_potential_adjacency(qc_graph *g, const double *sigmas, int32_t n_sigma, double M,
+                                 double *V_out, void *stream);
+
 /* Graph Gradient Descent and cluster centers (Algorithms 2 and 3) for n_sigma
  * potential vectors.  V: device double[n_sigma * n] (as written by
  * qc_potential), free of NaN (a NaN gives unspecified parents).  labels_out: device int32[n_sigma * n], the root node id each

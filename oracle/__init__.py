@@ -14,6 +14,8 @@ Per function, the passage it follows:
                        after Algorithm 4
   * ``find_centers``   Algorithm 3 (root of each parent chain)
   * ``solve``          Algorithm 4: potentials for every node, then GGD labels
+  * ``potential_adjacency``  Section 3.1 read literally: distance 1 on an edge,
+                       M (above every weight) between non-adjacent nodes
 """
 from __future__ import annotations
 
@@ -66,6 +68,8 @@ def _bind(lib):
     lib.qco_ggd_parent.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _i32p]
     lib.qco_find_centers.restype = ctypes.c_int32
     lib.qco_find_centers.argtypes = [ctypes.c_int32, _i32p, _i32p]
+    lib.qco_potential_adjacency.restype = None
+    lib.qco_potential_adjacency.argtypes = [ctypes.c_int32, _i32p, ctypes.c_double, ctypes.c_double, _f64p]
     return lib
 
 
@@ -133,6 +137,13 @@ class Oracle:
         d = self.bfs(graph, node)
         return float(self._lib.qco_potential_literal(d, graph.n, float(sigma)))
 
+    def potential_adjacency(self, graph, sigma: float, M: float = 2.0) -> np.ndarray:
+        """V with the paper-literal distance: 0 to itself, 1 to a neighbour, M otherwise."""
+        rp, _ = _csr(graph)
+        V = np.empty(graph.n, dtype=np.float64)
+        self._lib.qco_potential_adjacency(graph.n, rp, float(M), float(sigma), V)
+        return V
+
     def ggd_parent(self, graph, V: np.ndarray) -> tuple[np.ndarray, int]:
         """(parent, number of index-dependent ties)."""
         rp, ci = _csr(graph)
@@ -193,6 +204,10 @@ def potential(hist, sigma):
 
 def potential_literal(graph, node, sigma):
     return default().potential_literal(graph, node, sigma)
+
+
+def potential_adjacency(graph, sigma, M=2.0):
+    return default().potential_adjacency(graph, sigma, M)
 
 
 def ggd_parent(graph, V):

@@ -243,3 +243,31 @@ int32_t qco_find_centers(int32_t n, const int32_t *parent, int32_t *label)
     free(p);
     return roots;
 }
+
+/* ---- paper-literal distance (Section 3.1 as written) ----------------------- */
+
+/* Distance read straight from the adjacency matrix: 0 from a node to itself,
+ * the edge weight (1 in an unweighted graph) to a neighbour, and M, a value
+ * above every weight, to every other node.  Node i then has one term at
+ * distance 0, deg(i) terms at distance 1 and n - 1 - deg(i) terms at distance M;
+ * V is summed in that ascending order like the canonical form above. */
+void qco_potential_adjacency(int32_t n, const int32_t *row_ptr, double M, double sigma, double *V)
+{
+    const double dist[3] = {0.0, 1.0, M};
+    double w[3], u[3];
+    for (int k = 0; k < 3; ++k) {
+        double d2 = dist[k] * dist[k];
+        w[k] = exp(-d2 / (2.0 * (sigma * sigma)));
+        u[k] = d2 * w[k];
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t deg = row_ptr[i + 1] - row_ptr[i];
+        double h[3] = {1.0, (double)deg, (double)(n - 1 - deg)};
+        double sum1 = 0.0, sum2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            sum1 = sum1 + h[k] * u[k];
+            sum2 = sum2 + h[k] * w[k];
+        }
+        V[i] = (sum1 / sum2) / (2.0 * (sigma * sigma));
+    }
+}

@@ -159,6 +159,17 @@ class Graph:
                                                   _stream_handle(stream)))
         return out
 
+    def potential_adjacency(self, sigmas: Sequence[float], M: float = 2.0, out=None, stream=None):
+        """float64 tensor [S, n]: the potential with the paper-literal distance
+        (1 to a neighbour, M to any other node)."""
+        torch = _torch()
+        sig = (ctypes.c_double * len(sigmas))(*[float(x) for x in sigmas])
+        if out is None:
+            out = torch.empty((len(sigmas), self.n), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        self.ctx.check(self.ctx._lib.qc_potential_adjacency(self.handle, sig, len(sigmas), float(M),
+                                                            out.data_ptr(), _stream_handle(stream)))
+        return out
+
     def ggd_labels(self, V, out=None, stream=None, counts: bool = True):
         """(labels int32 tensor [S, n] of root node ids, clusters per sigma or None)."""
         torch = _torch()

@@ -71,7 +71,65 @@ __global__ void potential_kernel_inline(int32_t n, int32_t D, int32_t S, const i
     }
 }
 
+// Distance 0 to itself, 1 to each of deg(v) neighbours, M to the other
+// n - 1 - deg(v) nodes, summed in that ascending order.  tab: per sigma w0, w1,
+// wM, u0, u1, uM, den.
+__global__ void potential_adjacency_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
+                                           const __grid_constant__ InlineTables tab, double *__restrict__ V) {
+    const int s = blockIdx.y;
+    const double *t = tab.t + 7 * s;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int deg = row_ptr[v + 1] - row_ptr[v];
+        const double h[3] = {1.0, (double)deg, (double)(n - 1 - deg)};
+        double sum1 = 0.0, sum2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (h[k] == 0.0) continue;
+            sum1 = __dadd_rn(sum1, __dmul_rn(h[k], t[3 + k]));
+            sum2 = __dadd_rn(sum2, __dmul_rn(h[k], t[k]));
+        }
+        V[(size_t)s * n + v] = __ddiv_rn(__ddiv_rn(sum1, sum2), t[6]);
+    }
+}
+
 }  // namespace
+
+extern "C" qc_status qc_potential_adjacency(qc_graph *g, const double *sigmas, int32_t n_sigma, double M,
+                                            double *V_out, void *stream_) {
+    if (!g || !sigmas || n_sigma < 1 || !V_out) return QC_ERR_INVALID_ARG;
+    qc_ctx *ctx = g->ctx;
+    if (!std::isfinite(M) || !(M > 1.0)) {
+        qc_set_error(ctx, "qc_potential_adjacency: M = %g must be finite and > 1", M);
+        return QC_ERR_INVALID_ARG;
+    }
+    for (int32_t s = 0; s < n_sigma; ++s)
+        if (!qc_sigma_ok(sigmas[s])) {
+            qc_set_error(ctx, "qc_potential_adjacency: sigma[%d] = %g is not finite and > 0", s, sigmas[s]);
+            return QC_ERR_INVALID_ARG;
+        }
+    cudaStream_t stream = qc_stream(stream_);
+    QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const double dist[3] = {0.0, 1.0, M};
+    const int per = INLINE_DOUBLES / 7;
+    for (int32_t s0 = 0; s0 < n_sigma; s0 += per) {
+        const int32_t sn = (n_sigma - s0) < per ? (n_sigma - s0) : per;
+        InlineTables it;
+        for (int32_t s = 0; s < sn; ++s) {
+            const double sigma = sigmas[s0 + s];
+            for (int k = 0; k < 3; ++k) {
+                const double d2 = dist[k] * dist[k];
+                it.t[7 * s + k] = std::exp(-d2 / (2.0 * (sigma * sigma)));
+                it.t[7 * s + 3 + k] = d2 * it.t[7 * s + k];
+            }
+            it.t[7 * s + 6] = 2.0 * (sigma * sigma);
+        }
+        dim3 grid(qc_ceil_div(g->n, 256) < 2 * ctx->num_sms ? qc_ceil_div(g->n, 256) : 2 * ctx->num_sms, sn);
+        potential_adjacency_kernel<<<grid, 256, 0, stream>>>(g->n, g->row_ptr.as<int32_t>(), it,
+                                                             V_out + (size_t)s0 * g->n);
+        QC_LAUNCHED(ctx);
+    }
+    return QC_OK;
+}
 
 qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V,
                                  cudaStream_t stream) {

@@ -77,6 +77,8 @@ SIGNATURES = [
     ("qc_graph_histogram", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int32_p, ctypes.c_void_p]),
     ("qc_potential", ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_int32, ctypes.c_void_p,
                                     ctypes.c_void_p]),
+    ("qc_potential_adjacency", ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_int32, ctypes.c_double,
+                                              ctypes.c_void_p, ctypes.c_void_p]),
     ("qc_ggd_labels", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                      c_int32_p, ctypes.c_void_p]),
     ("qc_solve", ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_int32, ctypes.c_void_p,

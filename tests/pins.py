@@ -333,3 +333,29 @@ ALL_CHECKS = [
     check_isolated_and_tiny, check_exact_arithmetic, check_literal_form, check_descent,
     check_relabel_invariance,
 ]
+
+
+def check_adjacency_mode(orc):
+    """Paper-literal distance (1 on an edge, M otherwise): on graphs of diameter
+    <= 2 with M = 2 it coincides with the hop distance, bit for bit; on a path it
+    matches the definition evaluated from the adjacency matrix in 50 digits."""
+    for graph in [gg.complete(9), gg.star(12, 4), gg.two_cliques_bridge(1)]:
+        for sigma in (0.6, 1.0, 2.5):
+            hop = orc.potential(orc.histograms(graph), sigma)
+            adj = orc.potential_adjacency(graph, sigma, 2.0)
+            assert np.array_equal(hop, adj), (graph.name, sigma)
+    graph = gg.path(6)
+    A = np.zeros((6, 6))
+    A[np.arange(5), np.arange(1, 6)] = 1
+    A = A + A.T
+    for M, sigma in [(3.0, 1.0), (2.5, 0.7), (10.0, 2.0)]:
+        V = orc.potential_adjacency(graph, sigma, M)
+        for i in range(6):
+            dists = [0.0 if j == i else (1.0 if A[i, j] else M) for j in range(6)]
+            s = mpmath.mpf(sigma)
+            num = sum(mpmath.mpf(d) ** 2 * mpmath.exp(-mpmath.mpf(d) ** 2 / (2 * s * s)) for d in dists)
+            den = sum(mpmath.exp(-mpmath.mpf(d) ** 2 / (2 * s * s)) for d in dists)
+            assert close(V[i], num / den / (2 * s * s)), (M, sigma, i)
+
+
+ALL_CHECKS.append(check_adjacency_mode)

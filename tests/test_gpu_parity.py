@@ -196,3 +196,24 @@ def test_many_sigmas_in_groups(qc, ctx):
     graph = gg.planted_partition(1200, 6, 0.03, 0.002, gg.rng(29))
     sigmas = [0.4 + 0.1 * k for k in range(37)]
     assert_solution_matches(qc, ctx, graph, sigmas)
+
+
+@pytest.mark.parametrize("M", [2.0, 3.5, 100.0])
+def test_adjacency_mode(qc, ctx, M):
+    """Paper-literal distance: potentials and labels equal the oracle's bit for bit."""
+    sigmas = [0.5, 1.0, 2.0]
+    for graph in [gg.config1()[0], gg.erdos_renyi(700, 0.01, gg.rng(30)), gg.star(50, 3)]:
+        G = qc.Graph.from_graph(ctx, graph)
+        V = G.potential_adjacency(sigmas, M)
+        labels, counts = G.ggd_labels(V)
+        Vh = V.cpu().numpy()
+        for k, s in enumerate(sigmas):
+            ref = oracle.potential_adjacency(graph, s, M)
+            assert np.array_equal(Vh[k], ref), (graph.name, s)
+            p, _ = oracle.ggd_parent(graph, ref)
+            lab, nc = oracle.find_centers(p)
+            assert np.array_equal(labels.cpu().numpy()[k], lab)
+            assert counts[k] == nc
+        with pytest.raises(qc.QCError):
+            G.potential_adjacency(sigmas, 0.5)
+        G.close()
