@@ -225,6 +225,7 @@ typedef struct {
 /* Per-request times on the host clock (milliseconds from submission). */
 typedef struct {
     double admit_ms;           /* admitted to the GPU */
+    double start_ms;           /* its GPU work issued (batched launch, or taken by a large-graph worker) */
     double done_ms;            /* result available (the request's latency) */
     int32_t n;
     int64_t nnz;

@@ -292,7 +292,7 @@ class Server:
         return rid.value
 
     def _result(self, rid, labels, nc, info):
-        return {"labels": labels, "n_clusters": nc.value, "admit_ms": info.admit_ms,
+        return {"labels": labels, "n_clusters": nc.value, "admit_ms": info.admit_ms, "start_ms": info.start_ms,
                 "latency_ms": info.done_ms, "batch_size": info.batch_size}
 
     def poll(self, rid: int):

@@ -44,6 +44,7 @@
 // records a timeout and returns).  If the histogram runs out of rows the kernel
 // stops at a level boundary and the host grows it and relaunches from that
 // level.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -369,7 +370,7 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
 }
 
 template <int G>
-__global__ void __launch_bounds__(256, G == 32 ? 1 : 4) bfs_persistent(const BfsParams p) {
+__global__ void __launch_bounds__(256, G == 32 ? 3 : 4) bfs_persistent(const BfsParams p) {
     __shared__ ulonglong2 red[WARPS][32];
     int level = p.start_level;
     const bool stamp = p.stamp && blockIdx.x == 0 && threadIdx.x == 0;
@@ -562,6 +563,13 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
             if (timing) QC_CUDA_TRY(ctx, cudaEventRecord(ev.b, stream));
             QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_status, ctl.ptr, 2 * sizeof(int32_t),
                                              cudaMemcpyDeviceToHost, stream));
+            // level stamps ride in the same pinned block, after the status words
+            unsigned long long *h_stamp = reinterpret_cast<unsigned long long *>(
+                static_cast<char *>(pin.ptr) + 64);
+            const size_t stamp_cap = std::min<size_t>((size_t)n + 3, (QC_PINNED_BYTES - 64) / 8);
+            if (timing)
+                QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_stamp, stamps.ptr, sizeof(unsigned long long) * stamp_cap,
+                                                 cudaMemcpyDeviceToHost, stream));
             QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
             const int32_t st = h_status[0], reached = h_status[1];
             if (timing) {
@@ -570,11 +578,11 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
                 const int passes = reached - start + 1 + (start == 2 ? 1 : 0);
                 const double per_pass = qc_bfs_level_model_bytes(n, g->nnz, wn);
                 qc_record_kernel(ctx, "bfs_level", ms, passes * per_pass);
-                // stamp[l] opens level l (stamp[1] = launch start; the set-up covers levels 1-2)
-                std::vector<unsigned long long> h((size_t)reached + 2);
-                QC_CUDA_TRY(ctx, cudaMemcpy(h.data(), stamps.ptr, sizeof(unsigned long long) * h.size(),
-                                            cudaMemcpyDeviceToHost));
-                for (int l = start - 1; l <= reached && l + 1 < (int)h.size(); ++l) {
+                // stamp[l] opens level l (stamp[1] = launch start; the set-up covers levels 1-2);
+                // levels past the pinned block's room are left out of the per-level figures
+                const unsigned long long *h = h_stamp;
+                const int n_stamps = (int)std::min<size_t>((size_t)reached + 2, stamp_cap);
+                for (int l = start - 1; l <= reached && l + 1 < n_stamps; ++l) {
                     if (!h[l] || !h[l + 1] || h[l + 1] < h[l]) continue;
                     char name[32];
                     snprintf(name, sizeof name, "bfs_pass_%d", l);

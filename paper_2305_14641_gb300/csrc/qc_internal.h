@@ -158,7 +158,7 @@ struct qc_graph {
 // prep.cu
 // Degree bucket (floor(log2(deg + 1))) from which a row counts as heavy: its BFS
 // item is shared by all warps of a block instead of one warp.
-#define QC_HEAVY_BUCKET 6
+#define QC_HEAVY_BUCKET 7
 qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream);
 // hist[0][v] = 1, hist[1][v] = deg(v)
 qc_status qc_fill_first_rows(qc_graph *g, cudaStream_t stream);

@@ -49,7 +49,7 @@ struct Req {
     RState state = RState::Queued;
     qc_status status = QC_OK;
     bool cancel = false;
-    Clock::time_point t_submit, t_admit, t_done;
+    Clock::time_point t_submit, t_admit, t_start, t_done;
     int32_t batch_size = 0;
     qc_graph *g = nullptr;
     qc_buffer labels_dev;
@@ -267,7 +267,11 @@ struct qc_server {
             if (!pending.empty() && free_slot) {
                 std::vector<Req *> rs;
                 rs.swap(pending);
-                for (Req *r : rs) r->batch_size = (int32_t)rs.size();
+                const Clock::time_point t_launch = Clock::now();
+                for (Req *r : rs) {
+                    r->batch_size = (int32_t)rs.size();
+                    r->t_start = t_launch;
+                }
                 free_slot->busy = true;
                 free_slot->finished = false;
                 free_slot->reqs = rs;
@@ -311,6 +315,7 @@ struct qc_server {
                 finish(r, RState::Cancelled, QC_ERR_CANCELLED);
                 continue;
             }
+            r->t_start = Clock::now();
             lk.unlock();
             qc_status status = QC_OK;
             if (r->g) {
@@ -352,6 +357,9 @@ struct qc_server {
             info->admit_ms = r->state == RState::Cancelled && r->t_admit.time_since_epoch().count() == 0
                                  ? -1.0
                                  : std::chrono::duration<double, std::milli>(r->t_admit - r->t_submit).count();
+            info->start_ms = r->t_start.time_since_epoch().count() == 0
+                                 ? -1.0
+                                 : std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count();
             info->done_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
             info->n = r->n;
             info->nnz = r->nnz;

@@ -42,7 +42,8 @@ class qc_server_stats(ctypes.Structure):
 
 
 class qc_request_info(ctypes.Structure):
-    _fields_ = [("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double), ("n", ctypes.c_int32),
+    _fields_ = [("admit_ms", ctypes.c_double), ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
+                ("n", ctypes.c_int32),
                 ("nnz", ctypes.c_int64), ("batch_size", ctypes.c_int32)]
 
 
