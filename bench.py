@@ -38,7 +38,16 @@ WORKLOAD = ("dcsbm-16384: degree-corrected SBM, N=16384, 32 equal communities, p
             "values log-spaced 0.5-4.0 reusing one histogram")
 METRIC = "clusterings/s"
 PROFILE = os.path.join(ROOT, "profiles", "bfs_persistent_dcsbm16384.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_2305_14641_gb300", "csrc", "bfs.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2305_14641_gb300", "csrc", f)
+              for f in ("bfs.cu", "qc_device.cuh", "qc_internal.h")]
+
+
+def kernel_source_sha256() -> str:
+    """sha256 over the sources the BFS kernel is built from, in a fixed order."""
+    h = hashlib.sha256()
+    for path in KERNEL_SRC:
+        h.update(open(path, "rb").read())
+    return h.hexdigest()
 
 
 def dist_env():
@@ -147,7 +156,7 @@ def profile_traffic():
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not h:
         return None
-    if hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest() != h.group(1):
+    if kernel_source_sha256() != h.group(1):
         return None
     return float(m.group(1))
 
@@ -225,6 +234,9 @@ def bench_ours(args, graph, sigmas):
     # timed region: K steps, each bracketed by events after an L2 flush
     ctx.set_timing(True)
     ctx.kernel_stats("bfs_level", reset=True)
+    for lvl in range(n + 2):
+        if ctx.kernel_stats(f"bfs_pass_{lvl}", reset=True)["launches"] == 0 and lvl > 2:
+            break
     launches0 = ctx.launch_count()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -242,6 +254,14 @@ def bench_ours(args, graph, sigmas):
         torch.distributed.barrier()
     launches = ctx.launch_count() - launches0
     kstats = ctx.kernel_stats("bfs_level", reset=True)
+    # per-level device time inside the BFS launch (globaltimer stamps at each grid barrier);
+    # level 1 is the set-up that writes the rows of levels 0-1
+    level_us = {}
+    for lvl in range(1, n + 2):
+        st = ctx.kernel_stats(f"bfs_pass_{lvl}", reset=True)
+        if st["launches"] == 0:
+            break
+        level_us[lvl] = round(1000.0 * st["total_ms"] / st["launches"], 2)
     ctx.set_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = max_over_ranks(float(sum(step_ms)), dev)
@@ -320,6 +340,7 @@ def bench_ours(args, graph, sigmas):
                                            if kstats["launches"] else None)},
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
+            "bfs_level_us": level_us,
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
@@ -378,6 +399,7 @@ def bench_batch(args):
     line = {"metric": "clusterings/s", "workload": BATCH_WORKLOAD, "graphs": len(graphs),
             "nodes": int(sum(g.n for g in graphs)), "directed_edges": int(sum(g.nnz for g in graphs)),
             "batched": batched, "ms_per_batch": sum(times) / len(times), "plain": plain,
+            "kernel_config": plan.config(),
             "plain_sample_graphs": m, "batched_over_plain": batched / plain, "plan_seconds": plan_s,
             "steps": args.steps, "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)

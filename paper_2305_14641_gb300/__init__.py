@@ -241,6 +241,12 @@ class BatchPlan:
         self.ctx.check(self.ctx._lib.qc_batch_run(self.handle, nc, _stream_handle(stream)))
         return list(nc) if counts else None
 
+    def config(self) -> dict:
+        """The kernel configuration the plan runs (threads per CTA, source words per chunk)."""
+        t, c = ctypes.c_int32(), ctypes.c_int32()
+        self.ctx.check(self.ctx._lib.qc_batch_config(self.handle, ctypes.byref(t), ctypes.byref(c)))
+        return {"threads": t.value, "chunk_words": c.value}
+
     def labels_of(self, k: int):
         o = int(self.offsets[k])
         return self.labels[o:o + self.graphs[k].n]

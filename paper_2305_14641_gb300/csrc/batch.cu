@@ -25,6 +25,8 @@
 // (largest n, mean degree) bucket in the context.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <memory>
 #include <numeric>
 #include <vector>
@@ -603,6 +605,14 @@ qc_status qc_batch_create(qc_ctx *ctx, int32_t n_graphs, qc_graph *const *graphs
             qc_set_error(ctx, "qc_batch_create: no kernel configuration fits n = %d", b->n_max);
             return QC_ERR_INVALID_ARG;
         }
+        // QCGRAPH_BATCH_CONFIG="threads,chunk_words" fixes the choice when it is a
+        // candidate (reproducible profiling), else the autotuner decides
+        if (const char *env = getenv("QCGRAPH_BATCH_CONFIG")) {
+            int t = 0, c = 0;
+            if (sscanf(env, "%d,%d", &t, &c) == 2)
+                for (size_t i = 0; i < cands.size(); ++i)
+                    if (cands[i].first == t && cands[i].second == c) choice = (int)i;
+        }
         if (choice < 0 || choice >= (int)cands.size()) {
             qc_event_pair ev;
             QC_TRY(ev.create(ctx));
@@ -688,6 +698,13 @@ qc_status qc_batch_run(qc_batch *b, int32_t *n_clusters_out, void *stream_) {
 }
 
 void qc_batch_destroy(qc_batch *b) { delete b; }
+
+qc_status qc_batch_config(const qc_batch *b, int32_t *threads, int32_t *chunk_words) {
+    if (!b || !threads || !chunk_words) return QC_ERR_INVALID_ARG;
+    *threads = b->n_cta > 0 ? b->threads : 0;
+    *chunk_words = b->n_cta > 0 ? b->c : 0;
+    return QC_OK;
+}
 
 qc_status qc_solve_batch(qc_ctx *ctx, int32_t n_graphs, qc_graph *const *graphs,
                          const double *sigma_per_graph, int32_t *labels_out,

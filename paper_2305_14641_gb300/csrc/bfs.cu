@@ -27,7 +27,7 @@
 //
 // Work: items are (node, tile of 32 segments) taken in the graph's order
 // (heaviest degree bucket first; sat is indexed in that order).  Items of rows
-// with degree >= 63 are heavy: all warps of a block share one, splitting its
+// with degree >= 127 are heavy: all warps of a block share one, splitting its
 // neighbour list.  Other items go one warp each, GRAB list positions per counter
 // update: the first pull level lists every light item, and each level appends
 // the items it pulled (still open, or saturated just now and owed one copy of

@@ -58,6 +58,24 @@ def test_batch_planted(qc, ctx):
     check_batch(qc, ctx, graphs, sigmas)
 
 
+@pytest.mark.parametrize("threads,words", [(256, 1), (512, 4)])
+def test_batch_fixed_config(qc, ctx, monkeypatch, threads, words):
+    # every kernel configuration the autotuner may pick gives the oracle's labels
+    monkeypatch.setenv("QCGRAPH_BATCH_CONFIG", f"{threads},{words}")
+    graphs, sigmas = gg.config4_batch(48)
+    Gs = [qc.Graph.from_graph(ctx, g) for g in graphs]
+    plan = qc.BatchPlan(ctx, Gs, sigmas)
+    assert plan.config() == {"threads": threads, "chunk_words": words}
+    counts = plan.run()
+    for k, (g, s) in enumerate(zip(graphs, sigmas)):
+        ref = oracle.solve(g, [s])
+        assert np.array_equal(plan.labels_of(k).cpu().numpy(), ref.labels[0]), (g.name, threads, words)
+        assert counts[k] == ref.n_clusters[0]
+    plan.close()
+    for G in Gs:
+        G.close()
+
+
 def test_batch_edge_cases_and_deep_graph(qc, ctx):
     """Single nodes, no edges, cliques, a path too deep for the batched kernel's
     histogram (finished by the single-graph path) and a graph above the CTA limit."""
