@@ -3,6 +3,12 @@
 sigma values, descent and roots for each).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload dcsbm16384|sbm262144|batch4096|serve]
+
+The other workloads: sbm262144 (one SBM of 262,144 nodes, sigma 1.5, the same
+line format; its CPU baseline is a bounded sample scaled to the whole graph),
+batch4096 (4096 small graphs, batched plan vs the plain path) and serve (a
+Poisson request stream through the serving loop, p50/p99).
 
 Prints one JSON line.  `value` is clusterings/s (one clustering = one label
 vector for one (graph, sigma) pair) over all ranks, timed on the device with
@@ -38,6 +44,19 @@ WORKLOAD = ("dcsbm-16384: degree-corrected SBM, N=16384, 32 equal communities, p
             "values log-spaced 0.5-4.0 reusing one histogram")
 METRIC = "clusterings/s"
 PROFILE = os.path.join(ROOT, "profiles", "bfs_persistent_dcsbm16384.md")
+
+# single-graph workloads: generator, description, the ncu summary holding the BFS
+# kernel's DRAM traffic per launch, and how many nodes the CPU baseline samples
+# (None: the whole workload)
+SINGLE = {
+    "dcsbm16384": {"make": lambda: gg.config2(), "desc": WORKLOAD, "profile": PROFILE,
+                   "cpu_sample_nodes": None, "steps": 200},
+    "sbm262144": {"make": lambda: gg.config3(),
+                  "desc": ("sbm-262144: SBM, N=262144, 256 equal communities of 1024, mean degree 20, "
+                           "mixing 0.15, seed 2; sigma 1.5"),
+                  "profile": os.path.join(ROOT, "profiles", "bfs_persistent_sbm262144.md"),
+                  "cpu_sample_nodes": 512, "steps": 3},
+}
 KERNEL_SRC = [os.path.join(ROOT, "paper_2305_14641_gb300", "csrc", f)
               for f in ("bfs.cu", "qc_device.cuh", "qc_internal.h")]
 
@@ -146,12 +165,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def profile_traffic():
+def profile_traffic(path=PROFILE):
     """dram bytes per launch from the committed ncu summary, if it was taken on the
     current kernel source (else None)."""
-    if not os.path.exists(PROFILE):
+    if not path or not os.path.exists(path):
         return None
-    text = open(PROFILE).read()
+    text = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not h:
@@ -168,24 +187,51 @@ def measured_peak_gbs():
     return 6800.0, "fallback"
 
 
-def run_cpu_oracle(graph, sigmas, threads):
+def run_cpu_oracle(graph, sigmas, threads, sample_nodes=None):
+    """Seconds the oracle takes for one solve of the workload.  With sample_nodes,
+    the per-source BFS runs from that many evenly spaced nodes only and its time
+    is scaled by n / sample_nodes; potentials, descent and roots then run on all
+    n nodes over the sampled histogram rows repeated to n rows (the same
+    per-node work)."""
     import oracle
+    if sample_nodes is None or sample_nodes >= graph.n:
+        t0 = time.perf_counter()
+        oracle.solve(graph, sigmas, threads=threads)
+        return time.perf_counter() - t0
+    nodes = np.linspace(0, graph.n - 1, sample_nodes).astype(np.int32)
     t0 = time.perf_counter()
-    oracle.solve(graph, sigmas, threads=threads)
-    return time.perf_counter() - t0
+    h = oracle.histograms(graph, nodes, threads=threads)
+    t_bfs = (time.perf_counter() - t0) * graph.n / sample_nodes
+    full = np.ascontiguousarray(np.resize(h, (graph.n, h.shape[1])))
+    t0 = time.perf_counter()
+    for s in sigmas:
+        V = oracle.potential(full, s)
+        p, _ = oracle.ggd_parent(graph, V)
+        oracle.find_centers(p)
+    return t_bfs + time.perf_counter() - t0
 
 
-def bench_reference(args, graph, sigmas):
-    """The oracle, as it stands, on the host cores: each step one full solve of the workload."""
+def cpu_sample_text(graph, sigmas, sample_nodes):
+    if sample_nodes is None or sample_nodes >= graph.n:
+        return (f"one full solve of the workload: queue BFS from all {graph.n} sources, histograms, "
+                f"{len(sigmas)} potential(s), descent, roots")
+    return (f"queue BFS from {sample_nodes} evenly spaced sources of {graph.n}, time scaled by "
+            f"{graph.n}/{sample_nodes}; then potential, descent and roots over all {graph.n} nodes")
+
+
+def bench_reference(args, graph, sigmas, spec):
+    """The oracle, as it stands, on the host cores: each step one solve of the workload
+    (a bounded sample of it, scaled, where the whole would take minutes)."""
     import oracle
     rank, world, _ = dist_env()
     if rank != 0:
         return
     threads = oracle.default_threads()
     oracle.build()
+    sample = spec["cpu_sample_nodes"]
     for _ in range(args.warmup):
-        run_cpu_oracle(graph, sigmas, threads)
-    times = [run_cpu_oracle(graph, sigmas, threads) for _ in range(args.steps)]
+        run_cpu_oracle(graph, sigmas, threads, sample)
+    times = [run_cpu_oracle(graph, sigmas, threads, sample) for _ in range(args.steps)]
     total = sum(times)
     value = len(sigmas) * args.steps / total
     line = {
@@ -193,16 +239,15 @@ def bench_reference(args, graph, sigmas):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": graph.n, "nnz": graph.nnz, "sigmas": len(sigmas)},
+        "config": {"workload": spec["desc"], "n": graph.n, "nnz": graph.nnz, "sigmas": len(sigmas)},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
-                         "sample": "the full workload per step: queue BFS from all 16384 sources, "
-                                   "histograms, 16 potentials, descent and roots"},
+                         "sample": cpu_sample_text(graph, sigmas, sample)},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def bench_ours(args, graph, sigmas):
+def bench_ours(args, graph, sigmas, spec):
     import torch
     import paper_2305_14641_gb300 as qc
 
@@ -302,7 +347,7 @@ def bench_ours(args, graph, sigmas):
         peak, peak_kind = measured_peak_gbs()
         achieved = (kstats["model_bytes"] / (kstats["total_ms"] / 1000.0) / 1e9
                     if kstats["total_ms"] > 0 else None)
-        traffic = profile_traffic()
+        traffic = profile_traffic(spec["profile"])
         edges = gteps_edges(graph)
         bfs_ms = kstats["total_ms"] / args.steps
         cpu = None
@@ -310,17 +355,16 @@ def bench_ours(args, graph, sigmas):
             import oracle
             oracle.build()
             threads = oracle.default_threads()
-            t = run_cpu_oracle(graph, sigmas, threads)
+            t = run_cpu_oracle(graph, sigmas, threads, spec["cpu_sample_nodes"])
             cpu = {"value": S / t, "unit": METRIC, "cores": threads, "kind": "oracle",
-                   "sample": "one full solve of the workload (queue BFS from all 16384 sources, "
-                             "histograms, 16 potentials, descent, roots)",
+                   "sample": cpu_sample_text(graph, sigmas, spec["cpu_sample_nodes"]),
                    "seconds": t}
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64 bitsets / f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "nnz": graph.nnz, "sigmas": S,
+            "config": {"workload": spec["desc"], "n": n, "nnz": graph.nnz, "sigmas": S,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "256 MiB buffer written between timed steps"},
             "gteps": edges * world * args.steps / (total_ms / 1000.0) / 1e9,
@@ -332,10 +376,11 @@ def bench_ours(args, graph, sigmas):
                          "model_bytes_per_launch": (kstats["model_bytes"] / kstats["launches"]
                                                     if kstats["launches"] else None),
                          "launches": kstats["launches"],
-                         "bytes_model": "pull-all: per level 8*W*(E+3N) bitset bytes + CSR + one "
-                                        "histogram row, W = 256 source words; saturated rows are "
-                                        "skipped and the 64 MiB of bitsets stay in L2, so the DRAM "
-                                        "traffic is far below the model",
+                         "bytes_model": f"pull-all: per level and chunk of source words, 8*wn*(E+3N) "
+                                        f"bitset bytes + CSR + one histogram row (W = {(n + 63) // 64} "
+                                        f"words in chunks sized to half of L2); saturated rows are "
+                                        f"skipped and each chunk's bitsets stay in L2, so the DRAM "
+                                        f"traffic is far below the model",
                          "avg_launch_ms": (kstats["total_ms"] / kstats["launches"]
                                            if kstats["launches"] else None)},
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
@@ -499,26 +544,31 @@ def bench_serve(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 200; 3 for sbm262144)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["dcsbm16384", "batch4096", "serve"], default="dcsbm16384")
+    ap.add_argument("--workload", choices=["dcsbm16384", "sbm262144", "batch4096", "serve"],
+                    default="dcsbm16384")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--plain-graphs", type=int, default=512)
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--large-workers", type=int, default=4)
     ap.add_argument("--large-sm-share", type=float, default=0.4)
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = SINGLE[args.workload]["steps"] if args.workload in SINGLE else 200
     if args.workload == "batch4096":
         return bench_batch(args)
     if args.workload == "serve":
         return bench_serve(args)
-    graph, sigmas = gg.config2()
+    spec = SINGLE[args.workload]
+    graph, sigmas = spec["make"]()
     if args.impl == "reference":
-        bench_reference(args, graph, sigmas)
+        bench_reference(args, graph, sigmas, spec)
     else:
-        bench_ours(args, graph, sigmas)
+        bench_ours(args, graph, sigmas, spec)
 
 
 if __name__ == "__main__":

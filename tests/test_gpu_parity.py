@@ -99,6 +99,49 @@ def test_config2_full(qc, ctx):
     assert_solution_matches(qc, ctx, graph, sigmas)
 
 
+def test_config3_full_size_sampled(qc, ctx):
+    """SBM N=262144 (5.24M directed edges) at full size.  The oracle's per-source
+    BFS is too slow for every node, so: histogram rows of sampled nodes (random,
+    first, last, extreme degrees) bit-exact against the oracle; invariants at every
+    node (h(0) = 1, h(1) = degree, row sum = component size); potentials of every
+    node against the oracle's potential of the GPU histogram, and of the sampled
+    nodes against the oracle's own histograms; labels bit-exact against the
+    oracle's descent and roots run on those potentials."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    graph, sigmas = gg.config3()
+    n = graph.n
+    g = qc.Graph.from_graph(ctx, graph)
+    hist = g.histogram().cpu().numpy()
+    D = hist.shape[0] - 1
+    deg = np.diff(graph.row_ptr)
+    assert np.all(hist[0] == 1) and np.array_equal(hist[1], deg)
+    a = csr_matrix((np.ones(graph.nnz), graph.col_idx, graph.row_ptr), shape=(n, n))
+    _, comp = connected_components(a, directed=False)
+    assert np.array_equal(hist.sum(axis=0, dtype=np.int64), np.bincount(comp)[comp])
+    rs = gg.rng(30)
+    nodes = np.unique(np.concatenate([rs.choice(n, 60, replace=False),
+                                      [0, n - 1, int(np.argmax(deg)), int(np.argmin(deg))]])).astype(np.int32)
+    ref_h = oracle.histograms(graph, nodes, threads=oracle.default_threads(), cap=D + 1)
+    cols = ref_h.shape[1]
+    assert cols <= D + 1
+    assert np.array_equal(hist[:cols, nodes].T, ref_h)
+    assert not hist[cols:, nodes].any()
+    V = g.potential(sigmas)
+    Vh = V.cpu().numpy()
+    for k, s in enumerate(sigmas):
+        assert np.array_equal(Vh[k], oracle.potential(np.ascontiguousarray(hist.T), s))
+        assert np.array_equal(Vh[k, nodes], oracle.potential(ref_h, s))
+    labels, counts = g.ggd_labels(V)
+    labels = labels.cpu().numpy()
+    for k in range(len(sigmas)):
+        p, _ = oracle.ggd_parent(graph, Vh[k])
+        lab, roots = oracle.find_centers(p)
+        assert np.array_equal(labels[k], lab)
+        assert counts[k] == roots
+    g.close()
+
+
 def test_sigma_reuse_and_edge_values(qc, ctx):
     """The cached histogram serves later sigma values; extreme sigmas stay exact."""
     graph = gg.planted_partition(600, 6, 0.06, 0.003, gg.rng(25))
