@@ -2,8 +2,9 @@
 the CUDA path.
 
 This module holds none of the clustering method's arithmetic: it only draws
-undirected, unweighted graphs (int32 CSR) and per-graph parameters (sigma
-values, request arrival times) from seeded pseudo-random streams.
+unweighted graphs (int32 CSR; undirected unless a generator says directed) and
+per-graph parameters (sigma values, request arrival times) from seeded
+pseudo-random streams.
 
 Random numbers: numpy's PCG64 bit generator (O'Neill 2014), seeded through
 ``SeedSequence([seed, *tags])`` so that every graph, block pair and request has
@@ -13,8 +14,9 @@ generation of large random networks"), which draws one variate per kept edge
 instead of one per candidate pair.  The degree-corrected SBM, whose pair
 probabilities differ per pair, is sampled pair by pair.
 
-Every graph returned is canonical: symmetric, no self-loops, no duplicate
-edges, rows sorted ascending.
+Every graph returned is canonical: no self-loops, no duplicate edges, rows
+sorted ascending, and symmetric unless it is directed (row v then lists the
+edges v -> u).
 """
 from __future__ import annotations
 
@@ -27,7 +29,8 @@ __all__ = [
     "Graph", "rng", "csr_from_pairs", "block_sizes", "planted_partition",
     "sbm_mean_degree", "dcsbm", "complete", "path", "star", "two_cliques_bridge",
     "erdos_renyi", "relabel", "config1", "config2", "config3", "config4_batch",
-    "config5_requests", "config2_sigmas", "Request",
+    "config5_requests", "config2_sigmas", "Request", "csr_from_arcs", "directed_cycle",
+    "directed_path", "directed_erdos_renyi", "directed_planted_partition",
 ]
 
 
@@ -39,6 +42,7 @@ class Graph:
     name: str = ""
     block: np.ndarray | None = None   # planted community of each node, when there is one
     meta: dict = field(default_factory=dict)
+    directed: bool = False            # row v lists the edges v -> u
 
     @property
     def nnz(self) -> int:
@@ -72,6 +76,20 @@ def csr_from_pairs(n: int, i: np.ndarray, j: np.ndarray) -> tuple[np.ndarray, np
     if row_ptr[-1] >= 2**31:
         raise ValueError("graph has 2^31 or more directed edges; int32 CSR cannot hold it")
     return row_ptr.astype(np.int32), cols.astype(np.int32)
+
+
+def csr_from_arcs(n: int, i: np.ndarray, j: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Directed CSR from arcs i -> j: deduplicated, no self-loops, rows sorted."""
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    keep = i != j
+    keys = np.unique(i[keep] * n + j[keep])
+    rows = keys // n
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=row_ptr[1:])
+    if row_ptr[-1] >= 2**31:
+        raise ValueError("graph has 2^31 or more arcs; int32 CSR cannot hold it")
+    return row_ptr.astype(np.int32), (keys - rows * n).astype(np.int32)
 
 
 def block_sizes(n: int, k: int) -> np.ndarray:
@@ -252,6 +270,51 @@ def erdos_renyi(n: int, p: float, g: np.random.Generator) -> Graph:
     keep = g.random(len(i)) < p
     rp, ci = csr_from_pairs(n, i[keep], j[keep])
     return Graph(n, rp, ci, name=f"G({n},{p})")
+
+
+def directed_cycle(n: int) -> Graph:
+    """Arcs v -> v + 1 (mod n)."""
+    i = np.arange(n)
+    rp, ci = csr_from_arcs(n, i, (i + 1) % n)
+    return Graph(n, rp, ci, name=f"C{n}->", directed=True)
+
+
+def directed_path(n: int) -> Graph:
+    """Arcs v -> v + 1 for v < n - 1."""
+    i = np.arange(n - 1)
+    rp, ci = csr_from_arcs(n, i, i + 1)
+    return Graph(n, rp, ci, name=f"P{n}->", directed=True)
+
+
+def directed_erdos_renyi(n: int, p: float, g: np.random.Generator) -> Graph:
+    """Every ordered pair (i, j), i != j, is an arc with probability p."""
+    t = _bernoulli_positions(g, n * (n - 1), p)
+    i = t // (n - 1)
+    j = t - i * (n - 1)
+    j = j + (j >= i)                      # skip the diagonal
+    rp, ci = csr_from_arcs(n, i, j)
+    return Graph(n, rp, ci, name=f"D({n},{p})", directed=True)
+
+
+def directed_planted_partition(n: int, k: int, p_in: float, p_out: float, g: np.random.Generator,
+                               name: str = "") -> Graph:
+    """Directed planted partition: each ordered pair is an arc with probability p_in
+    inside a block and p_out across (two independent undirected draws give the
+    arcs i -> j and j -> i of every pair i < j)."""
+    a = planted_partition(n, k, p_in, p_out, g)
+    b = planted_partition(n, k, p_in, p_out, g)
+    arcs_i, arcs_j = [], []
+    for graph, forward in ((a, True), (b, False)):
+        rows = np.repeat(np.arange(n, dtype=np.int64), graph.degrees())
+        cols = graph.col_idx.astype(np.int64)
+        lower = rows < cols
+        if forward:
+            arcs_i.append(rows[lower]); arcs_j.append(cols[lower])
+        else:
+            arcs_i.append(cols[lower]); arcs_j.append(rows[lower])
+    rp, ci = csr_from_arcs(n, np.concatenate(arcs_i), np.concatenate(arcs_j))
+    return Graph(n, rp, ci, name=name or f"dpp-{n}", block=a.block, directed=True,
+                 meta={"k": k, "p_in": p_in, "p_out": p_out})
 
 
 def relabel(graph: Graph, perm: np.ndarray) -> Graph:

@@ -106,15 +106,20 @@ const char *qc_last_error(const qc_ctx *ctx);
 
 enum {
     QC_PTR_DEVICE = 1u, /* row_ptr / col_idx are device pointers (else host) */
-    QC_VALIDATE = 2u    /* check the CSR: row_ptr[0] = 0, non-decreasing, row_ptr[n] =
+    QC_VALIDATE = 2u,   /* check the CSR: row_ptr[0] = 0, non-decreasing, row_ptr[n] =
                            nnz; column ids in [0, n); rows strictly ascending (sorted,
-                           no duplicates); no self-loops; symmetric (undirected) */
+                           no duplicates); no self-loops; symmetric (undirected) unless
+                           QC_DIRECTED */
+    QC_DIRECTED = 4u    /* the graph is directed: row v lists v's out-neighbours */
 };
 
-/* Upload an undirected, unweighted graph in CSR form (the paper's adjacency
- * matrix input of Algorithms 1 and 4, held sparse): node v's neighbours are
+/* Upload an unweighted graph in CSR form (the paper's adjacency matrix input
+ * of Algorithms 1 and 4, held sparse): node v's neighbours are
  * col_idx[row_ptr[v] .. row_ptr[v+1]-1].  row_ptr: int32[n+1]; col_idx:
- * int32[nnz], each undirected edge stored in both rows.  The library copies
+ * int32[nnz].  Undirected graphs store each edge in both rows.  With
+ * QC_DIRECTED row v holds the edges v -> u (graph(v, u) of Algorithm 1): the
+ * distance dist(i, j) is then the length of the shortest directed path from i
+ * to j, and the descent of Algorithm 2 looks at out-neighbours.  The library copies
  * the arrays into device memory it owns; the copy stays resident until
  * qc_graph_destroy.  Without QC_VALIDATE the CSR is trusted: an invalid one
  * gives undefined results (out-of-range ids may fault the GPU).
@@ -140,6 +145,20 @@ int64_t qc_graph_num_edges(const qc_graph *g);
  * only.  D_out: host, required.  Synchronises `stream` (D is a host output).
  * Errors: QC_ERR_INVALID_ARG, QC_ERR_BUDGET, QC_ERR_OOM, QC_ERR_CUDA. */
 qc_status qc_graph_histogram(qc_graph *g, int32_t *hist_out, int32_t *D_out, void *stream);
+
+/* Install a histogram computed earlier (qc_graph_histogram of the same graph,
+ * saved and reloaded), so that potentials for new sigma values need no BFS: the
+ * checkpoint of a sigma sweep.  hist: int32[(D+1) * n], level-major as
+ * qc_graph_histogram writes it, host memory or (QC_PTR_DEVICE) device memory;
+ * the library copies it.  0 <= D < n.  With QC_VALIDATE the rows are checked on
+ * the device against what the graph fixes: h(0, v) = 1, h(1, v) = out-degree,
+ * entries >= 0, sum over d <= n, row D not all zero, and D = 0 exactly when the
+ * graph has no edges.
+ * Errors: QC_ERR_INVALID_ARG (null pointers, D out of range),
+ * QC_ERR_INVALID_GRAPH (validation failed), QC_ERR_BUDGET, QC_ERR_OOM,
+ * QC_ERR_CUDA. */
+qc_status qc_graph_set_histogram(qc_graph *g, const int32_t *hist, int32_t D, uint32_t flags,
+                                 void *stream);
 
 /* Potential V for every node and every sigma (Eq. 7 last line, Algorithm 1),
  * in binary64, summed over distances in ascending order from the histogram.
@@ -275,6 +294,20 @@ qc_status qc_server_cancel(qc_server *s, uint64_t req_id);
 qc_status qc_server_get_stats(qc_server *s, qc_server_stats *out);
 /* Stop the loop (cancelling what is left) and free everything it holds. */
 void qc_server_destroy(qc_server *s);
+
+/* ---- self-test of the bounded device wait ----------------------------------------- */
+
+/* The paper has no counterpart to this call.  Every persistent kernel of the
+ * library synchronises its blocks with a grid barrier whose spin gives up after
+ * a bounded number of polls (about a second at the library's limit), records a
+ * timeout and returns, so that a block that never arrives surfaces as
+ * QC_ERR_TIMEOUT instead of a hung GPU.  This call launches that barrier with
+ * two blocks, one of which leaves without arriving, and a spin limit of
+ * spin_limit polls (1 .. 2^24, about 100 ns each).
+ * Returns QC_ERR_TIMEOUT (with qc_last_error describing it) when the wait gave
+ * up as designed; the context stays usable.  QC_ERR_CUDA if the barrier failed
+ * to notice the missing block, QC_ERR_INVALID_ARG for a bad limit. */
+qc_status qc_selftest_barrier_timeout(qc_ctx *ctx, int64_t spin_limit, void *stream);
 
 /* ---- histogram without device allocation ---------------------------------------- */
 

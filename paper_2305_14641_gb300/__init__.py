@@ -86,6 +86,12 @@ class Context:
     def launch_count(self) -> int:
         return int(self._lib.qc_context_launch_count(self.handle))
 
+    def selftest_barrier_timeout(self, spin_limit: int = 1 << 14, stream=None) -> str:
+        """Run the library's grid barrier with a block that never arrives; returns the
+        status name (QC_ERR_TIMEOUT when the bounded wait gave up as designed)."""
+        st = self._lib.qc_selftest_barrier_timeout(self.handle, int(spin_limit), _stream_handle(stream))
+        return native.STATUS.get(st, str(st))
+
     def bytes_in_use(self) -> int:
         return int(self._lib.qc_context_bytes_in_use(self.handle))
 
@@ -105,15 +111,20 @@ class Context:
 
 
 class Graph:
-    """An undirected, unweighted graph resident on the GPU (int32 CSR).
+    """An unweighted graph resident on the GPU (int32 CSR), undirected unless
+    `directed` (then row v lists the edges v -> u and distances follow them).
 
     row_ptr / col_idx: numpy arrays (host) or CUDA int32 tensors (device).
     """
 
-    def __init__(self, ctx: Context, row_ptr, col_idx, validate: bool = True, stream=None):
+    def __init__(self, ctx: Context, row_ptr, col_idx, validate: bool = True, stream=None,
+                 directed: bool = False):
         self.ctx = ctx
         torch = _torch()
         flags = native.QC_VALIDATE if validate else 0
+        if directed:
+            flags |= native.QC_DIRECTED
+        self.directed = bool(directed)
         if isinstance(row_ptr, torch.Tensor):
             rp = row_ptr.to(device=f"cuda:{ctx.device}", dtype=torch.int32).contiguous()
             ci = col_idx.to(device=f"cuda:{ctx.device}", dtype=torch.int32).contiguous()
@@ -137,7 +148,8 @@ class Graph:
 
     @classmethod
     def from_graph(cls, ctx: Context, g, validate: bool = True, stream=None) -> "Graph":
-        return cls(ctx, g.row_ptr, g.col_idx, validate=validate, stream=stream)
+        return cls(ctx, g.row_ptr, g.col_idx, validate=validate, stream=stream,
+                   directed=getattr(g, "directed", False))
 
     def histogram(self, stream=None):
         """int32 tensor [D+1, n]: hist[d][v] = number of nodes at hop distance d from v."""
@@ -148,6 +160,23 @@ class Graph:
         out = torch.empty((D.value + 1, self.n), dtype=torch.int32, device=f"cuda:{self.ctx.device}")
         self.ctx.check(self.ctx._lib.qc_graph_histogram(self.handle, out.data_ptr(), ctypes.byref(D), s))
         return out
+
+    def set_histogram(self, hist, validate: bool = True, stream=None) -> None:
+        """Install a histogram saved from `histogram()` of this graph ([D+1, n] int32,
+        numpy or CUDA tensor), so later potentials skip the BFS."""
+        torch = _torch()
+        flags = native.QC_VALIDATE if validate else 0
+        if isinstance(hist, torch.Tensor):
+            h = hist.to(device=f"cuda:{self.ctx.device}", dtype=torch.int32).contiguous()
+            flags |= native.QC_PTR_DEVICE
+            ptr = h.data_ptr()
+        else:
+            h = np.ascontiguousarray(hist, dtype=np.int32)
+            ptr = h.ctypes.data
+        if h.ndim != 2 or h.shape[1] != self.n:
+            raise ValueError(f"histogram must be [D+1, {self.n}], got {tuple(h.shape)}")
+        self.ctx.check(self.ctx._lib.qc_graph_set_histogram(self.handle, ptr, int(h.shape[0]) - 1, flags,
+                                                            _stream_handle(stream)))
 
     def potential(self, sigmas: Sequence[float], out=None, stream=None):
         """float64 tensor [S, n]: the potential of every node for every sigma."""

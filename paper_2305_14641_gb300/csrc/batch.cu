@@ -51,7 +51,7 @@ struct CtaGraph {
     const int32_t *col_idx;
     int32_t *labels;
     int32_t n;
-    int32_t pad;
+    int32_t directed;              // row v = out-neighbours: components are the weak ones
     double den;                    // 2 sigma^2
 };
 
@@ -129,7 +129,11 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
             const int a = VL[v];
             for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
                 const int b = VL[ci[e]];
-                if (b < a && atomicMin(L + a, b) > b) changed = true;
+                if (b < a) {
+                    if (atomicMin(L + a, b) > b) changed = true;
+                } else if (G.directed && a < b) {
+                    if (atomicMin(L + b, a) > a) changed = true;
+                }
             }
         }
         if (!__syncthreads_or(changed)) break;
@@ -450,7 +454,7 @@ qc_status qc_cta_launch_async(qc_ctx *ctx, int32_t m, qc_graph *const *graphs, c
         d[i].col_idx = g->col_idx.as<int32_t>();
         d[i].labels = labels[i];
         d[i].n = g->n;
-        d[i].pad = 0;
+        d[i].directed = g->directed ? 1 : 0;
         d[i].den = 2.0 * (sigmas[i] * sigmas[i]);
         qc_weight_table(sigmas[i], L_CAP, tab.data() + (size_t)i * 2 * L_CAP,
                         tab.data() + (size_t)i * 2 * L_CAP + L_CAP);
@@ -556,7 +560,7 @@ qc_status qc_batch_create(qc_ctx *ctx, int32_t n_graphs, qc_graph *const *graphs
             d[i].col_idx = g->col_idx.as<int32_t>();
             d[i].labels = labels_out + label_offsets[k];
             d[i].n = g->n;
-            d[i].pad = 0;
+            d[i].directed = g->directed ? 1 : 0;
             const double s = sigma_per_graph[k];
             d[i].den = 2.0 * (s * s);
             qc_weight_table(s, L_CAP, tab.data() + (size_t)i * 2 * L_CAP,

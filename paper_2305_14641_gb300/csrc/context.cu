@@ -201,6 +201,7 @@ qc_status qc_graph_create(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *ro
     g->ctx = ctx;
     g->n = n;
     g->nnz = nnz;
+    g->directed = (flags & QC_DIRECTED) != 0;
     qc_status st = g->row_ptr.allocate(ctx, sizeof(int32_t) * (size_t)(n + 1), stream);
     if (st == QC_OK) st = g->col_idx.allocate(ctx, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1), stream);
     if (st != QC_OK) {
@@ -217,7 +218,8 @@ qc_status qc_graph_create(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *ro
         return QC_ERR_CUDA;
     }
     if (flags & QC_VALIDATE) {
-        st = qc_validate_csr(ctx, n, nnz, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(), stream);
+        st = qc_validate_csr(ctx, n, nnz, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(), !g->directed,
+                             stream);
         if (st != QC_OK) {
             delete g;
             return st;
@@ -251,6 +253,31 @@ qc_status qc_graph_histogram(qc_graph *g, int32_t *hist_out, int32_t *D_out, voi
                                             sizeof(int32_t) * (size_t)(g->D + 1) * (size_t)g->n,
                                             cudaMemcpyDeviceToDevice, stream));
     QC_CUDA_TRY(g->ctx, cudaStreamSynchronize(stream));
+    return QC_OK;
+}
+
+qc_status qc_graph_set_histogram(qc_graph *g, const int32_t *hist, int32_t D, uint32_t flags, void *stream_) {
+    if (!g || !hist) return QC_ERR_INVALID_ARG;
+    qc_ctx *ctx = g->ctx;
+    if (D < 0 || D >= g->n) {
+        qc_set_error(ctx, "qc_graph_set_histogram: D = %d outside [0, n) for n = %d", D, g->n);
+        return QC_ERR_INVALID_ARG;
+    }
+    cudaStream_t stream = qc_stream(stream_);
+    QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    qc_buffer nb;
+    const size_t bytes = sizeof(int32_t) * (size_t)(D + 1) * (size_t)g->n;
+    QC_TRY(nb.allocate(ctx, bytes, stream));
+    QC_CUDA_TRY(ctx, cudaMemcpyAsync(nb.ptr, hist, bytes,
+                                     (flags & QC_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                     stream));
+    if (flags & QC_VALIDATE)
+        QC_TRY(qc_validate_hist(ctx, g->n, g->nnz, g->row_ptr.as<int32_t>(), nb.as<int32_t>(), D, stream));
+    QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));   // a host source may be freed on return
+    g->hist = std::move(nb);
+    g->hist_rows = D + 1;
+    g->D = D;
+    g->hist_valid = true;
     return QC_OK;
 }
 

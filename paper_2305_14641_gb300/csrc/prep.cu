@@ -8,7 +8,9 @@
 //             (the BFS gives those rows to whole blocks).
 // Sources in another component than v can never reach v: the BFS marks them
 // as already seen in v's row from the start, so a row is complete ("all ones")
-// as soon as v's own component has reached it.
+// as soon as v's own component has reached it.  For a directed graph the
+// components are the weakly connected ones: still a bound on reachability, but
+// a row may then never complete.
 #include "qc_device.cuh"
 #include "qc_internal.h"
 
@@ -21,11 +23,14 @@ namespace {
 //   shortcut: L[v] = L[L[v]] until L[v] is a root (L[L[v]] = L[v]).
 // An iteration in which no hook lowers a label leaves every edge's two ends with
 // the same root label, which is then the smallest id of the component.
+// A directed graph lists each edge in one row only, so there the hook runs in
+// both directions (a < b: L[b] = min(L[b], a)) and the result is the weakly
+// connected components, which bound what any node can reach.
 // ctl: [0] status, [1] iterations run, [2..3] barrier, [8 + it] "a hook changed
 // something in iteration it".
 __global__ void __launch_bounds__(256) cc_persistent(int32_t n, const int32_t *row_ptr,
                                                      const int32_t *col_idx, int32_t *L, int32_t *ctl,
-                                                     int32_t max_iters, int32_t resume) {
+                                                     int32_t max_iters, int32_t resume, int32_t directed) {
     unsigned *bar = reinterpret_cast<unsigned *>(ctl + 2);
     const int lane = threadIdx.x & 31;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -62,7 +67,11 @@ __global__ void __launch_bounds__(256) cc_persistent(int32_t n, const int32_t *r
             const int end = row_ptr[v + 1];
             for (int e = row_ptr[v] + lane; e < end; e += 32) {
                 const int b = VL[col_idx[e]];
-                if (b < a && atomicMin(L + a, b) > b) changed = true;
+                if (b < a) {
+                    if (atomicMin(L + a, b) > b) changed = true;
+                } else if (directed && a < b) {
+                    if (atomicMin(L + b, a) > a) changed = true;
+                }
             }
         }
         if (__syncthreads_or(changed) && threadIdx.x == 0) ctl[8 + it] = 1;
@@ -177,9 +186,9 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
         int32_t resume = 0;
         while (true) {
             QC_CUDA_TRY(ctx, cudaMemsetAsync(ctl.ptr, 0, ctl.bytes, stream));
-            int32_t n_ = n, iters = max_iters;
+            int32_t n_ = n, iters = max_iters, directed = g->directed ? 1 : 0;
             int32_t *L = p.as<int32_t>(), *c = ctl.as<int32_t>();
-            void *args[] = {&n_, (void *)&rp, (void *)&ci, &L, &c, &iters, &resume};
+            void *args[] = {&n_, (void *)&rp, (void *)&ci, &L, &c, &iters, &resume, &directed};
             QC_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)cc_persistent, dim3(blocks), dim3(256),
                                                          args, 0, stream));
             QC_LAUNCHED(ctx);

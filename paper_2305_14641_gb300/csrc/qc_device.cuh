@@ -14,7 +14,8 @@ constexpr unsigned long long BARRIER_SPINS = 1ull << 24;
 // bar[0] counts arrivals, bar[1] is the generation.  The spin is bounded: on
 // expiry the block records ST_TIMEOUT in *status and returns false; every
 // block then leaves at its next barrier.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *status) {
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *status,
+                                             unsigned long long spin_limit = BARRIER_SPINS) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -30,7 +31,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *status) {
         } else {
             unsigned long long spins = 0;
             while (*vgen == gen) {
-                if (++spins > BARRIER_SPINS) {
+                if (++spins > spin_limit) {
                     atomicExch(status, ST_TIMEOUT);
                     ok = 0;
                     break;

@@ -141,6 +141,7 @@ struct qc_graph {
     qc_ctx *ctx = nullptr;
     int32_t n = 0;
     int64_t nnz = 0;
+    bool directed = false;   // row v = out-neighbours (QC_DIRECTED)
     qc_buffer row_ptr;       // int32[n+1]
     qc_buffer col_idx;       // int32[nnz]
     // cached all-source BFS result
@@ -199,7 +200,9 @@ void qc_cta_launch_free(qc_cta_launch *L);
 
 // validate.cu
 qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
-                          const int32_t *col_idx_dev, cudaStream_t stream);
+                          const int32_t *col_idx_dev, bool symmetric, cudaStream_t stream);
+qc_status qc_validate_hist(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
+                           const int32_t *hist_dev, int32_t D, cudaStream_t stream);
 
 static inline cudaStream_t qc_stream(void *s) { return static_cast<cudaStream_t>(s); }
 

@@ -1,5 +1,6 @@
 // CSR validation on the device (QC_VALIDATE): the graph must be the sparse form
-// of a symmetric 0/1 adjacency matrix with an empty diagonal, rows sorted.
+// of a 0/1 adjacency matrix with an empty diagonal, rows sorted, and symmetric
+// unless it is directed.  Also the checks of an installed histogram.
 #include "qc_internal.h"
 
 namespace {
@@ -20,7 +21,8 @@ __global__ void check_row_ptr(int32_t n, int64_t nnz, const int32_t *row_ptr, in
 }
 
 // One warp per row.  Safe to run only after check_row_ptr passed.
-__global__ void check_rows(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t *err) {
+__global__ void check_rows(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, bool symmetric,
+                           int32_t *err) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -32,6 +34,7 @@ __global__ void check_rows(int32_t n, const int32_t *row_ptr, const int32_t *col
             if (u < 0 || u >= n) { bad |= BAD_COLUMN; continue; }
             if (u == v) bad |= BAD_SELF_LOOP;
             if (e > beg && col_idx[e - 1] >= u) bad |= BAD_ORDER;
+            if (!symmetric) continue;
             // symmetric: v must appear in row u (binary search; rows may be unsorted
             // only if BAD_ORDER is also reported)
             int lo = row_ptr[u], hi = row_ptr[u + 1] - 1;
@@ -49,10 +52,65 @@ __global__ void check_rows(int32_t n, const int32_t *row_ptr, const int32_t *col
     if (lane == 0 && bad) atomicOr(err, bad);
 }
 
+enum : int32_t {
+    BAD_H0 = 1,         // h(0, v) != 1
+    BAD_H1 = 2,         // h(1, v) != out-degree
+    BAD_NEGATIVE = 4,
+    BAD_SUM = 8,        // more than n nodes at finite distance
+    LAST_ROW_USED = 16, // some node has h(D, v) > 0 (required)
+};
+
+// One thread per node: the identities every histogram of this graph satisfies.
+__global__ void check_hist(int32_t n, const int32_t *row_ptr, const int32_t *hist, int32_t D, int32_t *err) {
+    int bad = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        long long sum = 0;
+        for (int d = 0; d <= D; ++d) {
+            const int h = hist[(size_t)d * n + v];
+            if (h < 0) bad |= BAD_NEGATIVE;
+            sum += h;
+        }
+        if (hist[v] != 1) bad |= BAD_H0;
+        if (D >= 1 && hist[(size_t)n + v] != row_ptr[v + 1] - row_ptr[v]) bad |= BAD_H1;
+        if (sum > n) bad |= BAD_SUM;
+        if (hist[(size_t)D * n + v] > 0) bad |= LAST_ROW_USED;
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicOr(err, bad);
+}
+
 }  // namespace
 
+qc_status qc_validate_hist(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *hist,
+                           int32_t D, cudaStream_t stream) {
+    if ((nnz == 0) != (D == 0)) {
+        qc_set_error(ctx, "invalid histogram: D = %d for a graph with %lld edges", D, (long long)nnz);
+        return QC_ERR_INVALID_GRAPH;
+    }
+    qc_buffer err;
+    QC_TRY(err.allocate(ctx, sizeof(int32_t), stream));
+    QC_CUDA_TRY(ctx, cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), stream));
+    const int blocks = qc_ceil_div(n, 256) < 4 * ctx->num_sms ? qc_ceil_div(n, 256) : 4 * ctx->num_sms;
+    check_hist<<<blocks, 256, 0, stream>>>(n, row_ptr, hist, D, err.as<int32_t>());
+    QC_LAUNCHED(ctx);
+    qc_pinned pin(ctx);
+    QC_TRY(pin.acquire());
+    int32_t *h = static_cast<int32_t *>(pin.ptr);
+    QC_CUDA_TRY(ctx, cudaMemcpyAsync(h, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    const int32_t e = h[0];
+    if ((e & ~LAST_ROW_USED) || !(e & LAST_ROW_USED)) {
+        qc_set_error(ctx, "invalid histogram (flags 0x%x):%s%s%s%s%s", e, (e & BAD_H0) ? " h(0) != 1;" : "",
+                     (e & BAD_H1) ? " h(1) != degree;" : "", (e & BAD_NEGATIVE) ? " negative count;" : "",
+                     (e & BAD_SUM) ? " more than n nodes;" : "",
+                     (e & LAST_ROW_USED) ? "" : " row D is empty;");
+        return QC_ERR_INVALID_GRAPH;
+    }
+    return QC_OK;
+}
+
 qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
-                          const int32_t *col_idx, cudaStream_t stream) {
+                          const int32_t *col_idx, bool symmetric, cudaStream_t stream) {
     qc_buffer err;
     QC_TRY(err.allocate(ctx, sizeof(int32_t), stream));
     QC_CUDA_TRY(ctx, cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), stream));
@@ -68,7 +126,7 @@ qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *ro
     }
     if (nnz == 0) return QC_OK;
     const int wblocks = qc_ceil_div(n, 8) < 8 * ctx->num_sms ? qc_ceil_div(n, 8) : 8 * ctx->num_sms;
-    check_rows<<<wblocks, 256, 0, stream>>>(n, row_ptr, col_idx, err.as<int32_t>());
+    check_rows<<<wblocks, 256, 0, stream>>>(n, row_ptr, col_idx, symmetric, err.as<int32_t>());
     QC_LAUNCHED(ctx);
     QC_CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
     QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));

@@ -57,6 +57,7 @@ STATUS = {0: "QC_OK", 1: "QC_ERR_INVALID_ARG", 2: "QC_ERR_INVALID_GRAPH", 3: "QC
           8: "QC_ERR_NOT_READY"}
 QC_PTR_DEVICE = 1
 QC_VALIDATE = 2
+QC_DIRECTED = 4
 
 # (name, restype, argtypes) for every entry point of include/qcgraph.h
 SIGNATURES = [
@@ -76,6 +77,8 @@ SIGNATURES = [
     ("qc_graph_num_nodes", ctypes.c_int32, [ctypes.c_void_p]),
     ("qc_graph_num_edges", ctypes.c_int64, [ctypes.c_void_p]),
     ("qc_graph_histogram", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int32_p, ctypes.c_void_p]),
+    ("qc_graph_set_histogram", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32,
+                                              ctypes.c_void_p]),
     ("qc_potential", ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_int32, ctypes.c_void_p,
                                     ctypes.c_void_p]),
     ("qc_potential_adjacency", ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_int32, ctypes.c_double,
@@ -101,6 +104,7 @@ SIGNATURES = [
     ("qc_server_cancel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     ("qc_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qc_server_stats)]),
     ("qc_server_destroy", None, [ctypes.c_void_p]),
+    ("qc_selftest_barrier_timeout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     ("qc_histogram_static_scratch", ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                                    c_int32_p, ctypes.c_void_p]),

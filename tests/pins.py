@@ -359,3 +359,56 @@ def check_adjacency_mode(orc):
 
 
 ALL_CHECKS.append(check_adjacency_mode)
+
+
+def check_directed(orc):
+    """Directed graphs (row v = arcs v -> u).  BFS distances equal Floyd-Warshall's
+    and scipy's directed shortest paths; node i's histogram counts the nodes i
+    reaches.  On the directed cycle C_n every node sees each distance 0..n-1 once,
+    so all potentials equal one 50-digit sum.  On the directed path node i reaches
+    n-1-i nodes at distances 1..n-1-i, V falls along the arcs, and every node
+    descends to the last node.  Descent on random digraphs equals brute force over
+    out-neighbours."""
+    for t in range(8):
+        g = gg.rng(97, t)
+        n = int(g.integers(2, 40))
+        graph = gg.directed_erdos_renyi(n, float(g.uniform(0.03, 0.3)), g)
+        fw = floyd_warshall(graph)
+        sd = shortest_path(adjacency(graph), method="D", directed=True, unweighted=True)
+        assert np.array_equal(fw, sd), graph.name
+        h = orc.histograms(graph)
+        for s in range(n):
+            d = orc.bfs(graph, s).astype(np.float64)
+            d[d < 0] = np.inf
+            assert np.array_equal(d, fw[s]), (graph.name, s)
+            row = fw[s][np.isfinite(fw[s])].astype(np.int64)
+            assert np.array_equal(h[s], np.bincount(row, minlength=h.shape[1])), (graph.name, s)
+        for sigma in (0.7, 1.6):
+            V = orc.potential(h, sigma)
+            labels, _ = orc.find_centers(orc.ggd_parent(graph, V)[0])
+            assert np.array_equal(labels, descend_brute(graph, V)), (graph.name, sigma)
+    for n in (2, 5, 9):
+        cyc = gg.directed_cycle(n)
+        h = orc.histograms(cyc)
+        assert np.array_equal(h, np.ones((n, n), dtype=np.int32))
+        for sigma in (0.5, 1.3):
+            V = orc.potential(h, sigma)
+            assert all(close(x, exact_potential_from_distances(range(n), sigma)) for x in V)
+            labels, k = orc.find_centers(orc.ggd_parent(cyc, V)[0])
+            assert k == n and np.array_equal(labels, np.arange(n))     # equal V: nobody moves
+    n = 7
+    pth = gg.directed_path(n)
+    h = orc.histograms(pth)
+    for i in range(n):
+        assert np.array_equal(h[i], np.r_[np.ones(n - i, np.int32), np.zeros(i, np.int32)])
+    for sigma in (0.6, 1.5, 2.0):
+        V = orc.potential(h, sigma)
+        for i in range(n):
+            assert close(V[i], exact_potential_from_distances(range(n - i), sigma)) or (i == n - 1 and V[i] == 0)
+        if sigma >= 1.5:    # (at sigma = 0.6 the far terms are below one ulp of the sums)
+            assert np.all(np.diff(V) < 0)
+            labels, k = orc.find_centers(orc.ggd_parent(pth, V)[0])
+            assert k == 1 and np.all(labels == n - 1)
+
+
+ALL_CHECKS.append(check_directed)

@@ -155,3 +155,11 @@ def test_server_rejects_invalid(qc):
         with pytest.raises(qc.QCError) as e:
             srv.submit(np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), -1.0)
         assert e.value.status_name == "QC_ERR_INVALID_ARG"
+
+
+def test_batch_directed(qc, ctx):
+    """Directed graphs in a batch: weak components, out-neighbour descent."""
+    g = gg.rng(44)
+    graphs = [gg.directed_erdos_renyi(int(n), 4.0 / n, g) for n in (40, 200, 700, 1500)] + \
+        [gg.directed_cycle(100), gg.directed_path(90), gg.directed_planted_partition(1200, 5, 0.03, 0.002, g)]
+    check_batch(qc, ctx, graphs, [0.8, 1.2, 1.7, 2.2, 1.0, 1.5, 0.9])

@@ -211,6 +211,18 @@ def test_budget(qc):
         assert c.bytes_in_use() == 0
 
 
+def test_bounded_wait_gives_up(qc, ctx):
+    """A grid barrier with a block that never arrives ends in QC_ERR_TIMEOUT after
+    its bounded spin; the context then still clusters exactly."""
+    import time
+    t0 = time.perf_counter()
+    assert ctx.selftest_barrier_timeout(1 << 14) == "QC_ERR_TIMEOUT"
+    assert time.perf_counter() - t0 < 30.0
+    assert ctx.selftest_barrier_timeout(0) == "QC_ERR_INVALID_ARG"
+    graph, sigmas = gg.config1()
+    assert_solution_matches(qc, ctx, graph, sigmas)
+
+
 def test_descent_on_given_potentials(qc, ctx):
     """GGD and roots alone, on seeded potentials with negatives, many exact ties,
     and -0.0 next to +0.0 (equal under IEEE comparison)."""
@@ -260,3 +272,61 @@ def test_adjacency_mode(qc, ctx, M):
         with pytest.raises(qc.QCError):
             G.potential_adjacency(sigmas, 0.5)
         G.close()
+
+
+@pytest.mark.parametrize("n", [2, 63, 64, 65, 129, 1000, 3001])
+def test_directed(qc, ctx, n):
+    """Directed graphs (rows are out-neighbours): histograms count the nodes each
+    node reaches; potentials and labels as the oracle's, which follows the arcs."""
+    g = gg.rng(31, n)
+    for p in (1.5 / n, 6.0 / n, 0.2):
+        graph = gg.directed_erdos_renyi(n, min(p, 0.9), g)
+        assert_solution_matches(qc, ctx, graph, [0.7, 1.9])
+
+
+def test_directed_structured_and_chunked(qc, ctx, monkeypatch):
+    for graph in [gg.directed_cycle(130), gg.directed_path(200),
+                  gg.directed_planted_partition(1500, 6, 0.02, 0.001, gg.rng(32))]:
+        assert_solution_matches(qc, ctx, graph, [0.8, 2.5])
+    monkeypatch.setenv("QCGRAPH_CHUNK_WORDS", "3")
+    assert_solution_matches(qc, ctx, gg.directed_planted_partition(900, 4, 0.03, 0.002, gg.rng(33)), [1.1])
+
+
+def test_directed_validation(qc, ctx):
+    graph = gg.directed_erdos_renyi(300, 0.02, gg.rng(34))
+    with pytest.raises(qc.QCError) as e:
+        qc.Graph(ctx, graph.row_ptr, graph.col_idx, validate=True, directed=False)
+    assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
+    qc.Graph(ctx, graph.row_ptr, graph.col_idx, validate=True, directed=True).close()
+
+
+def test_histogram_checkpoint(qc, ctx):
+    """A saved histogram, installed into a fresh graph (from host or device memory),
+    serves new sigma values without a BFS; a corrupted one is rejected."""
+    graph = gg.planted_partition(2500, 10, 0.02, 0.001, gg.rng(35))
+    g1 = qc.Graph.from_graph(ctx, graph)
+    saved = g1.histogram().cpu().numpy()
+    g1.close()
+    ref = oracle.solve(graph, [0.9, 3.0])
+    for source in ("host", "device"):
+        g2 = qc.Graph.from_graph(ctx, graph)
+        g2.set_histogram(saved if source == "host" else torch.tensor(saved, device="cuda"))
+        launches = ctx.launch_count()
+        V = g2.potential([0.9, 3.0])
+        labels, counts = g2.ggd_labels(V)
+        assert np.array_equal(V.cpu().numpy(), ref.V)
+        assert np.array_equal(labels.cpu().numpy(), ref.labels) and counts == ref.n_clusters
+        assert ctx.launch_count() - launches <= 6            # potential + descent only: no preparation, no BFS
+        g2.close()
+    g3 = qc.Graph.from_graph(ctx, graph)
+    bad = saved.copy()
+    bad[1, 7] += 1
+    with pytest.raises(qc.QCError) as e:
+        g3.set_histogram(bad)
+    assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
+    bad = saved.copy()
+    bad[2, 0] = -1
+    with pytest.raises(qc.QCError) as e:
+        g3.set_histogram(bad)
+    assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
+    g3.close()
