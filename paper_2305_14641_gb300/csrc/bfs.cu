@@ -70,6 +70,7 @@ struct BfsParams {
     const int32_t *row_ptr;
     const int32_t *col_idx;
     const int32_t *order;       // nodes, heaviest degree bucket first; order[n] = heavy count
+    const int4 *info;           // {node, row start, row end, 0} per order position
     const int32_t *comp;        // component (smallest node id) of each node
     const int32_t *wcomp;       // component shared by a whole source word, or -1
     ulonglong2 *buf[2];         // vis_l in buf[l & 1], [n][R]
@@ -258,11 +259,12 @@ __device__ void heavy_items(const BfsParams &p, const int level, bool &any_new, 
         __syncthreads();
         const int it = grab;
         if (it >= items) break;
+        const int oi = it / p.T;
+        const int4 inf = p.info[oi];
         const int sv = p.sat[it];
         if (sv <= level - 2) continue;
-        const int oi = it / p.T;
         const int t = it - oi * p.T;
-        const int v = p.order[oi];
+        const int v = inf.x;
         const int q = t * 32 + lane;
         const bool qok = q < p.R;
         ulonglong2 *orow = vout + (size_t)v * p.R;
@@ -271,7 +273,7 @@ __device__ void heavy_items(const BfsParams &p, const int level, bool &any_new, 
             continue;
         }
         const ulonglong2 own = qok ? vin[(size_t)v * p.R + q] : make_ulonglong2(ONES, ONES);
-        const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
+        const int beg = inf.y, end = inf.z;
         red[wib][lane] = gather_or<32>(p, vin, beg + 32 * wib, end, 32 * WARPS, q, qok, own);
         __syncthreads();
         if (wib == 0) {
@@ -312,14 +314,16 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
         const int pos = base + lane;
         const bool has = lane < GRAB && pos < count;
         const int it = has ? (from_list ? src[pos] : first + pos) : 0;
+        const int oi = it / p.T;
+        // the item's saturation level and its node's row come in two independent loads
+        const int4 inf = has ? p.info[oi] : make_int4(0, 0, 0, 0);
         const int sv = has ? p.sat[it] : 0;
         const bool ones = has && sv == level - 1;
         const bool pull = has && sv > level - 1;
-        const int oi = it / p.T;
-        const int v_l = (ones || pull) ? p.order[oi] : 0;
+        const int v_l = inf.x;
         const int t_l = it - oi * p.T;
-        const int beg_l = pull ? p.row_ptr[v_l] : 0;
-        const int end_l = pull ? p.row_ptr[v_l + 1] : 0;
+        const int beg_l = pull ? inf.y : 0;
+        const int end_l = pull ? inf.z : 0;
         unsigned mask = __ballot_sync(FULL, ones);
         while (mask) {
             const int b = __ffs(mask) - 1;
@@ -530,6 +534,7 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
             p.row_ptr = g->row_ptr.as<int32_t>();
             p.col_idx = g->col_idx.as<int32_t>();
             p.order = g->order.as<int32_t>();
+            p.info = g->oinfo.as<int4>();
             p.comp = g->comp.as<int32_t>();
             p.wcomp = g->wcomp.as<int32_t>();
             p.buf[0] = visB.as<ulonglong2>();

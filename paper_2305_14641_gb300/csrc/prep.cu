@@ -5,7 +5,9 @@
 //   order[i]  nodes by decreasing degree bucket (floor(log2(deg + 1))), so that
 //             dealing them round-robin to warps spreads the heavy rows;
 //             order[n] = how many lead the order with degree >= 2^QC_HEAVY_BUCKET - 1
-//             (the BFS gives those rows to whole blocks).
+//             (the BFS gives those rows to whole blocks);
+//   oinfo[i]  {order[i], row start, row end, 0}, so that a BFS item's node and
+//             row arrive in one load instead of two dependent ones.
 // Sources in another component than v can never reach v: the BFS marks them
 // as already seen in v's row from the start, so a row is complete ("all ones")
 // as soon as v's own component has reached it.  For a directed graph the
@@ -137,6 +139,15 @@ __global__ void bucket_scatter(int32_t n, const int32_t *row_ptr, int32_t *curso
         order[atomicAdd(&cursor[degree_bucket(row_ptr[v + 1] - row_ptr[v])], 1)] = v;
 }
 
+// info[i] = {order[i], its row start, its row end, 0}: one 16-byte load gives a
+// BFS item everything it needs before it reads the neighbour ids.
+__global__ void order_info(int32_t n, const int32_t *row_ptr, const int32_t *order, int4 *info) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int v = order[i];
+        info[i] = make_int4(v, row_ptr[v], row_ptr[v + 1], 0);
+    }
+}
+
 __global__ void first_rows(int32_t n, const int32_t *row_ptr, int32_t *hist) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         hist[v] = 1;
@@ -162,6 +173,7 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
     QC_TRY(g->comp.allocate(ctx, sizeof(int32_t) * (size_t)n, stream));
     QC_TRY(g->wcomp.allocate(ctx, sizeof(int32_t) * (size_t)W, stream));
     QC_TRY(g->order.allocate(ctx, sizeof(int32_t) * (size_t)(n + 1), stream));
+    QC_TRY(g->oinfo.allocate(ctx, sizeof(int4) * (size_t)n, stream));
     qc_buffer p, bins;
     QC_TRY(p.allocate(ctx, sizeof(int32_t) * (size_t)n, stream));
     QC_TRY(bins.allocate(ctx, sizeof(int32_t) * 64, stream));
@@ -214,6 +226,8 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
                                       g->order.as<int32_t>() + n);
     QC_LAUNCHED(ctx);
     bucket_scatter<<<nb, tb, 0, stream>>>(n, rp, bins.as<int32_t>() + 32, g->order.as<int32_t>());
+    QC_LAUNCHED(ctx);
+    order_info<<<nb, tb, 0, stream>>>(n, rp, g->order.as<int32_t>(), g->oinfo.as<int4>());
     QC_LAUNCHED(ctx);
     g->prepared = true;
     return QC_OK;

@@ -154,6 +154,7 @@ struct qc_graph {
     qc_buffer comp;          // int32[n] component = smallest node id in it
     qc_buffer wcomp;         // int32[W] component of a whole 64-source word, or -1
     qc_buffer order;         // int32[n] nodes, heaviest degree bucket first
+    qc_buffer oinfo;         // int4[n]: {node, row start, row end, 0} at each order position
 };
 
 // prep.cu
