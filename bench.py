@@ -51,6 +51,12 @@ PROFILE = os.path.join(ROOT, "profiles", "bfs_persistent_dcsbm16384.md")
 SINGLE = {
     "dcsbm16384": {"make": lambda: gg.config2(), "desc": WORKLOAD, "profile": PROFILE,
                    "cpu_sample_nodes": None, "steps": 200},
+    "directed16384": {"make": lambda: (gg.directed_planted_partition(16384, 32, 16.0 * 0.9 / 511,
+                                                                     16.0 * 0.1 / (16384 - 512), gg.rng(5, 1),
+                                                                     name="dpp-16384"), gg.config2_sigmas()),
+                      "desc": ("directed16384: directed planted partition, N=16384, 32 blocks of 512, "
+                               "mean out-degree 16, mixing 0.1, seed 5; the 16-value sigma sweep"),
+                      "profile": None, "cpu_sample_nodes": None, "steps": 200},
     "sbm262144": {"make": lambda: gg.config3(),
                   "desc": ("sbm-262144: SBM, N=262144, 256 equal communities of 1024, mean degree 20, "
                            "mixing 0.15, seed 2; sigma 1.5"),
@@ -94,7 +100,8 @@ def whole_job_rate(units_per_step: float, steps: int, world: int, max_total_ms: 
 
 
 def gteps_edges(graph) -> float:
-    """sum over sources of the undirected edges in the source's component."""
+    """sum over sources of the undirected edges in the source's component (for a
+    directed graph: the arcs of its weakly connected component, an upper bound)."""
     from scipy.sparse import csr_matrix
     from scipy.sparse.csgraph import connected_components
     n = graph.n
@@ -102,7 +109,7 @@ def gteps_edges(graph) -> float:
     _, comp = connected_components(a, directed=False)
     size = np.bincount(comp)
     rows = np.repeat(np.arange(n), graph.degrees())
-    edges = np.bincount(comp[rows], minlength=len(size)) / 2.0
+    edges = np.bincount(comp[rows], minlength=len(size)) / (1.0 if graph.directed else 2.0)
     return float((size * edges).sum())
 
 
@@ -321,7 +328,7 @@ def bench_ours(args, graph, sigmas, spec):
     d2h = lab_h.numel() * 4
 
     def e2e_step():
-        gg_ = qc.Graph(ctx, rp_h.numpy(), ci_h.numpy(), validate=True)
+        gg_ = qc.Graph(ctx, rp_h.numpy(), ci_h.numpy(), validate=True, directed=graph.directed)
         _, lab_d, counts = gg_.solve(sigmas, labels_out=labels, counts=False)
         lab_h.copy_(lab_d, non_blocking=True)
         torch.cuda.current_stream().synchronize()
@@ -541,6 +548,149 @@ def bench_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def _device_steps(step, steps, flush, stream):
+    """Mean CUDA-event milliseconds of `step` over `steps` runs, L2 flushed before each."""
+    import torch
+    times = []
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.mean(times))
+
+
+def bench_adjacency(args):
+    """The adjacency-distance mode (d = 0, 1 or M) on the dcsbm-16384 graph: 16 potentials,
+    descent and roots per step; no BFS.  Also the potential kernel alone against HBM."""
+    import torch
+    import paper_2305_14641_gb300 as qc
+    graph, sigmas = gg.config2()
+    ctx = qc.Context(0)
+    g = qc.Graph.from_graph(ctx, graph)
+    S, n = len(sigmas), graph.n
+    V = torch.empty((S, n), dtype=torch.float64, device="cuda")
+    lab = torch.empty((S, n), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g.potential_adjacency(sigmas, 2.0, out=V)
+        g.ggd_labels(V, out=lab, counts=False)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    with ClockSampler(0) as clocks:
+        ms = _device_steps(step, args.steps, flush, stream)
+    launches = ctx.launch_count() - launches0
+    pot_ms = _device_steps(lambda: g.potential_adjacency(sigmas, 2.0, out=V), args.steps, flush, stream)
+    peak, peak_kind = measured_peak_gbs()
+    pot_bytes = 4.0 * (n + 1) + 8.0 * n * S
+    line = {"metric": METRIC, "workload": "adjacency16384: " + WORKLOAD + "; distance 0 / 1 / M = 2",
+            "value": S / (ms / 1000.0), "unit": METRIC, "ms_per_step": ms, "steps": args.steps,
+            "gpu_launches": launches, "clocks": clocks.summary(),
+            "potential_kernel": {"ms": pot_ms, "bytes": pot_bytes,
+                                 "achieved_gbs": pot_bytes / (pot_ms / 1000.0) / 1e9, "peak": peak,
+                                 "peak_kind": peak_kind,
+                                 "note": "launch-bound: 2.2 MB per launch; the event span includes launch latency"}}
+    print(json.dumps(line), flush=True)
+    g.close()
+    ctx.close()
+
+
+def bench_fig3(args):
+    """Fully-connected graphs of growing n (the workload of the paper's GPU-vs-CPU figure):
+    time per clustering (sigma = 1) on the GPU, hop and adjacency distance, and the oracle
+    on the host cores (adjacency mode whole; hop mode from 32 sampled sources, scaled)."""
+    import torch
+    import oracle
+    import paper_2305_14641_gb300 as qc
+    oracle.build()
+    threads = oracle.default_threads()
+    ctx = qc.Context(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    for n in (512, 1024, 2048, 4096, 8192):
+        graph = gg.complete(n)
+        g = qc.Graph.from_graph(ctx, graph, validate=False)
+        V = torch.empty((1, n), dtype=torch.float64, device="cuda")
+        lab = torch.empty((1, n), dtype=torch.int32, device="cuda")
+
+        def hop():
+            g.drop_histogram()
+            g.solve([1.0], V_out=V, labels_out=lab, counts=False)
+
+        def adj():
+            g.potential_adjacency([1.0], 2.0, out=V)
+            g.ggd_labels(V, out=lab, counts=False)
+
+        for f in (hop, adj):
+            for _ in range(3):
+                f()
+        torch.cuda.synchronize()
+        steps = max(3, min(args.steps, 20))
+        hop_ms = _device_steps(hop, steps, flush, stream)
+        adj_ms = _device_steps(adj, steps, flush, stream)
+        t0 = time.perf_counter()
+        Va = oracle.potential_adjacency(graph, 1.0, 2.0)
+        oracle.find_centers(oracle.ggd_parent(graph, Va)[0])
+        cpu_adj = 1000.0 * (time.perf_counter() - t0)
+        cpu_hop = 1000.0 * run_cpu_oracle(graph, [1.0], threads, 32)
+        rows.append({"n": n, "directed_edges": graph.nnz, "gpu_hop_ms": hop_ms, "gpu_adjacency_ms": adj_ms,
+                     "cpu_hop_ms": cpu_hop, "cpu_adjacency_ms": cpu_adj})
+        g.close()
+    print(json.dumps({"workload": "fig3: complete graphs K_n, sigma 1, one clustering per step", "cpu_cores": threads,
+                      "rows": rows}), flush=True)
+    ctx.close()
+
+
+# (nodes, undirected edges, classes) the paper reports for its datasets; the graphs
+# below are planted partitions of those shapes, not the datasets
+QUALITY_SHAPES = {"cora-shaped": (2708, 5278, 7), "citeseer-shaped": (3327, 4676, 6),
+                  "wiki-shaped": (2405, 12761, 17), "cora-ml-shaped": (2995, 8158, 7),
+                  "karate-shaped": (34, 78, 2)}
+
+
+def bench_quality(args):
+    """Quality against the planted communities over the 16-value sigma sweep (the
+    analogue of the paper's sigma-sensitivity figure on synthetic stand-ins):
+    modularity, ARI, FMI, NMI and the number of clusters per sigma."""
+    import torch
+    import paper_2305_14641_gb300 as qc
+    from paper_2305_14641_gb300 import metrics
+    sigmas = gg.config2_sigmas()
+    ctx = qc.Context(0)
+    out = {}
+    for name, (n, m, k) in QUALITY_SHAPES.items():
+        graph = gg.sbm_mean_degree(n, k, 2.0 * m / n, 0.2, gg.rng(6, n), name=name)
+        g = qc.Graph.from_graph(ctx, graph)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, labels, counts = g.solve(sigmas)
+        labels = labels.cpu().numpy()
+        secs = time.perf_counter() - t0
+        curve = []
+        for s, lab, c in zip(sigmas, labels, counts):
+            curve.append({"sigma": round(s, 4), "clusters": int(c),
+                          "modularity": metrics.modularity(graph.row_ptr, graph.col_idx, lab),
+                          "ari": metrics.adjusted_rand_index(graph.block, lab),
+                          "fmi": metrics.fowlkes_mallows(graph.block, lab),
+                          "nmi": metrics.normalized_mutual_info(graph.block, lab)})
+        best = max(curve, key=lambda r: r["nmi"])
+        out[name] = {"n": n, "edges": graph.nnz // 2, "planted": k, "solve_ms": 1000.0 * secs,
+                     "best_by_nmi": best, "curve": curve}
+        g.close()
+    print(json.dumps({"workload": "quality: planted partitions (mixing 0.2) of the paper's dataset shapes; "
+                                  "16 sigma values 0.5-4.0", "graphs": out}), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -549,7 +699,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["dcsbm16384", "sbm262144", "batch4096", "serve"],
+    ap.add_argument("--workload", choices=["dcsbm16384", "sbm262144", "directed16384", "batch4096", "serve",
+                                           "adjacency16384", "fig3", "quality"],
                     default="dcsbm16384")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--plain-graphs", type=int, default=512)
@@ -563,6 +714,12 @@ def main():
         return bench_batch(args)
     if args.workload == "serve":
         return bench_serve(args)
+    if args.workload == "adjacency16384":
+        return bench_adjacency(args)
+    if args.workload == "fig3":
+        return bench_fig3(args)
+    if args.workload == "quality":
+        return bench_quality(args)
     spec = SINGLE[args.workload]
     graph, sigmas = spec["make"]()
     if args.impl == "reference":
