@@ -30,7 +30,7 @@ __all__ = [
     "sbm_mean_degree", "dcsbm", "complete", "path", "star", "two_cliques_bridge",
     "erdos_renyi", "relabel", "config1", "config2", "config3", "config4_batch",
     "config5_requests", "config2_sigmas", "Request", "csr_from_arcs", "directed_cycle",
-    "directed_path", "directed_erdos_renyi", "directed_planted_partition",
+    "directed_path", "directed_erdos_renyi", "directed_planted_partition", "edge_weights",
 ]
 
 
@@ -315,6 +315,22 @@ def directed_planted_partition(n: int, k: int, p_in: float, p_out: float, g: np.
     rp, ci = csr_from_arcs(n, np.concatenate(arcs_i), np.concatenate(arcs_j))
     return Graph(n, rp, ci, name=name or f"dpp-{n}", block=a.block, directed=True,
                  meta={"k": k, "p_in": p_in, "p_out": p_out})
+
+
+def edge_weights(graph: Graph, lo: float, hi: float, g: np.random.Generator) -> np.ndarray:
+    """Positive weights per CSR entry, drawn uniformly from [lo, hi); an undirected
+    graph gets one draw per edge, stored in both of its rows."""
+    if graph.directed:
+        return g.uniform(lo, hi, size=graph.nnz)
+    rows = np.repeat(np.arange(graph.n, dtype=np.int64), graph.degrees())
+    cols = graph.col_idx.astype(np.int64)
+    key = rows * graph.n + cols               # ascending: rows sorted, columns sorted in a row
+    lower = rows < cols
+    w = np.empty(graph.nnz)
+    w[lower] = g.uniform(lo, hi, size=int(lower.sum()))
+    mirror = np.searchsorted(key, cols * graph.n + rows)
+    w[~lower] = w[mirror[~lower]]
+    return w
 
 
 def relabel(graph: Graph, perm: np.ndarray) -> Graph:

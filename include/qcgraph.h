@@ -146,6 +146,17 @@ int64_t qc_graph_num_edges(const qc_graph *g);
  * Errors: QC_ERR_INVALID_ARG, QC_ERR_BUDGET, QC_ERR_OOM, QC_ERR_CUDA. */
 qc_status qc_graph_histogram(qc_graph *g, int32_t *hist_out, int32_t *D_out, void *stream);
 
+/* Edge weights for the weighted reading of Section 3.1 (an edge's distance is
+ * its weight; between any two nodes, the length of the lightest path, summed
+ * hop by hop in binary64).  w: double[nnz] aligned with col_idx (w[e] is the
+ * weight of the edge in position e), host memory or (QC_PTR_DEVICE) device
+ * memory; the library keeps a copy with the graph.  With QC_VALIDATE the
+ * weights must be finite and > 0, and equal in both rows of an undirected edge.
+ * The weights serve qc_potential_weighted only; the hop-distance calls ignore
+ * them.  Errors: QC_ERR_INVALID_ARG, QC_ERR_INVALID_GRAPH, QC_ERR_BUDGET,
+ * QC_ERR_OOM, QC_ERR_CUDA. */
+qc_status qc_graph_set_weights(qc_graph *g, const double *w, uint32_t flags, void *stream);
+
 /* Install a histogram computed earlier (qc_graph_histogram of the same graph,
  * saved and reloaded), so that potentials for new sigma values need no BFS: the
  * checkpoint of a sigma sweep.  hist: int32[(D+1) * n], level-major as
@@ -187,6 +198,20 @@ qc_status qc_potential_adjacency(qc_graph *g, const double *sigmas, int32_t n_si
  * Errors: QC_ERR_INVALID_ARG, QC_ERR_BUDGET, QC_ERR_OOM, QC_ERR_CUDA. */
 qc_status qc_ggd_labels(qc_graph *g, const double *V, int32_t n_sigma, int32_t *labels_out,
                         int32_t *n_clusters_out, void *stream);
+
+/* Algorithm 1 over weighted distances (qc_graph_set_weights first): for every
+ * node i and sigma, V = (sum_j d^2 e^{-d^2/2sigma^2} / sum_j e^{-d^2/2sigma^2}) /
+ * (2 sigma^2) with d = dist(i, j) the lightest-path length from i (along arcs
+ * for a directed graph), j over the nodes i reaches, i itself included.  All-
+ * source shortest paths run on the device in blocks of sources; the sums use
+ * binary64 with the device's exp, so V agrees with a sequential host
+ * evaluation to rounding (relative 1e-13 or better) and is the same on every
+ * run.  V_out: device double[n_sigma * n].  Descent: qc_ggd_labels on V_out.
+ * Errors: QC_ERR_INVALID_ARG (no weights, bad sigma), QC_ERR_BUDGET,
+ * QC_ERR_OOM, QC_ERR_CUDA (including weights that let lengths fall without
+ * end), QC_ERR_TIMEOUT. */
+qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
+                                void *stream);
 
 /* Algorithm 4 in one call: qc_potential then qc_ggd_labels.  V_out may be NULL
  * (the potentials then live in library scratch).  Same arguments and errors as

@@ -16,6 +16,11 @@ Per function, the passage it follows:
   * ``solve``          Algorithm 4: potentials for every node, then GGD labels
   * ``potential_adjacency``  Section 3.1 read literally: distance 1 on an edge,
                        M (above every weight) between non-adjacent nodes
+  * ``dijkstra``       Section 3.1 with edge weights: shortest weighted path
+                       lengths from one node (Dijkstra, binary heap)
+  * ``potential_weighted``  Algorithm 1 over those lengths, pair by pair
+Directed graphs (rows = arcs i -> j) need nothing special: every function
+follows the rows, so distances run along the arcs.
 """
 from __future__ import annotations
 
@@ -70,6 +75,11 @@ def _bind(lib):
     lib.qco_find_centers.argtypes = [ctypes.c_int32, _i32p, _i32p]
     lib.qco_potential_adjacency.restype = None
     lib.qco_potential_adjacency.argtypes = [ctypes.c_int32, _i32p, ctypes.c_double, ctypes.c_double, _f64p]
+    lib.qco_dijkstra.restype = ctypes.c_int
+    lib.qco_dijkstra.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, ctypes.c_int32, _f64p]
+    lib.qco_potential_weighted.restype = ctypes.c_int
+    lib.qco_potential_weighted.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, ctypes.c_int32, _f64p,
+                                           ctypes.c_int]
     return lib
 
 
@@ -144,6 +154,25 @@ class Oracle:
         self._lib.qco_potential_adjacency(graph.n, rp, float(M), float(sigma), V)
         return V
 
+    def dijkstra(self, graph, weights, src: int) -> np.ndarray:
+        """Weighted shortest-path lengths from src (+inf where unreachable)."""
+        rp, ci = _csr(graph)
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        dist = np.empty(graph.n, dtype=np.float64)
+        if self._lib.qco_dijkstra(graph.n, rp, ci, w, int(src), dist) != 0:
+            raise MemoryError("oracle Dijkstra scratch allocation failed")
+        return dist
+
+    def potential_weighted(self, graph, weights, sigmas, threads: int = 1) -> np.ndarray:
+        """V [S, n] over weighted shortest-path distances, summed pair by pair."""
+        rp, ci = _csr(graph)
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        sig = np.ascontiguousarray(np.atleast_1d(sigmas), dtype=np.float64)
+        V = np.empty((len(sig), graph.n), dtype=np.float64)
+        if self._lib.qco_potential_weighted(graph.n, rp, ci, w, sig, len(sig), V, int(threads)) != 0:
+            raise MemoryError("oracle weighted potential scratch allocation failed")
+        return V
+
     def ggd_parent(self, graph, V: np.ndarray) -> tuple[np.ndarray, int]:
         """(parent, number of index-dependent ties)."""
         rp, ci = _csr(graph)
@@ -208,6 +237,14 @@ def potential_literal(graph, node, sigma):
 
 def potential_adjacency(graph, sigma, M=2.0):
     return default().potential_adjacency(graph, sigma, M)
+
+
+def dijkstra(graph, weights, src):
+    return default().dijkstra(graph, weights, src)
+
+
+def potential_weighted(graph, weights, sigmas, threads=1):
+    return default().potential_weighted(graph, weights, sigmas, threads)
 
 
 def ggd_parent(graph, V):

@@ -5,7 +5,9 @@
  * benchmark's CPU-baseline leg are the only callers.  The CUDA library never
  * links, loads or calls this file, and this file shares no code with it.
  *
- * What it computes, for one undirected unweighted graph in CSR form:
+ * What it computes, for one unweighted graph in CSR form (undirected, or
+ * directed with row i holding the arcs i -> j; every step follows the rows),
+ * and, in part 7, for a graph with positive edge weights:
  *   1. hop distances from a source by a FIFO-queue BFS (Section 3.1: the
  *      distance between nodes, read as the number of edges on a shortest
  *      path; an unreachable pair has infinite distance);
@@ -270,4 +272,132 @@ void qco_potential_adjacency(int32_t n, const int32_t *row_ptr, double M, double
         }
         V[i] = (sum1 / sum2) / (2.0 * (sigma * sigma));
     }
+}
+
+/* ---- 7. weighted graphs (Section 3.1: an edge's distance is its weight) --- */
+
+/* Shortest-path lengths from src over positive edge weights by Dijkstra's
+ * algorithm with a binary heap.  A path's length is accumulated hop by hop in
+ * path order, dist[v] = dist[u] + w(u, v) in binary64, and the smallest such
+ * value is kept; unreachable nodes get +inf.  Returns 0, or -2 if scratch
+ * could not be allocated. */
+int qco_dijkstra(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const double *w,
+                 int32_t src, double *dist)
+{
+    /* heap of (key, node) with lazy deletion: at most nnz + 1 entries */
+    int64_t cap = (int64_t)row_ptr[n] + 1;
+    double *hk = malloc(sizeof(double) * (size_t)cap);
+    int32_t *hv = malloc(sizeof(int32_t) * (size_t)cap);
+    char *done = calloc((size_t)n, 1);
+    if (!hk || !hv || !done) {
+        free(hk); free(hv); free(done);
+        return -2;
+    }
+    for (int32_t v = 0; v < n; ++v) dist[v] = INFINITY;
+    int64_t size = 0;
+    dist[src] = 0.0;
+    hk[0] = 0.0; hv[0] = src; size = 1;
+    while (size > 0) {
+        double k = hk[0];
+        int32_t u = hv[0];
+        /* pop: move the last entry to the top and sift it down */
+        --size;
+        if (size > 0) {
+            double lk = hk[size];
+            int32_t lv = hv[size];
+            int64_t i = 0;
+            for (;;) {
+                int64_t c = 2 * i + 1;
+                if (c >= size) break;
+                if (c + 1 < size && hk[c + 1] < hk[c]) ++c;
+                if (!(hk[c] < lk)) break;
+                hk[i] = hk[c]; hv[i] = hv[c];
+                i = c;
+            }
+            hk[i] = lk; hv[i] = lv;
+        }
+        if (done[u] || k > dist[u]) continue;
+        done[u] = 1;
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            int32_t v = col_idx[e];
+            double nd = dist[u] + w[e];
+            if (nd < dist[v]) {
+                dist[v] = nd;
+                /* push and sift up */
+                int64_t i = size++;
+                while (i > 0) {
+                    int64_t p = (i - 1) / 2;
+                    if (!(nd < hk[p])) break;
+                    hk[i] = hk[p]; hv[i] = hv[p];
+                    i = p;
+                }
+                hk[i] = nd; hv[i] = v;
+            }
+        }
+    }
+    free(hk); free(hv); free(done);
+    return 0;
+}
+
+/* Algorithm 1 with weighted shortest-path distances: for node i and each
+ * sigma, sum1 = sum_j d^2 exp(-d^2 / (2 sigma^2)) and sum2 = sum_j exp(...) over
+ * every j in ascending order (unreachable j contribute nothing, j = i adds 1 to
+ * sum2), then V = (sum1 / sum2) / (2 sigma^2).  V is [n_sigma][n]. */
+struct qco_wpot_job {
+    int32_t n;
+    const int32_t *row_ptr, *col_idx;
+    const double *w, *sigmas;
+    int32_t n_sigma;
+    double *V;
+    int32_t first, step;
+    int status;
+};
+
+static void *qco_wpot_worker(void *arg)
+{
+    struct qco_wpot_job *job = arg;
+    double *dist = malloc(sizeof(double) * (size_t)job->n);
+    if (!dist) { job->status = -2; return NULL; }
+    for (int32_t i = job->first; i < job->n; i += job->step) {
+        if (qco_dijkstra(job->n, job->row_ptr, job->col_idx, job->w, i, dist) != 0) {
+            job->status = -2;
+            break;
+        }
+        for (int32_t s = 0; s < job->n_sigma; ++s) {
+            double sigma = job->sigmas[s];
+            double sum1 = 0.0, sum2 = 0.0;
+            for (int32_t j = 0; j < job->n; ++j) {
+                double d = dist[j];
+                if (!isfinite(d)) continue;
+                double d2 = d * d;
+                double e = exp(-d2 / (2.0 * (sigma * sigma)));
+                sum1 = sum1 + d2 * e;
+                sum2 = sum2 + e;
+            }
+            job->V[(size_t)s * job->n + i] = (sum1 / sum2) / (2.0 * (sigma * sigma));
+        }
+    }
+    free(dist);
+    return NULL;
+}
+
+int qco_potential_weighted(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const double *w,
+                           const double *sigmas, int32_t n_sigma, double *V, int threads)
+{
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    pthread_t tid[256];
+    struct qco_wpot_job job[256];
+    int started[256];
+    int status = 0;
+    for (int t = 0; t < threads; ++t) {
+        job[t] = (struct qco_wpot_job){n, row_ptr, col_idx, w, sigmas, n_sigma, V, t, threads, 0};
+        started[t] = threads > 1 && pthread_create(&tid[t], NULL, qco_wpot_worker, &job[t]) == 0;
+        if (!started[t]) qco_wpot_worker(&job[t]);   /* no thread: run the share here */
+    }
+    for (int t = 0; t < threads; ++t) {
+        if (started[t]) pthread_join(tid[t], NULL);
+        if (job[t].status) status = job[t].status;
+    }
+    return status;
 }

@@ -188,6 +188,32 @@ class Graph:
                                                   _stream_handle(stream)))
         return out
 
+    def set_weights(self, weights, validate: bool = True, stream=None) -> None:
+        """Edge weights aligned with col_idx (numpy or CUDA float64 tensor)."""
+        torch = _torch()
+        flags = native.QC_VALIDATE if validate else 0
+        if isinstance(weights, torch.Tensor):
+            w = weights.to(device=f"cuda:{self.ctx.device}", dtype=torch.float64).contiguous()
+            flags |= native.QC_PTR_DEVICE
+            ptr = ctypes.cast(w.data_ptr(), native.c_double_p)
+        else:
+            w = np.ascontiguousarray(weights, dtype=np.float64)
+            ptr = w.ctypes.data_as(native.c_double_p)
+        if w.shape != (self.nnz,):
+            raise ValueError(f"need one weight per CSR entry ({self.nnz}), got {tuple(w.shape)}")
+        self.ctx.check(self.ctx._lib.qc_graph_set_weights(self.handle, ptr, flags, _stream_handle(stream)))
+
+    def potential_weighted(self, sigmas: Sequence[float], out=None, stream=None):
+        """float64 tensor [S, n]: the potential over weighted shortest-path distances."""
+        torch = _torch()
+        S = len(sigmas)
+        sig = (ctypes.c_double * S)(*[float(x) for x in sigmas])
+        if out is None:
+            out = torch.empty((S, self.n), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        self.ctx.check(self.ctx._lib.qc_potential_weighted(self.handle, sig, S, out.data_ptr(),
+                                                           _stream_handle(stream)))
+        return out
+
     def potential_adjacency(self, sigmas: Sequence[float], M: float = 2.0, out=None, stream=None):
         """float64 tensor [S, n]: the potential with the paper-literal distance
         (1 to a neighbour, M to any other node)."""

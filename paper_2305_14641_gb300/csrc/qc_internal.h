@@ -144,6 +144,8 @@ struct qc_graph {
     bool directed = false;   // row v = out-neighbours (QC_DIRECTED)
     qc_buffer row_ptr;       // int32[n+1]
     qc_buffer col_idx;       // int32[nnz]
+    bool weighted = false;   // qc_graph_set_weights was called
+    qc_buffer weights;       // double[nnz], aligned with col_idx
     // cached all-source BFS result
     bool hist_valid = false;
     int32_t D = 0;           // largest finite hop distance

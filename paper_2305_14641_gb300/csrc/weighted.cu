@@ -1,0 +1,361 @@
+// Weighted graphs: Section 3.1 makes the distance between adjacent nodes the
+// weight of their edge; between any two nodes it is read here as the length of
+// the lightest path (for unit weights this is the hop distance).  Lengths are
+// real, so the potential of Algorithm 1 is summed pair by pair instead of
+// through integer distance bins.
+//
+// Shortest paths: sources are processed K at a time (K a multiple of 32, sized
+// so that the distance block fits in about half of L2).  dist[v][k] (node-major,
+// binary64) holds the best length found from source s0 + k to v.  One
+// persistent cooperative launch relaxes, pass after pass,
+//     dist[v][k] = min(dist[v][k], min_{u in row v} dist[u][k] + w(v, u))
+// (pull over the rows: dist[v][k] is the lightest path from v to the source
+// s0 + k along the arcs of row v and onwards; for an undirected graph that is
+// also the path from the source to v).  The potential of node v below sums over
+// its own row dist[v][.], i.e. over the lengths *from* v, as in the hop path.
+// A warp owns an item (v, group of 32 sources) and only reads the neighbours
+// whose group changed in the previous pass (chg[u][g] = pass of u's last
+// change), so quiet parts of the graph cost one int per neighbour.  Updates are
+// in place: a value only ever falls to another path's length, every change is
+// seen by the neighbours in the next pass, and a pass without change ends the
+// launch, so the result is the unique fixed point whatever the interleaving:
+// each length is accumulated hop by hop as dist[u] + w, rounded in binary64,
+// exactly as Dijkstra's relaxation in the oracle.
+//
+// Potential: for node v, sum1 = sum_j d^2 e^{-d^2 / 2 sigma^2} and
+// sum2 = sum_j e^{...} over the j that v reaches (the self term adds 1 to
+// sum2), d = dist[v][j - s0] of each batch, with CUDA's binary64 exp and
+// separately rounded multiplies and adds.  The sums run over each batch's
+// sources in a fixed pattern and over the batches in order, so the result is
+// the same on every run; it differs from the oracle's sequential sum over j
+// only by rounding (relative 1e-15 or so).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <vector>
+
+#include "qc_device.cuh"
+#include "qc_internal.h"
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct SsspParams {
+    int32_t n;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const double *w;
+    double *dist;                  // [n][K]
+    int32_t *chg;                  // [n][KG]
+    int32_t K, KG, s0, ns;         // sources s0 .. s0 + ns - 1 (ns <= K)
+    int32_t max_pass;
+    int32_t *status;               // [0] state, [1] passes run
+    unsigned *bar;
+    int32_t *pass_ctr;             // [max_pass + 1] items taken
+    int32_t *pass_new;             // [max_pass + 1] some value fell
+};
+
+__global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
+    const int lane = threadIdx.x & 31;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    const double INF = __longlong_as_double(0x7ff0000000000000ll);
+    // pass 0: each source at distance 0 from itself
+    for (long long i = tid; i < (long long)p.n * p.K; i += nthreads) {
+        const int v = (int)(i / p.K), k = (int)(i - (long long)v * p.K);
+        p.dist[i] = (k < p.ns && v == p.s0 + k) ? 0.0 : INF;
+    }
+    for (long long i = tid; i < (long long)p.n * p.KG; i += nthreads) {
+        const int v = (int)(i / p.KG), g = (int)(i - (long long)v * p.KG);
+        const int k = v - p.s0;
+        p.chg[i] = (k >= 0 && k < p.ns && (k >> 5) == g) ? 0 : -1;
+    }
+    if (!qcdev::grid_barrier(p.bar, p.status)) return;
+    const int items = p.n * p.KG;
+    int pass = 1;
+    for (; pass <= p.max_pass; ++pass) {
+        bool any = false;
+        while (true) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(p.pass_ctr + pass, 1);
+            it = __shfl_sync(FULL, it, 0);
+            if (it >= items) break;
+            const int v = it / p.KG, g = it - v * p.KG;
+            const int k = g * 32 + lane;
+            double *dv = p.dist + (size_t)v * p.K + k;
+            const double mine = *(volatile double *)dv;
+            double best = mine;
+            const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
+            for (int e0 = beg; e0 < end; e0 += 32) {
+                const int e = e0 + lane;
+                int u = 0;
+                double wt = 0.0;
+                bool fresh = false;
+                if (e < end) {
+                    u = p.col_idx[e];
+                    wt = p.w[e];
+                    fresh = *(volatile int32_t *)(p.chg + (size_t)u * p.KG + g) == pass - 1;
+                }
+                unsigned mask = __ballot_sync(FULL, fresh);
+                while (mask) {
+                    // up to four changed neighbours in flight
+                    int ub[4];
+                    double wb[4], db[4];
+                    int cnt = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (mask) {
+                            const int b = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            ub[q] = __shfl_sync(FULL, u, b);
+                            wb[q] = __shfl_sync(FULL, wt, b);
+                            cnt = q + 1;
+                        } else {
+                            ub[q] = v;
+                            wb[q] = 0.0;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        db[q] = (q < cnt) ? *(volatile const double *)(p.dist + (size_t)ub[q] * p.K + k) : INF;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const double c = __dadd_rn(db[q], wb[q]);
+                        if (c < best) best = c;
+                    }
+                }
+            }
+            const bool fell = best < mine;
+            if (fell) *(volatile double *)dv = best;
+            if (__any_sync(FULL, fell)) {
+                any = true;
+                if (lane == 0) *(volatile int32_t *)(p.chg + (size_t)v * p.KG + g) = pass;
+            }
+        }
+        if (__syncthreads_or(any) && threadIdx.x == 0) p.pass_new[pass] = 1;
+        if (!qcdev::grid_barrier(p.bar, p.status)) return;
+        if (*(volatile int32_t *)(p.pass_new + pass) == 0) break;
+    }
+    if (tid == 0) {
+        p.status[1] = pass;
+        if (pass > p.max_pass) p.status[0] = qcdev::ST_NEED_ROWS;   // not converged within max_pass
+    }
+}
+
+// acc[s][v] += (sum1, sum2) over the batch's sources for node v: a warp per node,
+// lane l takes sources l, l + 32, ... in order, then a butterfly over the lanes
+// (every lane ends with the same total) and one add into the running sums, so
+// the result is the same on every run.
+__global__ void wpot_accumulate(int32_t n, int32_t K, int32_t ns, const double *dist, int32_t S,
+                                const double *den, double2 *acc) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int v = warp; v < n; v += nwarps) {
+        const double *row = dist + (size_t)v * K;
+        for (int s = 0; s < S; ++s) {
+            const double dn = den[s];
+            double s1 = 0.0, s2 = 0.0;
+            for (int k = lane; k < ns; k += 32) {
+                const double d = row[k];
+                if (!(d < 1e308)) continue;                        // unreachable (+inf)
+                const double d2 = __dmul_rn(d, d);
+                const double e = exp(-__ddiv_rn(d2, dn));
+                s1 = __dadd_rn(s1, __dmul_rn(d2, e));
+                s2 = __dadd_rn(s2, e);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                s1 = __dadd_rn(s1, __shfl_xor_sync(FULL, s1, off));
+                s2 = __dadd_rn(s2, __shfl_xor_sync(FULL, s2, off));
+            }
+            if (lane == 0) {
+                double2 a = acc[(size_t)s * n + v];
+                a.x = __dadd_rn(a.x, s1);
+                a.y = __dadd_rn(a.y, s2);
+                acc[(size_t)s * n + v] = a;
+            }
+        }
+    }
+}
+
+__global__ void wpot_final(int32_t n, int32_t S, const double *den, const double2 *acc, double *V) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S * n; i += gridDim.x * blockDim.x) {
+        const int s = i / n;
+        const double2 a = acc[i];
+        V[i] = __ddiv_rn(__ddiv_rn(a.x, a.y), den[s]);
+    }
+}
+
+enum : int32_t { BAD_WEIGHT = 1, BAD_MIRROR = 2 };
+
+// Positive finite weights; for an undirected graph w(v, u) = w(u, v).
+__global__ void check_weights(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const double *w,
+                              bool symmetric, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    int bad = 0;
+    for (int v = warp; v < n; v += nwarps) {
+        for (int e = row_ptr[v] + lane; e < row_ptr[v + 1]; e += 32) {
+            const double x = w[e];
+            if (!(x > 0.0) || !(x < 1e308)) bad |= BAD_WEIGHT;
+            if (!symmetric) continue;
+            const int u = col_idx[e];
+            int lo = row_ptr[u], hi = row_ptr[u + 1] - 1;
+            bool same = false;
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const int y = col_idx[mid];
+                if (y == v) { same = (w[mid] == x); break; }
+                if (y < v) lo = mid + 1; else hi = mid - 1;
+            }
+            if (!same) bad |= BAD_MIRROR;
+        }
+    }
+    bad = __reduce_or_sync(FULL, bad);
+    if (lane == 0 && bad) atomicOr(err, bad);
+}
+
+int32_t sources_per_batch(const qc_ctx *ctx, int32_t n) {
+    int64_t K;
+    if (const char *env = getenv("QCGRAPH_SSSP_SOURCES")) {
+        K = atoll(env);
+    } else {
+        const size_t target = ctx->l2_bytes ? ctx->l2_bytes / 2 : (size_t)48 << 20;
+        K = (int64_t)(target / (8 * (size_t)n));
+    }
+    K = (K / 32) * 32;
+    if (K < 32) K = 32;
+    if (K > 1024) K = 1024;
+    const int64_t cover = ((int64_t)n + 31) / 32 * 32;
+    return (int32_t)std::min<int64_t>(K, cover);
+}
+
+}  // namespace
+
+extern "C" qc_status qc_graph_set_weights(qc_graph *g, const double *w, uint32_t flags, void *stream_) {
+    if (!g || (!w && g->nnz > 0)) return QC_ERR_INVALID_ARG;
+    qc_ctx *ctx = g->ctx;
+    cudaStream_t stream = qc_stream(stream_);
+    QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    qc_buffer nb;
+    const size_t bytes = sizeof(double) * (size_t)(g->nnz > 0 ? g->nnz : 1);
+    QC_TRY(nb.allocate(ctx, bytes, stream));
+    if (g->nnz > 0)
+        QC_CUDA_TRY(ctx, cudaMemcpyAsync(nb.ptr, w, sizeof(double) * (size_t)g->nnz,
+                                         (flags & QC_PTR_DEVICE) ? cudaMemcpyDeviceToDevice
+                                                                 : cudaMemcpyHostToDevice,
+                                         stream));
+    if ((flags & QC_VALIDATE) && g->nnz > 0) {
+        qc_buffer err;
+        QC_TRY(err.allocate(ctx, sizeof(int32_t), stream));
+        QC_CUDA_TRY(ctx, cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), stream));
+        const int blocks = qc_ceil_div(g->n, 8) < 8 * ctx->num_sms ? qc_ceil_div(g->n, 8) : 8 * ctx->num_sms;
+        check_weights<<<blocks, 256, 0, stream>>>(g->n, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(),
+                                                  nb.as<double>(), !g->directed, err.as<int32_t>());
+        QC_LAUNCHED(ctx);
+        qc_pinned pin(ctx);
+        QC_TRY(pin.acquire());
+        int32_t *h = static_cast<int32_t *>(pin.ptr);
+        QC_CUDA_TRY(ctx, cudaMemcpyAsync(h, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+        QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        if (h[0]) {
+            qc_set_error(ctx, "invalid weights (flags 0x%x):%s%s", h[0],
+                         (h[0] & BAD_WEIGHT) ? " not finite and > 0;" : "",
+                         (h[0] & BAD_MIRROR) ? " w(u, v) != w(v, u) in an undirected graph;" : "");
+            return QC_ERR_INVALID_GRAPH;
+        }
+    }
+    QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));   // a host source may be freed on return
+    g->weights = std::move(nb);
+    g->weighted = true;
+    return QC_OK;
+}
+
+extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
+                                           void *stream_) {
+    if (!g || !sigmas || n_sigma < 1 || !V_out) return QC_ERR_INVALID_ARG;
+    qc_ctx *ctx = g->ctx;
+    if (!g->weighted) {
+        qc_set_error(ctx, "qc_potential_weighted: the graph has no weights (qc_graph_set_weights)");
+        return QC_ERR_INVALID_ARG;
+    }
+    for (int32_t s = 0; s < n_sigma; ++s)
+        if (!qc_sigma_ok(sigmas[s])) {
+            qc_set_error(ctx, "qc_potential_weighted: sigma[%d] = %g is not finite and > 0", s, sigmas[s]);
+            return QC_ERR_INVALID_ARG;
+        }
+    cudaStream_t stream = qc_stream(stream_);
+    QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const int32_t n = g->n;
+    const int32_t K = sources_per_batch(ctx, n);
+    const int32_t KG = K / 32;
+    const int32_t max_pass = n + 1;     // a lightest path has at most n - 1 arcs
+    std::vector<double> den(n_sigma);
+    for (int32_t s = 0; s < n_sigma; ++s) den[s] = 2.0 * (sigmas[s] * sigmas[s]);
+    qc_buffer dist, chg, ctl, acc, dden;
+    QC_TRY(dist.allocate(ctx, sizeof(double) * (size_t)n * K, stream));
+    QC_TRY(chg.allocate(ctx, sizeof(int32_t) * (size_t)n * KG, stream));
+    QC_TRY(ctl.allocate(ctx, sizeof(int32_t) * (8 + 2 * ((size_t)max_pass + 1)), stream));
+    QC_TRY(acc.allocate(ctx, sizeof(double2) * (size_t)n_sigma * n, stream));
+    QC_CUDA_TRY(ctx, cudaMemsetAsync(acc.ptr, 0, acc.bytes, stream));
+    QC_TRY(dden.allocate(ctx, sizeof(double) * n_sigma, stream));
+    QC_CUDA_TRY(ctx, cudaMemcpyAsync(dden.ptr, den.data(), sizeof(double) * n_sigma, cudaMemcpyHostToDevice,
+                                     stream));
+    int per_sm = 0;
+    QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)sssp_persistent, 256, 0));
+    if (per_sm < 1) {
+        qc_set_error(ctx, "shortest-path kernel cannot be resident on an SM");
+        return QC_ERR_CUDA;
+    }
+    int blocks = per_sm * qc_coop_sms(ctx);
+    const int want = qc_ceil_div((int64_t)n * KG, 8);
+    if (blocks > want) blocks = want;
+    if (blocks < 1) blocks = 1;
+    qc_pinned pin(ctx);
+    QC_TRY(pin.acquire());
+    int32_t *h = static_cast<int32_t *>(pin.ptr);
+    const int pblocks = std::max(1, std::min(qc_ceil_div(n, 8), 8 * ctx->num_sms));
+    for (int32_t s0 = 0; s0 < n; s0 += K) {
+        SsspParams p;
+        p.n = n;
+        p.row_ptr = g->row_ptr.as<int32_t>();
+        p.col_idx = g->col_idx.as<int32_t>();
+        p.w = g->weights.as<double>();
+        p.dist = dist.as<double>();
+        p.chg = chg.as<int32_t>();
+        p.K = K;
+        p.KG = KG;
+        p.s0 = s0;
+        p.ns = std::min(K, n - s0);
+        p.max_pass = max_pass;
+        p.status = ctl.as<int32_t>();
+        p.bar = reinterpret_cast<unsigned *>(ctl.as<int32_t>() + 2);
+        p.pass_ctr = ctl.as<int32_t>() + 8;
+        p.pass_new = p.pass_ctr + (max_pass + 1);
+        QC_CUDA_TRY(ctx, cudaMemsetAsync(ctl.ptr, 0, ctl.bytes, stream));
+        void *args[] = {(void *)&p};
+        QC_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)sssp_persistent, dim3(blocks), dim3(256), args,
+                                                     0, stream));
+        QC_LAUNCHED(ctx);
+        QC_CUDA_TRY(ctx, cudaMemcpyAsync(h, ctl.ptr, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+        QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        if (h[0] == qcdev::ST_TIMEOUT) {
+            qc_set_error(ctx, "shortest paths: grid barrier timed out (sources from %d)", s0);
+            return QC_ERR_TIMEOUT;
+        }
+        if (h[0] != qcdev::ST_DONE) {
+            qc_set_error(ctx, "shortest paths did not settle within %d passes", max_pass);
+            return QC_ERR_CUDA;
+        }
+        wpot_accumulate<<<pblocks, 256, 0, stream>>>(n, K, p.ns, dist.as<double>(), n_sigma, dden.as<double>(),
+                                                     acc.as<double2>());
+        QC_LAUNCHED(ctx);
+    }
+    const int fb = std::max(1, std::min(qc_ceil_div((int64_t)n_sigma * n, 256), 2 * ctx->num_sms));
+    wpot_final<<<fb, 256, 0, stream>>>(n, n_sigma, dden.as<double>(), acc.as<double2>(), V_out);
+    QC_LAUNCHED(ctx);
+    return QC_OK;
+}

@@ -77,6 +77,9 @@ SIGNATURES = [
     ("qc_graph_num_nodes", ctypes.c_int32, [ctypes.c_void_p]),
     ("qc_graph_num_edges", ctypes.c_int64, [ctypes.c_void_p]),
     ("qc_graph_histogram", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, c_int32_p, ctypes.c_void_p]),
+    ("qc_graph_set_weights", ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_uint32, ctypes.c_void_p]),
+    ("qc_potential_weighted", ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_int32, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
     ("qc_graph_set_histogram", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32,
                                               ctypes.c_void_p]),
     ("qc_potential", ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_int32, ctypes.c_void_p,

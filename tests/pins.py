@@ -412,3 +412,64 @@ def check_directed(orc):
 
 
 ALL_CHECKS.append(check_directed)
+
+
+def weighted_floyd_warshall(graph, w) -> np.ndarray:
+    n = graph.n
+    D = np.full((n, n), np.inf)
+    np.fill_diagonal(D, 0.0)
+    rows = np.repeat(np.arange(n), graph.degrees())
+    D[rows, graph.col_idx] = np.minimum(D[rows, graph.col_idx], w)
+    for k in range(n):
+        D = np.minimum(D, D[:, k:k + 1] + D[k:k + 1, :])
+    return D
+
+
+def check_weighted(orc):
+    """Weighted graphs (distance = length of the lightest path).  Dijkstra equals
+    scipy's weighted shortest paths bit for bit and Floyd-Warshall within rounding
+    (its additions group differently); unit weights give the hop-mode potential;
+    constant weights c give the hop-mode potential at sigma / c; on a weighted path
+    V matches the 50-digit sum over the path's prefix lengths; directed weighted
+    graphs follow the arcs."""
+    for t in range(6):
+        g = gg.rng(98, t)
+        n = int(g.integers(2, 40))
+        graph = (gg.erdos_renyi(n, float(g.uniform(0.05, 0.3)), g) if t % 2 == 0
+                 else gg.directed_erdos_renyi(n, float(g.uniform(0.05, 0.3)), g))
+        w = gg.edge_weights(graph, 0.25, 3.0, g)
+        A = sp.csr_matrix((w, graph.col_idx, graph.row_ptr), shape=(n, n))
+        ref = shortest_path(A, method="D", directed=True)
+        fw = weighted_floyd_warshall(graph, w)
+        for s in range(n):
+            d = orc.dijkstra(graph, w, s)
+            assert np.array_equal(d, ref[s]), (graph.name, s)
+            fin = np.isfinite(fw[s])
+            assert np.array_equal(np.isfinite(d), fin)
+            assert np.allclose(d[fin], fw[s][fin], rtol=1e-12, atol=0), (graph.name, s)
+    for graph in [gg.planted_partition(120, 4, 0.15, 0.02, gg.rng(99)), gg.path(9), gg.star(11)]:
+        h = orc.histograms(graph)
+        ones = np.ones(graph.nnz)
+        for sigma in (0.6, 1.5):
+            Vw = orc.potential_weighted(graph, ones, [sigma])[0]
+            assert np.allclose(Vw, orc.potential(h, sigma), rtol=1e-13, atol=0), graph.name
+            for c in (0.5, 2.0, 3.0):
+                Vc = orc.potential_weighted(graph, np.full(graph.nnz, c), [sigma])[0]
+                assert np.allclose(Vc, orc.potential(h, sigma / c), rtol=1e-13, atol=0), (graph.name, c)
+    graph = gg.path(7)
+    step = np.array([0.5, 1.25, 2.0, 0.75, 1.5, 1.0])         # weight of edge (i, i + 1)
+    rows = np.repeat(np.arange(7), graph.degrees())
+    w = step[np.minimum(rows, graph.col_idx)]
+    pos = np.concatenate([[0.0], np.cumsum(step)])
+    for sigma in (0.8, 2.5):
+        V = orc.potential_weighted(graph, w, [sigma])[0]
+        for i in range(7):
+            d = orc.dijkstra(graph, w, i)
+            assert np.allclose(d, np.abs(pos - pos[i]), rtol=1e-15, atol=1e-15)
+            s = mpmath.mpf(sigma)
+            num = sum(mpmath.mpf(x) ** 2 * mpmath.exp(-mpmath.mpf(x) ** 2 / (2 * s * s)) for x in d)
+            den = sum(mpmath.exp(-mpmath.mpf(x) ** 2 / (2 * s * s)) for x in d)
+            assert close(V[i], num / den / (2 * s * s)), (sigma, i)
+
+
+ALL_CHECKS.append(check_weighted)

@@ -330,3 +330,62 @@ def test_histogram_checkpoint(qc, ctx):
         g3.set_histogram(bad)
     assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
     g3.close()
+
+
+def assert_weighted_matches(qc, ctx, graph, w, sigmas):
+    G = qc.Graph.from_graph(ctx, graph)
+    G.set_weights(w)
+    V = G.potential_weighted(sigmas)
+    Vh = V.cpu().numpy()
+    ref = oracle.potential_weighted(graph, w, sigmas, threads=oracle.default_threads())
+    rel = np.abs(Vh - ref) / np.maximum(np.abs(ref), np.finfo(np.float64).tiny)
+    assert np.all(rel <= 1e-12), (graph.name, float(rel.max()))
+    labels, counts = G.ggd_labels(V)
+    labels = labels.cpu().numpy()
+    for s in range(len(sigmas)):
+        p, _ = oracle.ggd_parent(graph, Vh[s])
+        lab, k = oracle.find_centers(p)
+        assert np.array_equal(labels[s], lab) and counts[s] == k, (graph.name, s)
+    G.close()
+    return Vh
+
+
+@pytest.mark.parametrize("n", [1, 3, 65, 300, 2000])
+def test_weighted(qc, ctx, n):
+    """Weighted shortest-path distances, undirected and directed: V within 1e-12 of
+    the oracle's Dijkstra-based sums; labels from the same V exactly."""
+    g = gg.rng(36, n)
+    for graph in (gg.erdos_renyi(n, min(6.0 / max(n, 2), 0.5), g),
+                  gg.directed_erdos_renyi(max(n, 2), min(5.0 / max(n, 2), 0.5), g)):
+        assert_weighted_matches(qc, ctx, graph, gg.edge_weights(graph, 0.25, 3.0, g), [0.7, 2.0])
+
+
+def test_weighted_batches_and_unit_weights(qc, ctx, monkeypatch):
+    """Sources in many blocks of 32; unit weights reproduce the hop-distance potential."""
+    monkeypatch.setenv("QCGRAPH_SSSP_SOURCES", "32")
+    graph = gg.planted_partition(700, 5, 0.04, 0.003, gg.rng(37))
+    assert_weighted_matches(qc, ctx, graph, gg.edge_weights(graph, 0.5, 2.0, gg.rng(38)), [0.9, 1.8, 3.0])
+    Vw = assert_weighted_matches(qc, ctx, graph, np.ones(graph.nnz), [0.9, 1.8])
+    hop = oracle.solve(graph, [0.9, 1.8]).V
+    assert np.allclose(Vw, hop, rtol=1e-12, atol=0)
+
+
+def test_weighted_invalid(qc, ctx):
+    graph = gg.erdos_renyi(200, 0.05, gg.rng(39))
+    G = qc.Graph.from_graph(ctx, graph)
+    with pytest.raises(qc.QCError) as e:
+        G.potential_weighted([1.0])
+    assert e.value.status_name == "QC_ERR_INVALID_ARG"
+    w = gg.edge_weights(graph, 0.5, 2.0, gg.rng(40))
+    bad = w.copy()
+    bad[3] = -1.0
+    with pytest.raises(qc.QCError) as e:
+        G.set_weights(bad)
+    assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
+    bad = w.copy()
+    bad[5] *= 1.5                         # the mirror entry keeps the old weight
+    with pytest.raises(qc.QCError) as e:
+        G.set_weights(bad)
+    assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
+    G.set_weights(torch.tensor(w, device="cuda"))
+    G.close()
