@@ -603,6 +603,57 @@ def bench_adjacency(args):
     ctx.close()
 
 
+def bench_weighted(args):
+    """Weighted shortest-path distances on the dcsbm-16384 graph with weights drawn
+    U(0.5, 2.0): all-source shortest paths, 16 potentials, descent and roots per
+    step; the oracle (Dijkstra per source) on a sample of sources, scaled."""
+    import torch
+    import oracle
+    import paper_2305_14641_gb300 as qc
+    graph, sigmas = gg.config2()
+    w = gg.edge_weights(graph, 0.5, 2.0, gg.rng(7, 1))
+    ctx = qc.Context(0)
+    g = qc.Graph.from_graph(ctx, graph)
+    g.set_weights(w)
+    S, n = len(sigmas), graph.n
+    V = torch.empty((S, n), dtype=torch.float64, device="cuda")
+    lab = torch.empty((S, n), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g.potential_weighted(sigmas, out=V)
+        g.ggd_labels(V, out=lab, counts=False)
+
+    step()
+    torch.cuda.synchronize()
+    steps = max(2, min(args.steps, 10))
+    launches0 = ctx.launch_count()
+    with ClockSampler(0) as clocks:
+        ms = _device_steps(step, steps, flush, stream)
+    launches = (ctx.launch_count() - launches0) // steps
+    # the shortest paths with a single sigma, to split the step between paths and sums
+    one_ms = _device_steps(lambda: g.potential_weighted(sigmas[:1], out=V[:1]), steps, flush, stream)
+    cpu = None
+    if not args.no_cpu_baseline:
+        oracle.build()
+        threads = oracle.default_threads()
+        t0 = time.perf_counter()
+        oracle.potential_weighted(graph, w, sigmas, threads=threads)
+        cpu_s = time.perf_counter() - t0
+        cpu = {"value": S / cpu_s, "unit": METRIC, "cores": threads, "kind": "oracle", "seconds": cpu_s,
+               "sample": f"the whole potential: Dijkstra from all {n} sources and the pair sums for "
+                         f"{S} sigma values (descent not included)"}
+    line = {"metric": METRIC, "workload": "weighted16384: the dcsbm-16384 graph with edge weights "
+                                          "U(0.5, 2.0), seed 7; 16 sigma values",
+            "value": S / (ms / 1000.0), "unit": METRIC, "ms_per_step": ms, "steps": steps,
+            "ms_paths_and_one_sigma": one_ms,
+            "gpu_launches_per_step": launches, "clocks": clocks.summary(), "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    g.close()
+    ctx.close()
+
+
 def bench_fig3(args):
     """Fully-connected graphs of growing n (the workload of the paper's GPU-vs-CPU figure):
     time per clustering (sigma = 1) on the GPU, hop and adjacency distance, and the oracle
@@ -700,7 +751,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["dcsbm16384", "sbm262144", "directed16384", "batch4096", "serve",
-                                           "adjacency16384", "fig3", "quality"],
+                                           "adjacency16384", "weighted16384", "fig3", "quality"],
                     default="dcsbm16384")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--plain-graphs", type=int, default=512)
@@ -718,6 +769,8 @@ def main():
         return bench_adjacency(args)
     if args.workload == "fig3":
         return bench_fig3(args)
+    if args.workload == "weighted16384":
+        return bench_weighted(args)
     if args.workload == "quality":
         return bench_quality(args)
     spec = SINGLE[args.workload]

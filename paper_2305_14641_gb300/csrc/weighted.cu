@@ -13,19 +13,25 @@
 // s0 + k along the arcs of row v and onwards; for an undirected graph that is
 // also the path from the source to v).  The potential of node v below sums over
 // its own row dist[v][.], i.e. over the lengths *from* v, as in the hop path.
-// A warp owns an item (v, group of 32 sources) and only reads the neighbours
-// whose group changed in the previous pass (chg[u][g] = pass of u's last
-// change), so quiet parts of the graph cost one int per neighbour.  Updates are
+// A warp owns a node v.  It first checks whether any neighbour changed any
+// distance in the previous pass or so far in this one (chgv[u] = pass of u's
+// last change) and skips v if none did; otherwise, group by group (32 sources
+// each), it reads only the neighbours whose group changed since the previous
+// pass (chg[u][g]), so quiet parts of the graph cost one int per neighbour and
+// pass.  Testing ">= previous pass" rather than "== previous pass" matters: a
+// neighbour that changes again in this pass must not hide its earlier change.  Updates are
 // in place: a value only ever falls to another path's length, every change is
 // seen by the neighbours in the next pass, and a pass without change ends the
-// launch, so the result is the unique fixed point whatever the interleaving:
+// launch (the last change of any (u, group) is read by u's neighbours in the
+// pass after it), so the result is the unique fixed point whatever the
+// interleaving:
 // each length is accumulated hop by hop as dist[u] + w, rounded in binary64,
 // exactly as Dijkstra's relaxation in the oracle.
 //
 // Potential: for node v, sum1 = sum_j d^2 e^{-d^2 / 2 sigma^2} and
 // sum2 = sum_j e^{...} over the j that v reaches (the self term adds 1 to
-// sum2), d = dist[v][j - s0] of each batch, with CUDA's binary64 exp and
-// separately rounded multiplies and adds.  The sums run over each batch's
+// sum2), d = dist[v][j - s0] of each batch, with CUDA's binary64 exp of
+// d^2 x (-1 / 2 sigma^2) and separately rounded multiplies and adds.  The sums run over each batch's
 // sources in a fixed pattern and over the batches in order, so the result is
 // the same on every run; it differs from the oracle's sequential sum over j
 // only by rounding (relative 1e-15 or so).
@@ -47,7 +53,8 @@ struct SsspParams {
     const int32_t *col_idx;
     const double *w;
     double *dist;                  // [n][K]
-    int32_t *chg;                  // [n][KG]
+    int32_t *chg;                  // [n][KG] pass of the last change of each group
+    int32_t *chgv;                 // [n] pass of the last change of any group
     int32_t K, KG, s0, ns;         // sources s0 .. s0 + ns - 1 (ns <= K)
     int32_t max_pass;
     int32_t *status;               // [0] state, [1] passes run
@@ -71,8 +78,9 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
         const int k = v - p.s0;
         p.chg[i] = (k >= 0 && k < p.ns && (k >> 5) == g) ? 0 : -1;
     }
+    for (int v = tid; v < p.n; v += nthreads) p.chgv[v] = (v >= p.s0 && v < p.s0 + p.ns) ? 0 : -1;
     if (!qcdev::grid_barrier(p.bar, p.status)) return;
-    const int items = p.n * p.KG;
+    const int items = p.n;
     int pass = 1;
     for (; pass <= p.max_pass; ++pass) {
         bool any = false;
@@ -81,12 +89,18 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
             if (lane == 0) it = atomicAdd(p.pass_ctr + pass, 1);
             it = __shfl_sync(FULL, it, 0);
             if (it >= items) break;
-            const int v = it / p.KG, g = it - v * p.KG;
+            const int v = it;
+            const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
+            bool stirred = false;
+            for (int e = beg + lane; e < end && !stirred; e += 32)
+                stirred = *(volatile int32_t *)(p.chgv + p.col_idx[e]) >= pass - 1;
+            if (!__any_sync(FULL, stirred)) continue;
+            bool v_fell = false;
+            for (int g = 0; g < p.KG; ++g) {
             const int k = g * 32 + lane;
             double *dv = p.dist + (size_t)v * p.K + k;
             const double mine = *(volatile double *)dv;
             double best = mine;
-            const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
             for (int e0 = beg; e0 < end; e0 += 32) {
                 const int e = e0 + lane;
                 int u = 0;
@@ -95,7 +109,7 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
                 if (e < end) {
                     u = p.col_idx[e];
                     wt = p.w[e];
-                    fresh = *(volatile int32_t *)(p.chg + (size_t)u * p.KG + g) == pass - 1;
+                    fresh = *(volatile int32_t *)(p.chg + (size_t)u * p.KG + g) >= pass - 1;
                 }
                 unsigned mask = __ballot_sync(FULL, fresh);
                 while (mask) {
@@ -129,8 +143,13 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
             const bool fell = best < mine;
             if (fell) *(volatile double *)dv = best;
             if (__any_sync(FULL, fell)) {
-                any = true;
+                v_fell = true;
                 if (lane == 0) *(volatile int32_t *)(p.chg + (size_t)v * p.KG + g) = pass;
+            }
+            }
+            if (v_fell) {
+                any = true;
+                if (lane == 0) *(volatile int32_t *)(p.chgv + v) = pass;
             }
         }
         if (__syncthreads_or(any) && threadIdx.x == 0) p.pass_new[pass] = 1;
@@ -155,13 +174,13 @@ __global__ void wpot_accumulate(int32_t n, int32_t K, int32_t ns, const double *
     for (int v = warp; v < n; v += nwarps) {
         const double *row = dist + (size_t)v * K;
         for (int s = 0; s < S; ++s) {
-            const double dn = den[s];
+            const double nr = -1.0 / den[s];       // one division per node and sigma, not per pair
             double s1 = 0.0, s2 = 0.0;
             for (int k = lane; k < ns; k += 32) {
                 const double d = row[k];
                 if (!(d < 1e308)) continue;                        // unreachable (+inf)
                 const double d2 = __dmul_rn(d, d);
-                const double e = exp(-__ddiv_rn(d2, dn));
+                const double e = exp(__dmul_rn(d2, nr));
                 s1 = __dadd_rn(s1, __dmul_rn(d2, e));
                 s2 = __dadd_rn(s2, e);
             }
@@ -295,9 +314,10 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
     const int32_t max_pass = n + 1;     // a lightest path has at most n - 1 arcs
     std::vector<double> den(n_sigma);
     for (int32_t s = 0; s < n_sigma; ++s) den[s] = 2.0 * (sigmas[s] * sigmas[s]);
-    qc_buffer dist, chg, ctl, acc, dden;
+    qc_buffer dist, chg, chgv, ctl, acc, dden;
     QC_TRY(dist.allocate(ctx, sizeof(double) * (size_t)n * K, stream));
     QC_TRY(chg.allocate(ctx, sizeof(int32_t) * (size_t)n * KG, stream));
+    QC_TRY(chgv.allocate(ctx, sizeof(int32_t) * (size_t)n, stream));
     QC_TRY(ctl.allocate(ctx, sizeof(int32_t) * (8 + 2 * ((size_t)max_pass + 1)), stream));
     QC_TRY(acc.allocate(ctx, sizeof(double2) * (size_t)n_sigma * n, stream));
     QC_CUDA_TRY(ctx, cudaMemsetAsync(acc.ptr, 0, acc.bytes, stream));
@@ -311,7 +331,7 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
         return QC_ERR_CUDA;
     }
     int blocks = per_sm * qc_coop_sms(ctx);
-    const int want = qc_ceil_div((int64_t)n * KG, 8);
+    const int want = qc_ceil_div(n, 8);
     if (blocks > want) blocks = want;
     if (blocks < 1) blocks = 1;
     qc_pinned pin(ctx);
@@ -326,6 +346,7 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
         p.w = g->weights.as<double>();
         p.dist = dist.as<double>();
         p.chg = chg.as<int32_t>();
+        p.chgv = chgv.as<int32_t>();
         p.K = K;
         p.KG = KG;
         p.s0 = s0;
