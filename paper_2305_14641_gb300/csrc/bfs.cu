@@ -73,6 +73,8 @@ struct BfsParams {
     const int4 *info;           // {node, row start, row end, 0} per order position
     const int32_t *comp;        // component (smallest node id) of each node
     const int32_t *wcomp;       // component shared by a whole source word, or -1
+    const int32_t *wmajor;      // component holding most of a word's sources
+    const unsigned long long *wmask;   // bits of those sources
     ulonglong2 *buf[2];         // vis_l in buf[l & 1], [n][R]
     int32_t R;                  // 16-byte segments per row in this chunk
     int32_t T;                  // tiles per row
@@ -107,6 +109,8 @@ __device__ __forceinline__ uint64_t preset_word(const BfsParams &p, int gw, int 
     const int wc = p.wcomp[gw];
     if (wc >= 0) {
         m = (wc == cv) ? 0ull : ONES;
+    } else if (p.wmajor[gw] == cv) {
+        m = ~p.wmask[gw];             // v is in the word's main component
     } else {
         m = 0ull;
         const int s0 = 64 * gw;
@@ -537,6 +541,8 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
             p.info = g->oinfo.as<int4>();
             p.comp = g->comp.as<int32_t>();
             p.wcomp = g->wcomp.as<int32_t>();
+            p.wmajor = g->wmajor.as<int32_t>();
+            p.wmask = g->wmask.as<unsigned long long>();
             p.buf[0] = visB.as<ulonglong2>();
             p.buf[1] = visA.as<ulonglong2>();
             p.R = R;

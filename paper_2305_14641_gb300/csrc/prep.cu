@@ -2,6 +2,8 @@
 //   comp[v]   connected component of v, as the smallest node id in it;
 //   wcomp[k]  the component shared by all valid sources of 64-source word k,
 //             or -1 when the word mixes components;
+//   wmajor[k], wmask[k]  the component holding most of word k's sources and
+//             the bits of those sources;
 //   order[i]  nodes by decreasing degree bucket (floor(log2(deg + 1))), so that
 //             dealing them round-robin to warps spreads the heavy rows;
 //             order[n] = how many lead the order with degree >= 2^QC_HEAVY_BUCKET - 1
@@ -98,14 +100,34 @@ __global__ void cc_flatten(int32_t n, const int32_t *L, int32_t *comp) {
     }
 }
 
-__global__ void word_components(int32_t n, int32_t W, const int32_t *comp, int32_t *wcomp) {
+// Per 64-source word: wcomp = the one component of all its sources, or -1; the
+// component holding most of them (wmajor) and their bits (wmask), so that the
+// BFS presets the row of a node in that component with one mask and walks the
+// word bit by bit only for nodes of the word's minor components.
+__global__ void word_components(int32_t n, int32_t W, const int32_t *comp, int32_t *wcomp, int32_t *wmajor,
+                                unsigned long long *wmask) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < W; k += gridDim.x * blockDim.x) {
         const int s0 = 64 * k;
         const int cnt = min(64, n - s0);
-        const int c0 = comp[s0];
-        bool same = true;
-        for (int b = 1; b < cnt && same; ++b) same = comp[s0 + b] == c0;
-        wcomp[k] = same ? c0 : -1;
+        int best = comp[s0], best_count = 0;
+        unsigned long long best_mask = 0ull, seen = 0ull;
+        for (int b = 0; b < cnt; ++b) {
+            if ((seen >> b) & 1ull) continue;
+            const int c = comp[s0 + b];
+            unsigned long long m = 0ull;
+            for (int b2 = b; b2 < cnt; ++b2)
+                if (comp[s0 + b2] == c) m |= 1ull << b2;
+            seen |= m;
+            const int pc = __popcll(m);
+            if (pc > best_count) {
+                best = c;
+                best_count = pc;
+                best_mask = m;
+            }
+        }
+        wcomp[k] = (best_count == cnt) ? best : -1;
+        wmajor[k] = best;
+        wmask[k] = best_mask;
     }
 }
 
@@ -172,6 +194,8 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
     const int32_t W = (n + 63) / 64;
     QC_TRY(g->comp.allocate(ctx, sizeof(int32_t) * (size_t)n, stream));
     QC_TRY(g->wcomp.allocate(ctx, sizeof(int32_t) * (size_t)W, stream));
+    QC_TRY(g->wmajor.allocate(ctx, sizeof(int32_t) * (size_t)W, stream));
+    QC_TRY(g->wmask.allocate(ctx, sizeof(unsigned long long) * (size_t)W, stream));
     QC_TRY(g->order.allocate(ctx, sizeof(int32_t) * (size_t)(n + 1), stream));
     QC_TRY(g->oinfo.allocate(ctx, sizeof(int4) * (size_t)n, stream));
     qc_buffer p, bins;
@@ -216,8 +240,9 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
     }
     cc_flatten<<<nb, tb, 0, stream>>>(n, p.as<int32_t>(), g->comp.as<int32_t>());
     QC_LAUNCHED(ctx);
-    word_components<<<qc_ceil_div(W, 128), 128, 0, stream>>>(n, W, g->comp.as<int32_t>(),
-                                                            g->wcomp.as<int32_t>());
+    word_components<<<qc_ceil_div(W, 128), 128, 0, stream>>>(n, W, g->comp.as<int32_t>(), g->wcomp.as<int32_t>(),
+                                                            g->wmajor.as<int32_t>(),
+                                                            g->wmask.as<unsigned long long>());
     QC_LAUNCHED(ctx);
     QC_CUDA_TRY(ctx, cudaMemsetAsync(bins.ptr, 0, bins.bytes, stream));
     bucket_count<<<nb, tb, 0, stream>>>(n, rp, bins.as<int32_t>());

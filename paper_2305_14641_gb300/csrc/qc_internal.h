@@ -155,6 +155,8 @@ struct qc_graph {
     bool prepared = false;
     qc_buffer comp;          // int32[n] component = smallest node id in it
     qc_buffer wcomp;         // int32[W] component of a whole 64-source word, or -1
+    qc_buffer wmajor;        // int32[W] the component holding most of a mixed word's sources
+    qc_buffer wmask;         // uint64[W] bits of the word's sources in that component
     qc_buffer order;         // int32[n] nodes, heaviest degree bucket first
     qc_buffer oinfo;         // int4[n]: {node, row start, row end, 0} at each order position
 };
