@@ -163,3 +163,51 @@ def test_batch_directed(qc, ctx):
     graphs = [gg.directed_erdos_renyi(int(n), 4.0 / n, g) for n in (40, 200, 700, 1500)] + \
         [gg.directed_cycle(100), gg.directed_path(90), gg.directed_planted_partition(1200, 5, 0.03, 0.002, g)]
     check_batch(qc, ctx, graphs, [0.8, 1.2, 1.7, 2.2, 1.0, 1.5, 0.9])
+
+
+def test_batch_config4_full_size_sampled(qc, ctx):
+    """The whole 4096-graph batch of the benchmark, in the configuration the
+    autotuner picks for it; the labels and cluster counts of 64 sampled graphs
+    (the largest, the smallest and a seeded sample) against the oracle."""
+    graphs, sigmas = gg.config4_batch(4096)
+    Gs = [qc.Graph.from_graph(ctx, g, validate=False) for g in graphs]
+    plan = qc.BatchPlan(ctx, Gs, sigmas)
+    counts = plan.run()
+    sizes = np.array([g.n for g in graphs])
+    pick = np.unique(np.concatenate([[int(np.argmax(sizes)), int(np.argmin(sizes))],
+                                     gg.rng(45).choice(len(graphs), 62, replace=False)]))
+    for k in pick:
+        ref = oracle.solve(graphs[k], [sigmas[k]], threads=oracle.default_threads())
+        assert np.array_equal(plan.labels_of(int(k)).cpu().numpy(), ref.labels[0]), graphs[k].name
+        assert counts[k] == ref.n_clusters[0]
+    plan.close()
+    for G in Gs:
+        G.close()
+
+
+def test_server_config5_stream_sampled(qc, ctx):
+    """The first 400 requests of the serving stream (N up to 65,536), all submitted
+    at once.  Sampled requests of up to 8192 nodes against the oracle; every other
+    sampled request against the single-graph path, itself checked against the
+    oracle elsewhere."""
+    reqs = gg.config5_requests(400)
+    graphs = [r.graph() for r in reqs]
+    with qc.Server(0) as srv:
+        ids = [srv.submit(g.row_ptr, g.col_idx, r.sigma) for g, r in zip(graphs, reqs)]
+        res = [srv.wait(i, timeout_ms=300000) for i in ids]
+        st = srv.stats()
+    assert st["completed"] == 400 and st["failed"] == 0
+    sizes = np.array([r.n for r in reqs])
+    pick = np.unique(np.concatenate([[int(np.argmax(sizes))], gg.rng(46).choice(400, 40, replace=False)]))
+    for k in pick:
+        g, s = graphs[k], reqs[k].sigma
+        if g.n <= 8192:
+            ref = oracle.solve(g, [s], threads=oracle.default_threads())
+            assert np.array_equal(res[k]["labels"], ref.labels[0]), g.name
+            assert res[k]["n_clusters"] == ref.n_clusters[0]
+        else:
+            G = qc.Graph.from_graph(ctx, g)
+            _, lab, nc = G.solve([s])
+            assert np.array_equal(res[k]["labels"], lab.cpu().numpy()[0]), g.name
+            assert res[k]["n_clusters"] == nc[0]
+            G.close()
