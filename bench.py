@@ -172,19 +172,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def profile_traffic(path=PROFILE):
-    """dram bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+def profile_value(key: str, path=PROFILE):
+    """A figure recorded in the committed ncu summary (`key: value`), if the summary
+    was taken on the current kernel source (else None)."""
     if not path or not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", text)
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not h:
         return None
     if kernel_source_sha256() != h.group(1):
         return None
     return float(m.group(1))
+
+
+def profile_traffic(path=PROFILE):
+    """dram bytes per launch from the committed ncu summary (None if stale)."""
+    return profile_value("traffic_bytes_per_launch", path)
 
 
 def measured_peak_gbs():
@@ -380,6 +385,11 @@ def bench_ours(args, graph, sigmas, spec):
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
                          "traffic": traffic,
+                         # the level at which the kernel actually works: bytes it reads from L2
+                         # per launch and L2 throughput as a share of its peak, from the same
+                         # ncu capture as `traffic`
+                         "l2_read_bytes": profile_value("l2_read_bytes_per_launch", spec["profile"]),
+                         "l2_throughput_frac": profile_value("l2_throughput_frac", spec["profile"]),
                          "model_bytes_per_launch": (kstats["model_bytes"] / kstats["launches"]
                                                     if kstats["launches"] else None),
                          "launches": kstats["launches"],
