@@ -447,7 +447,9 @@ def check_weighted(orc):
             fin = np.isfinite(fw[s])
             assert np.array_equal(np.isfinite(d), fin)
             assert np.allclose(d[fin], fw[s][fin], rtol=1e-12, atol=0), (graph.name, s)
-    for graph in [gg.planted_partition(120, 4, 0.15, 0.02, gg.rng(99)), gg.path(9), gg.star(11)]:
+    disconnected = gg.erdos_renyi(60, 0.03, gg.rng(96))
+    assert connected_components(adjacency(disconnected), directed=False)[0] > 1
+    for graph in [gg.planted_partition(120, 4, 0.15, 0.02, gg.rng(99)), gg.path(9), gg.star(11), disconnected]:
         h = orc.histograms(graph)
         ones = np.ones(graph.nnz)
         for sigma in (0.6, 1.5):

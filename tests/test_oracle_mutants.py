@@ -34,6 +34,12 @@ MUTANTS = {
     "last-index-tie-break": ("if (best < 0 || V[j] < V[best]) {", "if (best < 0 || V[j] <= V[best]) {"),
     "ascent-instead-of-descent": ("if (best < 0 || V[j] < V[best]) {", "if (best < 0 || V[j] > V[best]) {"),
     "label-is-node-not-root": ("label[i] = r;", "label[i] = i;"),
+    # the adjacency-distance and weighted forms
+    "adjacency-degree-as-distant": ("double h[3] = {1.0, (double)deg, (double)(n - 1 - deg)};",
+                                    "double h[3] = {1.0, (double)deg, (double)(n - deg)};"),
+    "weighted-hop-not-weight": ("double nd = dist[u] + w[e];", "double nd = dist[u] + 1.0;"),
+    "weighted-first-power": ("double d2 = d * d;", "double d2 = d;"),
+    "weighted-unreached-counted": ("if (!isfinite(d)) continue;", "if (!isfinite(d)) d = 0.0;"),
 }
 
 CHILD = r"""
