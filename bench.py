@@ -3,12 +3,17 @@
 sigma values, descent and roots for each).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload dcsbm16384|sbm262144|batch4096|serve]
+                    [--workload NAME]
 
-The other workloads: sbm262144 (one SBM of 262,144 nodes, sigma 1.5, the same
-line format; its CPU baseline is a bounded sample scaled to the whole graph),
-batch4096 (4096 small graphs, batched plan vs the plain path) and serve (a
-Poisson request stream through the serving loop, p50/p99).
+Other workloads, each printing its own JSON line: sbm262144 (one SBM of
+262,144 nodes, sigma 1.5, the same line format; its CPU baseline is a bounded
+sample scaled to the whole graph), directed16384 (a directed planted
+partition, same format), batch4096 (4096 small graphs, batched plan vs the
+plain path), serve (a Poisson request stream through the serving loop,
+p50/p99), adjacency16384 (the distance-0/1/M mode), weighted16384 (weighted
+shortest-path distances), fig3 (complete graphs of growing n, GPU vs oracle)
+and quality (modularity, ARI, FMI, NMI over the sigma sweep on planted
+partitions).
 
 Prints one JSON line.  `value` is clusterings/s (one clustering = one label
 vector for one (graph, sigma) pair) over all ranks, timed on the device with
@@ -49,15 +54,15 @@ PROFILE = os.path.join(ROOT, "profiles", "bfs_persistent_dcsbm16384.md")
 # kernel's DRAM traffic per launch, and how many nodes the CPU baseline samples
 # (None: the whole workload)
 SINGLE = {
-    "dcsbm16384": {"make": lambda: gg.config2(), "desc": WORKLOAD, "profile": PROFILE,
+    "dcsbm16384": {"make": lambda: gg.dcsbm16384(), "desc": WORKLOAD, "profile": PROFILE,
                    "cpu_sample_nodes": None, "steps": 200},
     "directed16384": {"make": lambda: (gg.directed_planted_partition(16384, 32, 16.0 * 0.9 / 511,
                                                                      16.0 * 0.1 / (16384 - 512), gg.rng(5, 1),
-                                                                     name="dpp-16384"), gg.config2_sigmas()),
+                                                                     name="dpp-16384"), gg.sigma_sweep16()),
                       "desc": ("directed16384: directed planted partition, N=16384, 32 blocks of 512, "
                                "mean out-degree 16, mixing 0.1, seed 5; the 16-value sigma sweep"),
                       "profile": None, "cpu_sample_nodes": None, "steps": 200},
-    "sbm262144": {"make": lambda: gg.config3(),
+    "sbm262144": {"make": lambda: gg.sbm262144(),
                   "desc": ("sbm-262144: SBM, N=262144, 256 equal communities of 1024, mean degree 20, "
                            "mixing 0.15, seed 2; sigma 1.5"),
                   "profile": os.path.join(ROOT, "profiles", "bfs_persistent_sbm262144.md"),
@@ -425,7 +430,7 @@ def bench_batch(args):
     """Batched plan vs the plain form (one graph at a time through qc_solve)."""
     import torch
     import paper_2305_14641_gb300 as qc
-    graphs, sigmas = gg.config4_batch(args.batch_graphs)
+    graphs, sigmas = gg.planted_batch(args.batch_graphs)
     ctx = qc.Context(0)
     Gs = [qc.Graph.from_graph(ctx, g, validate=False) for g in graphs]
     t0 = time.perf_counter()
@@ -473,7 +478,7 @@ def bench_serve(args):
     throughput, and the same requests solved serially with the plain form."""
     import threading as th
     import paper_2305_14641_gb300 as qc
-    reqs = gg.config5_requests(args.requests)
+    reqs = gg.sbm_request_stream(args.requests)
     graphs = [r.graph() for r in reqs]
     lat, results = {}, {}
     with qc.Server(0, large_workers=args.large_workers, large_sm_share=args.large_sm_share) as srv:
@@ -578,7 +583,7 @@ def bench_adjacency(args):
     descent and roots per step; no BFS.  Also the potential kernel alone against HBM."""
     import torch
     import paper_2305_14641_gb300 as qc
-    graph, sigmas = gg.config2()
+    graph, sigmas = gg.dcsbm16384()
     ctx = qc.Context(0)
     g = qc.Graph.from_graph(ctx, graph)
     S, n = len(sigmas), graph.n
@@ -620,7 +625,7 @@ def bench_weighted(args):
     import torch
     import oracle
     import paper_2305_14641_gb300 as qc
-    graph, sigmas = gg.config2()
+    graph, sigmas = gg.dcsbm16384()
     w = gg.edge_weights(graph, 0.5, 2.0, gg.rng(7, 1))
     ctx = qc.Context(0)
     g = qc.Graph.from_graph(ctx, graph)
@@ -725,7 +730,7 @@ def bench_quality(args):
     import torch
     import paper_2305_14641_gb300 as qc
     from paper_2305_14641_gb300 import metrics
-    sigmas = gg.config2_sigmas()
+    sigmas = gg.sigma_sweep16()
     ctx = qc.Context(0)
     out = {}
     for name, (n, m, k) in QUALITY_SHAPES.items():

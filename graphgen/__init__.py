@@ -28,8 +28,8 @@ import numpy as np
 __all__ = [
     "Graph", "rng", "csr_from_pairs", "block_sizes", "planted_partition",
     "sbm_mean_degree", "dcsbm", "complete", "path", "star", "two_cliques_bridge",
-    "erdos_renyi", "relabel", "config1", "config2", "config3", "config4_batch",
-    "config5_requests", "config2_sigmas", "Request", "csr_from_arcs", "directed_cycle",
+    "erdos_renyi", "relabel", "planted128", "dcsbm16384", "sbm262144", "planted_batch",
+    "sbm_request_stream", "sigma_sweep16", "Request", "csr_from_arcs", "directed_cycle",
     "directed_path", "directed_erdos_renyi", "directed_planted_partition", "edge_weights",
 ]
 
@@ -341,26 +341,26 @@ def relabel(graph: Graph, perm: np.ndarray) -> Graph:
     return Graph(graph.n, rp, ci, name=graph.name + "-relabelled")
 
 
-# --- the five workloads ------------------------------------------------------------------
+# --- the benchmark and test workloads -------------------------------------------------------
 
-def config1() -> tuple[Graph, list[float]]:
+def planted128() -> tuple[Graph, list[float]]:
     """Planted partition N=128, 4 blocks of 32, p_in=0.3, p_out=0.02, seed 0; sigma = 1.0."""
     return planted_partition(128, 4, 0.3, 0.02, rng(0, 1), name="pp-128"), [1.0]
 
 
-def config2_sigmas() -> list[float]:
+def sigma_sweep16() -> list[float]:
     """16 sigma values log-spaced from 0.5 to 4.0: sigma_k = 0.5 * 8^(k/15)."""
     return [0.5 * 8.0 ** (k / 15.0) for k in range(16)]
 
 
-def config2() -> tuple[Graph, list[float]]:
+def dcsbm16384() -> tuple[Graph, list[float]]:
     """DC-SBM N=16384, 32 equal communities, power-law expected degrees (exponent 2.5,
     mean 16, max 512), mixing 0.1, seed 1; the 16-value sigma sweep."""
     return (dcsbm(16384, 32, 2.5, 16.0, 512.0, 0.1, rng(1, 2), name="dcsbm-16384"),
-            config2_sigmas())
+            sigma_sweep16())
 
 
-def config3(n: int = 262144, k: int = 256) -> tuple[Graph, list[float]]:
+def sbm262144(n: int = 262144, k: int = 256) -> tuple[Graph, list[float]]:
     """Plain SBM N=262144, 256 equal communities, mean degree 20, mixing 0.15, seed 2; sigma 1.5."""
     nc = n // k
     p_in = 20.0 * 0.85 / (nc - 1)
@@ -368,7 +368,7 @@ def config3(n: int = 262144, k: int = 256) -> tuple[Graph, list[float]]:
     return planted_partition(n, k, p_in, p_out, rng(2, 3), name=f"sbm-{n}"), [1.5]
 
 
-def config4_batch(count: int = 4096, seed: int = 3, n_min: int = 32, n_max: int = 2048,
+def planted_batch(count: int = 4096, seed: int = 3, n_min: int = 32, n_max: int = 2048,
                   ) -> tuple[list[Graph], list[float]]:
     """Batch of planted-partition graphs: N = floor(exp(U(ln n_min, ln n_max))), k ~ U{2..16},
     p_in ~ U(0.1, 0.5), p_out = 0.02, sigma ~ U(0.5, 3.0); graph g draws from stream (seed, g)."""
@@ -400,7 +400,7 @@ class Request:
         return sbm_mean_degree(self.n, self.k, 12.0, 0.1, g, name=f"req-{self.index}")
 
 
-def config5_requests(count: int = 4000, rate: float = 200.0, seed: int = 4, n_min: int = 64,
+def sbm_request_stream(count: int = 4000, rate: float = 200.0, seed: int = 4, n_min: int = 64,
                      n_max: int = 65536) -> list[Request]:
     """Poisson request stream: exponential inter-arrival times at `rate` per second;
     N log-uniform in [n_min, n_max], k ~ U{4..min(64, N/4)}, mean degree 12, mixing 0.1,

@@ -84,7 +84,10 @@ size_t qc_context_bytes_in_use(const qc_ctx *ctx);
 /* Per-kernel timing, for measurement.  When enabled, the library brackets every
  * launch of its dominant kernels with CUDA events on the launching stream and
  * accumulates their durations and the modelled bytes each launch must move
- * (documented per kernel in the design notes).  Off by default. */
+ * (for the BFS, per level pass over a chunk of wn source words:
+ * 8 wn (E + 3N) bitset bytes + the CSR + one histogram row).  Names: "bfs_level"
+ * per launch, "bfs_pass_<l>" per level from device timestamps.  Off by
+ * default. */
 typedef struct {
     uint64_t launches;
     double total_ms;        /* sum of event-measured launch durations */

@@ -26,9 +26,12 @@
  *   5. cluster centers (Algorithm 3): the root each node's parent chain
  *      reaches, found iteratively with path compression.
  *
- * Readings of the paper taken here (unreachable pairs contribute nothing,
- * the self term has d = 0, strict descent, lowest-index tie-break, the
- * root id as the label) are listed with their reasons in the design notes.
+ * Readings of the paper taken here, where it is silent or garbled: an
+ * unreachable pair contributes nothing (its distance is infinite); the self
+ * term has d = 0 (Algorithm 1 sums over all n nodes); a node moves only to a
+ * strictly lower neighbour (the prose after Algorithm 4; equal potentials on a
+ * bridge must not merge two cliques); among equal minima the lowest index wins;
+ * the label is the root's id (Algorithm 3 returns the root).
  *
  * Floating point: IEEE binary64 throughout; compile with -ffp-contract=off so
  * that no multiply-add is fused.

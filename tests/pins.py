@@ -131,7 +131,7 @@ def check_histograms_library(orc):
 def check_histogram_identities(orc):
     """h_i(0) = 1, h_i(1) = deg(i), sum_d h_i(d) = |component(i)|,
     sum_i h_i(d) even for d >= 1, sum_i sum_d d h_i(d) = 2 x Wiener index."""
-    graphs = random_graphs(6, 20, 60, seed=13, p_lo=0.02, p_hi=0.2) + [gg.config1()[0]]
+    graphs = random_graphs(6, 20, 60, seed=13, p_lo=0.02, p_hi=0.2) + [gg.planted128()[0]]
     for graph in graphs:
         h = orc.histograms(graph)
         assert np.all(h[:, 0] == 1)

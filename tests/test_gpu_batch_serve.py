@@ -54,7 +54,7 @@ def check_batch(qc, ctx, graphs, sigmas, runs=2):
 
 
 def test_batch_planted(qc, ctx):
-    graphs, sigmas = gg.config4_batch(160)
+    graphs, sigmas = gg.planted_batch(160)
     check_batch(qc, ctx, graphs, sigmas)
 
 
@@ -62,7 +62,7 @@ def test_batch_planted(qc, ctx):
 def test_batch_fixed_config(qc, ctx, monkeypatch, threads, words):
     # every kernel configuration the autotuner may pick gives the oracle's labels
     monkeypatch.setenv("QCGRAPH_BATCH_CONFIG", f"{threads},{words}")
-    graphs, sigmas = gg.config4_batch(48)
+    graphs, sigmas = gg.planted_batch(48)
     Gs = [qc.Graph.from_graph(ctx, g) for g in graphs]
     plan = qc.BatchPlan(ctx, Gs, sigmas)
     assert plan.config() == {"threads": threads, "chunk_words": words}
@@ -85,7 +85,7 @@ def test_batch_edge_cases_and_deep_graph(qc, ctx):
 
 
 def test_solve_batch_one_shot(qc, ctx):
-    graphs, sigmas = gg.config4_batch(20, seed=9)
+    graphs, sigmas = gg.planted_batch(20, seed=9)
     Gs = [qc.Graph.from_graph(ctx, g) for g in graphs]
     labels, offsets = qc.solve_batch(ctx, Gs, sigmas)
     lab = labels.cpu().numpy()
@@ -95,7 +95,7 @@ def test_solve_batch_one_shot(qc, ctx):
 
 
 def serve_requests(count, seed=4):
-    reqs = gg.config5_requests(count, seed=seed, n_max=12000)
+    reqs = gg.sbm_request_stream(count, seed=seed, n_max=12000)
     return [(r.graph(), r.sigma) for r in reqs]
 
 
@@ -165,11 +165,11 @@ def test_batch_directed(qc, ctx):
     check_batch(qc, ctx, graphs, [0.8, 1.2, 1.7, 2.2, 1.0, 1.5, 0.9])
 
 
-def test_batch_config4_full_size_sampled(qc, ctx):
+def test_batch4096_full_size_sampled(qc, ctx):
     """The whole 4096-graph batch of the benchmark, in the configuration the
     autotuner picks for it; the labels and cluster counts of 64 sampled graphs
     (the largest, the smallest and a seeded sample) against the oracle."""
-    graphs, sigmas = gg.config4_batch(4096)
+    graphs, sigmas = gg.planted_batch(4096)
     Gs = [qc.Graph.from_graph(ctx, g, validate=False) for g in graphs]
     plan = qc.BatchPlan(ctx, Gs, sigmas)
     counts = plan.run()
@@ -185,12 +185,12 @@ def test_batch_config4_full_size_sampled(qc, ctx):
         G.close()
 
 
-def test_server_config5_stream_sampled(qc, ctx):
+def test_server_request_stream_sampled(qc, ctx):
     """The first 400 requests of the serving stream (N up to 65,536), all submitted
     at once.  Sampled requests of up to 8192 nodes against the oracle; every other
     sampled request against the single-graph path, itself checked against the
     oracle elsewhere."""
-    reqs = gg.config5_requests(400)
+    reqs = gg.sbm_request_stream(400)
     graphs = [r.graph() for r in reqs]
     with qc.Server(0) as srv:
         ids = [srv.submit(g.row_ptr, g.col_idx, r.sigma) for g, r in zip(graphs, reqs)]

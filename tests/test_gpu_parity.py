@@ -51,8 +51,8 @@ def assert_solution_matches(qc, ctx, graph, sigmas, threads=None):
     return ref
 
 
-def test_config1(qc, ctx):
-    graph, sigmas = gg.config1()
+def test_planted128(qc, ctx):
+    graph, sigmas = gg.planted128()
     assert_solution_matches(qc, ctx, graph, sigmas + [0.5, 0.8, 2.0, 4.0])
 
 
@@ -90,16 +90,16 @@ def test_planted_and_dcsbm_mid(qc, ctx):
     g1 = gg.planted_partition(4000, 16, 0.02, 0.0005, gg.rng(23))
     g2 = gg.dcsbm(3000, 8, 2.5, 10.0, 200.0, 0.1, gg.rng(24))
     for graph in (g1, g2):
-        assert_solution_matches(qc, ctx, graph, gg.config2_sigmas()[::3])
+        assert_solution_matches(qc, ctx, graph, gg.sigma_sweep16()[::3])
 
 
-def test_config2_full(qc, ctx):
+def test_dcsbm16384_full(qc, ctx):
     """DC-SBM N=16384 with the 16-value sigma sweep, every node checked."""
-    graph, sigmas = gg.config2()
+    graph, sigmas = gg.dcsbm16384()
     assert_solution_matches(qc, ctx, graph, sigmas)
 
 
-def test_config3_full_size_sampled(qc, ctx):
+def test_sbm262144_full_size_sampled(qc, ctx):
     """SBM N=262144 (5.24M directed edges) at full size.  The oracle's per-source
     BFS is too slow for every node, so: histogram rows of sampled nodes (random,
     first, last, extreme degrees) bit-exact against the oracle; invariants at every
@@ -109,7 +109,7 @@ def test_config3_full_size_sampled(qc, ctx):
     oracle's descent and roots run on those potentials."""
     from scipy.sparse import csr_matrix
     from scipy.sparse.csgraph import connected_components
-    graph, sigmas = gg.config3()
+    graph, sigmas = gg.sbm262144()
     n = graph.n
     g = qc.Graph.from_graph(ctx, graph)
     hist = g.histogram().cpu().numpy()
@@ -219,7 +219,7 @@ def test_bounded_wait_gives_up(qc, ctx):
     assert ctx.selftest_barrier_timeout(1 << 14) == "QC_ERR_TIMEOUT"
     assert time.perf_counter() - t0 < 30.0
     assert ctx.selftest_barrier_timeout(0) == "QC_ERR_INVALID_ARG"
-    graph, sigmas = gg.config1()
+    graph, sigmas = gg.planted128()
     assert_solution_matches(qc, ctx, graph, sigmas)
 
 
@@ -257,7 +257,7 @@ def test_many_sigmas_in_groups(qc, ctx):
 def test_adjacency_mode(qc, ctx, M):
     """Paper-literal distance: potentials and labels equal the oracle's bit for bit."""
     sigmas = [0.5, 1.0, 2.0]
-    for graph in [gg.config1()[0], gg.erdos_renyi(700, 0.01, gg.rng(30)), gg.star(50, 3)]:
+    for graph in [gg.planted128()[0], gg.erdos_renyi(700, 0.01, gg.rng(30)), gg.star(50, 3)]:
         G = qc.Graph.from_graph(ctx, graph)
         V = G.potential_adjacency(sigmas, M)
         labels, counts = G.ggd_labels(V)

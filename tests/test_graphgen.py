@@ -27,12 +27,12 @@ def test_structured_graphs():
     assert gg.two_cliques_bridge(4).nnz == 2 * 12 + 2
 
 
-def test_config1_shape_and_determinism():
-    g, sig = gg.config1()
+def test_planted128_shape_and_determinism():
+    g, sig = gg.planted128()
     assert_canonical(g)
     assert g.n == 128 and sig == [1.0]
     assert 1000 < g.nnz < 1900          # about 718 undirected edges expected
-    g2, _ = gg.config1()
+    g2, _ = gg.planted128()
     assert np.array_equal(g.col_idx, g2.col_idx)
 
 
@@ -48,24 +48,24 @@ def test_planted_partition_rates():
 
 
 def test_sigma_sweep():
-    s = gg.config2_sigmas()
+    s = gg.sigma_sweep16()
     assert len(s) == 16 and s[0] == 0.5 and abs(s[-1] - 4.0) < 1e-12
     assert all(b > a for a, b in zip(s, s[1:]))
 
 
 def test_batch_and_requests():
-    graphs, sig = gg.config4_batch(24)
+    graphs, sig = gg.planted_batch(24)
     for g, s in zip(graphs, sig):
         assert_canonical(g)
         assert 32 <= g.n <= 2048 and 0.5 <= s <= 3.0
-    reqs = gg.config5_requests(40)
+    reqs = gg.sbm_request_stream(40)
     assert all(64 <= r.n <= 65536 and 0.5 <= r.sigma <= 3.0 for r in reqs)
     assert all(b.arrival_s > a.arrival_s for a, b in zip(reqs, reqs[1:]))
     assert_canonical(reqs[0].graph())
 
 
 @pytest.mark.slow
-def test_config2_shape():
-    g, _ = gg.config2()
+def test_dcsbm16384_shape():
+    g, _ = gg.dcsbm16384()
     assert_canonical(g)
     assert g.n == 16384 and abs(g.degrees().mean() - 16) < 1.0 and g.degrees().max() <= 600

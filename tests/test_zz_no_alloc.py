@@ -46,7 +46,7 @@ def static_histogram(lib, graph, max_levels):
 
 
 CASES = [
-    ("planted N=128", lambda: gg.config1()[0]),
+    ("planted N=128", lambda: gg.planted128()[0]),
     ("ragged N=1000, sparse", lambda: gg.erdos_renyi(1000, 0.004, gg.rng(31))),
     ("planted N=5000", lambda: gg.planted_partition(5000, 10, 0.01, 0.0004, gg.rng(32))),
     ("path N=70", lambda: gg.path(70)),
