@@ -661,6 +661,7 @@ qc_status qc_batch_create(qc_ctx *ctx, int32_t n_graphs, qc_graph *const *graphs
 }
 
 qc_status qc_batch_run(qc_batch *b, int32_t *n_clusters_out, void *stream_) {
+    qc_range range("qc.batch_run");
     if (!b) return QC_ERR_INVALID_ARG;
     qc_ctx *ctx = b->ctx;
     cudaStream_t stream = qc_stream(stream_);

@@ -475,6 +475,7 @@ int32_t qc_bfs_chunk_words(const qc_ctx *ctx, int32_t n) {
 }
 
 qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
+    qc_range range("qc.bfs");
     qc_ctx *ctx = g->ctx;
     const int32_t n = g->n;
     const int32_t W = (n + 63) / 64;

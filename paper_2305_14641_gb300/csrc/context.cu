@@ -174,6 +174,7 @@ size_t qc_context_bytes_in_use(const qc_ctx *ctx) { return ctx ? ctx->in_use.loa
 
 qc_status qc_graph_create(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
                           const int32_t *col_idx, uint32_t flags, void *stream_, qc_graph **out) {
+    qc_range range("qc.graph_create");
     if (!ctx || !out) return QC_ERR_INVALID_ARG;
     *out = nullptr;
     if (n < 1 || nnz < 0 || nnz >= (int64_t(1) << 31) || !row_ptr || (nnz > 0 && !col_idx)) {
@@ -300,6 +301,7 @@ qc_status qc_potential(qc_graph *g, const double *sigmas, int32_t n_sigma, doubl
 
 qc_status qc_ggd_labels(qc_graph *g, const double *V, int32_t n_sigma, int32_t *labels_out,
                         int32_t *n_clusters_out, void *stream_) {
+    qc_range range("qc.ggd");
     if (!g || !V || n_sigma < 1 || !labels_out) {
         if (g) qc_set_error(g->ctx, "qc_ggd_labels: null pointer or n_sigma < 1");
         return QC_ERR_INVALID_ARG;
@@ -323,6 +325,7 @@ qc_status qc_ggd_labels(qc_graph *g, const double *V, int32_t n_sigma, int32_t *
 
 qc_status qc_solve(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
                    int32_t *labels_out, int32_t *n_clusters_out, void *stream_) {
+    qc_range range("qc.solve");
     if (!g || !sigmas || n_sigma < 1 || !labels_out) return QC_ERR_INVALID_ARG;
     cudaStream_t stream = qc_stream(stream_);
     qc_buffer Vtmp;

@@ -133,6 +133,7 @@ extern "C" qc_status qc_potential_adjacency(qc_graph *g, const double *sigmas, i
 
 qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V,
                                  cudaStream_t stream) {
+    qc_range range("qc.potential");
     qc_ctx *ctx = g->ctx;
     const int32_t L = g->D + 1;
     std::vector<double> tab((size_t)n_sigma * (2 * L + 1));

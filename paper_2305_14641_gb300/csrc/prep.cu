@@ -189,6 +189,7 @@ qc_status qc_fill_first_rows(qc_graph *g, cudaStream_t stream) {
 
 qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
     if (g->prepared) return QC_OK;
+    qc_range range("qc.prepare");
     qc_ctx *ctx = g->ctx;
     const int32_t n = g->n;
     const int32_t W = (n + 63) / 64;

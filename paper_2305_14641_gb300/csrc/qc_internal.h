@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cstdint>
@@ -70,6 +71,17 @@ struct qc_event_pair {
         if (a) cudaEventDestroy(a);
         if (b) cudaEventDestroy(b);
     }
+};
+
+// An NVTX range around one phase of the method (graph upload, preparation,
+// BFS, potential, descent, batch run, shortest paths), for profilers that read
+// NVTX (ncu --nvtx, Nsight Systems).  Without such a tool attached a push or
+// pop costs a function call.
+struct qc_range {
+    explicit qc_range(const char *name) { nvtxRangePushA(name); }
+    ~qc_range() { nvtxRangePop(); }
+    qc_range(const qc_range &) = delete;
+    qc_range &operator=(const qc_range &) = delete;
 };
 
 // Count one launch (and surface launch-configuration errors).

@@ -295,6 +295,7 @@ extern "C" qc_status qc_graph_set_weights(qc_graph *g, const double *w, uint32_t
 
 extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
                                            void *stream_) {
+    qc_range range("qc.potential_weighted");
     if (!g || !sigmas || n_sigma < 1 || !V_out) return QC_ERR_INVALID_ARG;
     qc_ctx *ctx = g->ctx;
     if (!g->weighted) {
