@@ -20,75 +20,87 @@
 
 namespace {
 
-// Connected components by hooking and shortcutting (after Shiloach & Vishkin),
-// all iterations in one cooperative launch.  L[v] always names a node of v's
-// component with id <= v, and labels only decrease:
-//   hook:     for every edge (v, u) with a = L[v] > b = L[u]: L[a] = min(L[a], b);
-//   shortcut: L[v] = L[L[v]] until L[v] is a root (L[L[v]] = L[v]).
-// An iteration in which no hook lowers a label leaves every edge's two ends with
-// the same root label, which is then the smallest id of the component.
-// A directed graph lists each edge in one row only, so there the hook runs in
-// both directions (a < b: L[b] = min(L[b], a)) and the result is the weakly
-// connected components, which bound what any node can reach.
-// ctl: [0] status, [1] iterations run, [2..3] barrier, [8 + it] "a hook changed
-// something in iteration it".
-__global__ void __launch_bounds__(256) cc_persistent(int32_t n, const int32_t *row_ptr,
-                                                     const int32_t *col_idx, int32_t *L, int32_t *ctl,
-                                                     int32_t max_iters, int32_t resume, int32_t directed) {
+// Connected components by sampled union-find (after Sutton et al., "Optimizing
+// Parallel Graph Connectivity Computation via Subgraph Sampling", 2018), in
+// one cooperative launch:
+//   1. every node links to its first and then its second neighbour (lock-free
+//      union: a root is attached below a smaller root by compare-and-swap, so
+//      every root is the smallest id of its tree), compressing after each round;
+//   2. the label shared by most of 64 evenly spaced nodes names the largest
+//      component found so far;
+//   3. nodes outside that component link to their remaining neighbours; nodes
+//      inside it skip theirs (in an undirected graph the other end of each such
+//      edge, if outside, links it), and a final compression leaves every node
+//      pointing at its root, the smallest id of its component.
+// A directed graph lists an arc in one row only, so there every node links all
+// its arcs (the result: weakly connected components).
+__device__ __forceinline__ void uf_link(int32_t *L, int u, int v) {
+    volatile int32_t *VL = L;
+    int p1 = VL[u], p2 = VL[v];
+    while (p1 != p2) {
+        const int high = max(p1, p2), low = min(p1, p2);
+        const int ph = VL[high];
+        if (ph == low) break;
+        if (ph == high && atomicCAS(L + high, high, low) == high) break;
+        p1 = VL[VL[high]];
+        p2 = VL[low];
+    }
+}
+
+__device__ __forceinline__ void uf_compress(int32_t *L, int n, int tid, int nthreads) {
+    volatile int32_t *VL = L;
+    for (int v = tid; v < n; v += nthreads) {
+        int x = VL[v];
+        while (VL[x] != x) x = VL[x];
+        VL[v] = x;
+    }
+}
+
+__global__ void __launch_bounds__(256) cc_afforest(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                                                   int32_t *L, int32_t *ctl, int32_t directed) {
     unsigned *bar = reinterpret_cast<unsigned *>(ctl + 2);
-    const int lane = threadIdx.x & 31;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
-    const int warp = tid >> 5;
-    const int nwarps = nthreads >> 5;
-    if (!resume) {
-        // start at the smallest neighbour when smaller (Jaiganesh & Burtscher, ECL-CC, 2018)
+    for (int v = tid; v < n; v += nthreads) L[v] = v;
+    if (!qcdev::grid_barrier(bar, ctl)) return;
+    for (int r = 0; r < 2; ++r) {
         for (int v = tid; v < n; v += nthreads) {
-            int m = v;
-            const int end = row_ptr[v + 1];
-            for (int e = row_ptr[v]; e < end; ++e) m = min(m, col_idx[e]);
-            L[v] = m;
+            const int e = row_ptr[v] + r;
+            if (e < row_ptr[v + 1]) uf_link(L, v, col_idx[e]);
         }
         if (!qcdev::grid_barrier(bar, ctl)) return;
-    }
-    volatile int32_t *VL = L;
-    for (int it = 0; it < max_iters; ++it) {
-        // shortcut
-        for (int v = tid; v < n; v += nthreads) {
-            int x = VL[v];
-            int y = VL[x];
-            while (x != y) {
-                x = y;
-                y = VL[x];
-            }
-            VL[v] = x;
-        }
+        uf_compress(L, n, tid, nthreads);
         if (!qcdev::grid_barrier(bar, ctl)) return;
-        // hook
-        bool changed = false;
-        for (int v = warp; v < n; v += nwarps) {
-            const int a = VL[v];
-            const int end = row_ptr[v + 1];
-            for (int e = row_ptr[v] + lane; e < end; e += 32) {
-                const int b = VL[col_idx[e]];
-                if (b < a) {
-                    if (atomicMin(L + a, b) > b) changed = true;
-                } else if (directed && a < b) {
-                    if (atomicMin(L + b, a) > a) changed = true;
-                }
-            }
+    }
+    // the most common label among 64 evenly spaced nodes
+    __shared__ int s_lab[64], s_cnt[64];
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < 64) s_lab[threadIdx.x] = L[(int)(((long long)threadIdx.x * (n - 1)) / 63)];
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            int c = 0;
+            for (int i = 0; i < 64; ++i) c += (s_lab[i] == s_lab[threadIdx.x]);
+            s_cnt[threadIdx.x] = c;
         }
-        if (__syncthreads_or(changed) && threadIdx.x == 0) ctl[8 + it] = 1;
-        if (!qcdev::grid_barrier(bar, ctl)) return;
-        if (*(volatile int32_t *)(ctl + 8 + it) == 0) {
-            if (tid == 0) ctl[1] = it + 1;
-            return;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int best = 0;
+            for (int i = 1; i < 64; ++i)
+                if (s_cnt[i] > s_cnt[best]) best = i;
+            ctl[4] = directed ? -1 : s_lab[best];
         }
     }
-    if (tid == 0) {
-        ctl[1] = max_iters;
-        ctl[0] = qcdev::ST_NEED_ROWS;     // not converged yet: run again
+    if (!qcdev::grid_barrier(bar, ctl)) return;
+    const int giant = *(volatile int32_t *)(ctl + 4);
+    const int lane = threadIdx.x & 31;
+    for (int v = tid >> 5; v < n; v += nthreads >> 5) {
+        if (*(volatile int32_t *)(L + v) == giant) continue;
+        const int end = row_ptr[v + 1];
+        for (int e = row_ptr[v] + 2 + lane; e < end; e += 32) uf_link(L, v, col_idx[e]);
     }
+    if (!qcdev::grid_barrier(bar, ctl)) return;
+    uf_compress(L, n, tid, nthreads);
+    if (tid == 0) ctl[1] = 1;
 }
 
 // Final labels: the root of each node's label chain.
@@ -209,34 +221,28 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
     const int32_t *ci = g->col_idx.as<int32_t>();
     {
         int per_sm = 0;
-        QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)cc_persistent,
+        QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)cc_afforest,
                                                                        256, 0));
         int blocks = per_sm * qc_coop_sms(ctx);
         if (blocks > wb) blocks = wb;
         if (blocks < 1) blocks = 1;
         qc_buffer ctl;
-        const int32_t max_iters = 512;
-        QC_TRY(ctl.allocate(ctx, sizeof(int32_t) * (8 + max_iters), stream));
+        QC_TRY(ctl.allocate(ctx, sizeof(int32_t) * 8, stream));
         qc_pinned pin(ctx);
         QC_TRY(pin.acquire());
         int32_t *h = static_cast<int32_t *>(pin.ptr);
-        int32_t resume = 0;
-        while (true) {
-            QC_CUDA_TRY(ctx, cudaMemsetAsync(ctl.ptr, 0, ctl.bytes, stream));
-            int32_t n_ = n, iters = max_iters, directed = g->directed ? 1 : 0;
-            int32_t *L = p.as<int32_t>(), *c = ctl.as<int32_t>();
-            void *args[] = {&n_, (void *)&rp, (void *)&ci, &L, &c, &iters, &resume, &directed};
-            QC_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)cc_persistent, dim3(blocks), dim3(256),
-                                                         args, 0, stream));
-            QC_LAUNCHED(ctx);
-            QC_CUDA_TRY(ctx, cudaMemcpyAsync(h, ctl.ptr, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
-            QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
-            if (h[0] == qcdev::ST_TIMEOUT) {
-                qc_set_error(ctx, "connected components: grid barrier timed out");
-                return QC_ERR_TIMEOUT;
-            }
-            if (h[0] == qcdev::ST_DONE) break;
-            resume = 1;
+        QC_CUDA_TRY(ctx, cudaMemsetAsync(ctl.ptr, 0, ctl.bytes, stream));
+        int32_t n_ = n, directed = g->directed ? 1 : 0;
+        int32_t *L = p.as<int32_t>(), *c = ctl.as<int32_t>();
+        void *args[] = {&n_, (void *)&rp, (void *)&ci, &L, &c, &directed};
+        QC_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)cc_afforest, dim3(blocks), dim3(256), args, 0,
+                                                     stream));
+        QC_LAUNCHED(ctx);
+        QC_CUDA_TRY(ctx, cudaMemcpyAsync(h, ctl.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+        QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        if (h[0] == qcdev::ST_TIMEOUT) {
+            qc_set_error(ctx, "connected components: grid barrier timed out");
+            return QC_ERR_TIMEOUT;
         }
     }
     cc_flatten<<<nb, tb, 0, stream>>>(n, p.as<int32_t>(), g->comp.as<int32_t>());
