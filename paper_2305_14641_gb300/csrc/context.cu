@@ -220,7 +220,7 @@ qc_status qc_graph_create(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *ro
     }
     if (flags & QC_VALIDATE) {
         st = qc_validate_csr(ctx, n, nnz, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(), !g->directed,
-                             stream);
+                             !on_device, stream);
         if (st != QC_OK) {
             delete g;
             return st;

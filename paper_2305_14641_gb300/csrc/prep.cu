@@ -116,30 +116,47 @@ __global__ void cc_flatten(int32_t n, const int32_t *L, int32_t *comp) {
 // component holding most of them (wmajor) and their bits (wmask), so that the
 // BFS presets the row of a node in that component with one mask and walks the
 // word bit by bit only for nodes of the word's minor components.
+// One warp per word: a vote settles the common case of a word inside one
+// component; lane 0 counts the components of a mixed word.
 __global__ void word_components(int32_t n, int32_t W, const int32_t *comp, int32_t *wcomp, int32_t *wmajor,
                                 unsigned long long *wmask) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < W; k += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int k = warp; k < W; k += nwarps) {
         const int s0 = 64 * k;
         const int cnt = min(64, n - s0);
-        int best = comp[s0], best_count = 0;
-        unsigned long long best_mask = 0ull, seen = 0ull;
-        for (int b = 0; b < cnt; ++b) {
-            if ((seen >> b) & 1ull) continue;
-            const int c = comp[s0 + b];
-            unsigned long long m = 0ull;
-            for (int b2 = b; b2 < cnt; ++b2)
-                if (comp[s0 + b2] == c) m |= 1ull << b2;
-            seen |= m;
-            const int pc = __popcll(m);
-            if (pc > best_count) {
-                best = c;
-                best_count = pc;
-                best_mask = m;
+        const int c0 = comp[s0];
+        const bool same = (lane >= cnt || comp[s0 + lane] == c0) && (lane + 32 >= cnt || comp[s0 + 32 + lane] == c0);
+        const bool whole = __all_sync(0xffffffffu, same);
+        if (lane == 0) {
+            if (whole) {
+                wcomp[k] = c0;
+                wmajor[k] = c0;
+                wmask[k] = cnt == 64 ? ~0ull : ((1ull << cnt) - 1);
+            } else {
+                int best = c0, best_count = 0;
+                unsigned long long best_mask = 0ull, seen = 0ull;
+                for (int b = 0; b < cnt; ++b) {
+                    if ((seen >> b) & 1ull) continue;
+                    const int c = comp[s0 + b];
+                    unsigned long long m = 0ull;
+                    for (int b2 = b; b2 < cnt; ++b2)
+                        if (comp[s0 + b2] == c) m |= 1ull << b2;
+                    seen |= m;
+                    const int pc = __popcll(m);
+                    if (pc > best_count) {
+                        best = c;
+                        best_count = pc;
+                        best_mask = m;
+                    }
+                }
+                wcomp[k] = -1;
+                wmajor[k] = best;
+                wmask[k] = best_mask;
             }
         }
-        wcomp[k] = (best_count == cnt) ? best : -1;
-        wmajor[k] = best;
-        wmask[k] = best_mask;
+        __syncwarp();
     }
 }
 
@@ -247,7 +264,7 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
     }
     cc_flatten<<<nb, tb, 0, stream>>>(n, p.as<int32_t>(), g->comp.as<int32_t>());
     QC_LAUNCHED(ctx);
-    word_components<<<qc_ceil_div(W, 128), 128, 0, stream>>>(n, W, g->comp.as<int32_t>(), g->wcomp.as<int32_t>(),
+    word_components<<<qc_ceil_div(W, 8), 256, 0, stream>>>(n, W, g->comp.as<int32_t>(), g->wcomp.as<int32_t>(),
                                                             g->wmajor.as<int32_t>(),
                                                             g->wmask.as<unsigned long long>());
     QC_LAUNCHED(ctx);

@@ -216,8 +216,9 @@ int32_t *qc_cta_flags(qc_cta_launch *L);
 void qc_cta_launch_free(qc_cta_launch *L);
 
 // validate.cu
+// row_ptr_checked: the caller already checked row_ptr on the host (skip that pass).
 qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
-                          const int32_t *col_idx_dev, bool symmetric, cudaStream_t stream);
+                          const int32_t *col_idx_dev, bool symmetric, bool row_ptr_checked, cudaStream_t stream);
 qc_status qc_validate_hist(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
                            const int32_t *hist_dev, int32_t D, cudaStream_t stream);
 

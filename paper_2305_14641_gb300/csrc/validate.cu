@@ -110,19 +110,22 @@ qc_status qc_validate_hist(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
 }
 
 qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
-                          const int32_t *col_idx, bool symmetric, cudaStream_t stream) {
+                          const int32_t *col_idx, bool symmetric, bool row_ptr_checked, cudaStream_t stream) {
     qc_buffer err;
     QC_TRY(err.allocate(ctx, sizeof(int32_t), stream));
     QC_CUDA_TRY(ctx, cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), stream));
     int32_t h_err = 0;
-    const int blocks = qc_ceil_div(n, 256) < 4 * ctx->num_sms ? qc_ceil_div(n, 256) : 4 * ctx->num_sms;
-    check_row_ptr<<<blocks, 256, 0, stream>>>(n, nnz, row_ptr, err.as<int32_t>());
-    QC_LAUNCHED(ctx);
-    QC_CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
-    QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
-    if (h_err) {
-        qc_set_error(ctx, "invalid CSR: row_ptr is not 0-based, non-decreasing and ending at nnz");
-        return QC_ERR_INVALID_GRAPH;
+    if (!row_ptr_checked) {
+        // the row scan indexes through row_ptr, so row_ptr is checked (and waited for) first
+        const int blocks = qc_ceil_div(n, 256) < 4 * ctx->num_sms ? qc_ceil_div(n, 256) : 4 * ctx->num_sms;
+        check_row_ptr<<<blocks, 256, 0, stream>>>(n, nnz, row_ptr, err.as<int32_t>());
+        QC_LAUNCHED(ctx);
+        QC_CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+        QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        if (h_err) {
+            qc_set_error(ctx, "invalid CSR: row_ptr is not 0-based, non-decreasing and ending at nnz");
+            return QC_ERR_INVALID_GRAPH;
+        }
     }
     if (nnz == 0) return QC_OK;
     const int wblocks = qc_ceil_div(n, 8) < 8 * ctx->num_sms ? qc_ceil_div(n, 8) : 8 * ctx->num_sms;
