@@ -486,6 +486,12 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
     if (g->nnz == 0) {
         // no edges: h(0) = 1 for every node, nothing else
         QC_TRY(qc_fill_first_rows(g, stream));
+        if (!g->prep_checked) {
+            int32_t st = 0;
+            QC_CUDA_TRY(ctx, cudaMemcpyAsync(&st, g->prep_ctl.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+            QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+            QC_TRY(qc_graph_prepare_status(g, st));
+        }
         g->hist_valid = true;
         return QC_OK;
     }
@@ -575,6 +581,10 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
             if (timing) QC_CUDA_TRY(ctx, cudaEventRecord(ev.b, stream));
             QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_status, ctl.ptr, 2 * sizeof(int32_t),
                                              cudaMemcpyDeviceToHost, stream));
+            // the preparation's status rides in the same wait (slot 2 of the pinned block)
+            if (!g->prep_checked)
+                QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_status + 2, g->prep_ctl.ptr, sizeof(int32_t),
+                                                 cudaMemcpyDeviceToHost, stream));
             // level stamps ride in the same pinned block, after the status words
             unsigned long long *h_stamp = reinterpret_cast<unsigned long long *>(
                 static_cast<char *>(pin.ptr) + 64);
@@ -584,6 +594,7 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
                                                  cudaMemcpyDeviceToHost, stream));
             QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
             const int32_t st = h_status[0], reached = h_status[1];
+            QC_TRY(qc_graph_prepare_status(g, h_status[2]));
             if (timing) {
                 float ms = 0.f;
                 QC_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ev.a, ev.b));

@@ -243,24 +243,15 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
         int blocks = per_sm * qc_coop_sms(ctx);
         if (blocks > wb) blocks = wb;
         if (blocks < 1) blocks = 1;
-        qc_buffer ctl;
-        QC_TRY(ctl.allocate(ctx, sizeof(int32_t) * 8, stream));
-        qc_pinned pin(ctx);
-        QC_TRY(pin.acquire());
-        int32_t *h = static_cast<int32_t *>(pin.ptr);
-        QC_CUDA_TRY(ctx, cudaMemsetAsync(ctl.ptr, 0, ctl.bytes, stream));
+        QC_TRY(g->prep_ctl.allocate(ctx, sizeof(int32_t) * 8, stream));
+        QC_CUDA_TRY(ctx, cudaMemsetAsync(g->prep_ctl.ptr, 0, g->prep_ctl.bytes, stream));
         int32_t n_ = n, directed = g->directed ? 1 : 0;
-        int32_t *L = p.as<int32_t>(), *c = ctl.as<int32_t>();
+        int32_t *L = p.as<int32_t>(), *c = g->prep_ctl.as<int32_t>();
         void *args[] = {&n_, (void *)&rp, (void *)&ci, &L, &c, &directed};
         QC_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)cc_afforest, dim3(blocks), dim3(256), args, 0,
                                                      stream));
         QC_LAUNCHED(ctx);
-        QC_CUDA_TRY(ctx, cudaMemcpyAsync(h, ctl.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
-        QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
-        if (h[0] == qcdev::ST_TIMEOUT) {
-            qc_set_error(ctx, "connected components: grid barrier timed out");
-            return QC_ERR_TIMEOUT;
-        }
+        g->prep_checked = false;
     }
     cc_flatten<<<nb, tb, 0, stream>>>(n, p.as<int32_t>(), g->comp.as<int32_t>());
     QC_LAUNCHED(ctx);
@@ -279,5 +270,16 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
     order_info<<<nb, tb, 0, stream>>>(n, rp, g->order.as<int32_t>(), g->oinfo.as<int4>());
     QC_LAUNCHED(ctx);
     g->prepared = true;
+    return QC_OK;
+}
+
+qc_status qc_graph_prepare_status(qc_graph *g, int32_t host_status) {
+    if (g->prep_checked) return QC_OK;
+    if (host_status == qcdev::ST_TIMEOUT) {
+        qc_set_error(g->ctx, "connected components: grid barrier timed out");
+        g->prepared = false;          // prepare again next time
+        return QC_ERR_TIMEOUT;
+    }
+    g->prep_checked = true;
     return QC_OK;
 }

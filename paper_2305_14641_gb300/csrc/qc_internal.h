@@ -165,6 +165,8 @@ struct qc_graph {
     qc_buffer hist;          // int32[hist_rows][n], level-major
     // preparation (see prep.cu), computed once
     bool prepared = false;
+    bool prep_checked = false;   // the components launch's status has been read
+    qc_buffer prep_ctl;      // int32[8]: status and grid barrier of that launch
     qc_buffer comp;          // int32[n] component = smallest node id in it
     qc_buffer wcomp;         // int32[W] component of a whole 64-source word, or -1
     qc_buffer wmajor;        // int32[W] the component holding most of a mixed word's sources
@@ -177,7 +179,13 @@ struct qc_graph {
 // Degree bucket (floor(log2(deg + 1))) from which a row counts as heavy: its BFS
 // item is shared by all warps of a block instead of one warp.
 #define QC_HEAVY_BUCKET 7
+// Queues the preparation kernels without waiting; the components launch's
+// status stays on the device until qc_graph_prepare_status reads it (the BFS
+// reads it in the same wait as its own status).
 qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream);
+// QC_OK or QC_ERR_TIMEOUT from the last preparation, given its status word as
+// copied to the host after a wait.
+qc_status qc_graph_prepare_status(qc_graph *g, int32_t host_status);
 // hist[0][v] = 1, hist[1][v] = deg(v)
 qc_status qc_fill_first_rows(qc_graph *g, cudaStream_t stream);
 // bfs.cu helpers shared with the batched paths
