@@ -72,6 +72,29 @@ def test_structured(qc, ctx):
         assert_solution_matches(qc, ctx, graph, [0.5, 1.0, 3.0])
 
 
+def test_hubs_and_long_rows(qc, ctx):
+    """A star with 20,000 leaves (one row of 20k neighbours: a block-shared item of
+    625 chunks), two such hubs joined through a path, and a dense core with a
+    sparse fringe: rows far past every per-warp and per-block split."""
+    star = gg.star(20001, 0)
+    rng = gg.rng(47)
+    n = 30000
+    # hub 0 - leaves 2..14001, path 2-3-...-10, edge 10-14002 into hub 1's leaves 14002..28001,
+    # and 1998 isolated nodes
+    i = np.concatenate([np.full(14000, 0), np.full(14000, 1), np.arange(2, 10), [10]])
+    j = np.concatenate([np.arange(2, 14002), np.arange(14002, 28002), np.arange(3, 11), [14002]])
+    rp, ci = gg.csr_from_pairs(n, i, j)
+    hubs = gg.Graph(n, rp, ci, name="two-hubs")
+    core = gg.erdos_renyi(600, 0.5, rng)
+    fringe_i = rng.integers(0, 600, size=5000)
+    fringe_j = np.arange(600, 5600)
+    rp2, ci2 = gg.csr_from_pairs(5600, np.concatenate([np.repeat(np.arange(600), np.diff(core.row_ptr)), fringe_i]),
+                                 np.concatenate([core.col_idx, fringe_j]))
+    dense = gg.Graph(5600, rp2, ci2, name="core-fringe")
+    for graph in (star, hubs, dense):
+        assert_solution_matches(qc, ctx, graph, [0.6, 1.5])
+
+
 def test_no_edges(qc, ctx):
     graph = gg.Graph(100, np.zeros(101, dtype=np.int32), np.zeros(0, dtype=np.int32), name="empty")
     ref = assert_solution_matches(qc, ctx, graph, [1.0])
