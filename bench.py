@@ -68,8 +68,7 @@ SINGLE = {
                   "profile": os.path.join(ROOT, "profiles", "bfs_persistent_sbm262144.md"),
                   "cpu_sample_nodes": 512, "steps": 3},
 }
-KERNEL_SRC = [os.path.join(ROOT, "paper_2305_14641_gb300", "csrc", f)
-              for f in ("bfs.cu", "qc_device.cuh", "qc_internal.h")]
+KERNEL_SRC = [os.path.join(ROOT, "paper_2305_14641_gb300", "csrc", f) for f in ("bfs.cu", "qc_device.cuh")]
 
 
 def kernel_source_sha256() -> str:

@@ -3,6 +3,10 @@
 
 #include <cstdint>
 
+// Degree bucket (floor(log2(deg + 1))) from which a row counts as heavy: its BFS
+// item is shared by all warps of a block instead of one warp.
+#define QC_HEAVY_BUCKET 7
+
 namespace qcdev {
 
 enum : int32_t { ST_DONE = 0, ST_NEED_ROWS = 1, ST_TIMEOUT = 2 };

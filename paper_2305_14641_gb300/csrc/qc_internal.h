@@ -176,9 +176,6 @@ struct qc_graph {
 };
 
 // prep.cu
-// Degree bucket (floor(log2(deg + 1))) from which a row counts as heavy: its BFS
-// item is shared by all warps of a block instead of one warp.
-#define QC_HEAVY_BUCKET 7
 // Queues the preparation kernels without waiting; the components launch's
 // status stays on the device until qc_graph_prepare_status reads it (the BFS
 // reads it in the same wait as its own status).
