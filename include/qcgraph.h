@@ -240,11 +240,13 @@ qc_status qc_batch_create(qc_ctx *ctx, int32_t n_graphs, qc_graph *const *graphs
                           const int64_t *label_offsets, void *stream, qc_batch **out);
 qc_status qc_batch_run(qc_batch *b, int32_t *n_clusters_out, void *stream);
 void qc_batch_destroy(qc_batch *b);
-/* The configuration the plan runs: threads per CTA and source words per chunk
- * (the autotuner's choice, or QCGRAPH_BATCH_CONFIG="threads,words" from the
- * environment when that names a candidate).  Both are 0 when no graph of the
- * plan fits the graph-per-CTA kernel.  Errors: QC_ERR_INVALID_ARG. */
-qc_status qc_batch_config(const qc_batch *b, int32_t *threads, int32_t *chunk_words);
+/* The configuration the plan runs: threads per CTA, source words per chunk and
+ * the mean degree below which a thread instead of a warp takes a node (the
+ * autotuner's choice, or QCGRAPH_BATCH_CONFIG="threads,words[,degree]" from the
+ * environment when that names candidates).  All are 0 when no graph of the
+ * plan fits the graph-per-CTA kernel.  sparse_degree may be NULL.
+ * Errors: QC_ERR_INVALID_ARG. */
+qc_status qc_batch_config(const qc_batch *b, int32_t *threads, int32_t *chunk_words, int32_t *sparse_degree);
 
 /* One-shot form: create a plan, run it once, destroy it. */
 qc_status qc_solve_batch(qc_ctx *ctx, int32_t n_graphs, qc_graph *const *graphs,

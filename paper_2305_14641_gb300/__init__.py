@@ -297,10 +297,12 @@ class BatchPlan:
         return list(nc) if counts else None
 
     def config(self) -> dict:
-        """The kernel configuration the plan runs (threads per CTA, source words per chunk)."""
-        t, c = ctypes.c_int32(), ctypes.c_int32()
-        self.ctx.check(self.ctx._lib.qc_batch_config(self.handle, ctypes.byref(t), ctypes.byref(c)))
-        return {"threads": t.value, "chunk_words": c.value}
+        """The kernel configuration the plan runs (threads per CTA, source words per
+        chunk, mean degree below which a thread takes a node)."""
+        t, c, sd = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self.ctx.check(self.ctx._lib.qc_batch_config(self.handle, ctypes.byref(t), ctypes.byref(c),
+                                                     ctypes.byref(sd)))
+        return {"threads": t.value, "chunk_words": c.value, "sparse_degree": sd.value}
 
     def labels_of(self, k: int):
         o = int(self.offsets[k])

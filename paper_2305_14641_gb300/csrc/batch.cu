@@ -40,7 +40,8 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint64_t ONES = ~0ull;
 constexpr int MAXC = 8;            // most source words per chunk (held per lane in registers)
 constexpr int L_CAP = 32;          // histogram rows per graph in the batched kernel
-constexpr int SPARSE_DEGREE = 24;  // below this mean degree a thread, not a warp, takes a node
+constexpr int SPARSE_DEGREE = 24;  // default: below this mean degree a thread, not a warp, takes a node
+constexpr int SPARSE_CANDIDATES[3] = {12, 24, 48};   // the autotuner's choices for that threshold
 // Larger graphs take the single-graph path: one CTA walks all n/64 source words
 // of its graph, so its time grows as n^2 x degree while the multi-CTA path
 // spreads a large graph over the whole GPU.
@@ -63,6 +64,7 @@ struct CtaParams {
     const double *tables;          // [graph][w: L_CAP][u: L_CAP]
     int32_t n_max;
     int32_t c;                     // source words per chunk
+    int32_t sparse_degree;         // graphs of lower mean degree: a thread per node
     int32_t *hist;                 // [gridDim.x][L_CAP][n_max]
     int32_t *n_clusters;           // [n_graphs]
     int32_t *overflow;             // [n_graphs + 1]: per graph, and [n_graphs] = any
@@ -151,7 +153,7 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
     __syncthreads();
 
     // 2. BFS, chunk by chunk
-    const bool sparse = rp[n] < SPARSE_DEGREE * n;   // short rows: a thread per node
+    const bool sparse = (long long)rp[n] < (long long)P.sparse_degree * n;   // short rows: a thread per node
     int rows_ready = 2;       // hist rows zeroed / written so far
     int D = (rp[n] > 0) ? 1 : 0;
     bool overflow = false;
@@ -378,7 +380,7 @@ struct qc_batch {
     std::vector<int32_t> big;        // graphs that take the single-graph path
     int32_t n_cta = 0;               // graphs in the batched kernel
     qc_buffer descs, order, tables, hist, counts, flags, queue;
-    int threads = 256, c = 1, grid = 1;
+    int threads = 256, c = 1, grid = 1, sparse_degree = SPARSE_DEGREE;
     size_t smem = 0;
     int32_t n_max = 0;
     cudaStream_t cap_stream = nullptr;
@@ -392,7 +394,7 @@ struct qc_batch {
     }
 };
 
-static qc_status batch_enqueue(qc_batch *b, cudaStream_t s, int threads, int c) {
+static qc_status batch_enqueue(qc_batch *b, cudaStream_t s, int threads, int c, int sparse_degree) {
     qc_ctx *ctx = b->ctx;
     const size_t smem = smem_bytes(b->n_max, c);
     QC_CUDA_TRY(ctx, cudaFuncSetAttribute((const void *)batch_kernel,
@@ -412,6 +414,7 @@ static qc_status batch_enqueue(qc_batch *b, cudaStream_t s, int threads, int c) 
     P.tables = b->tables.as<double>();
     P.n_max = b->n_max;
     P.c = c;
+    P.sparse_degree = sparse_degree;
     P.hist = b->hist.as<int32_t>();
     P.n_clusters = b->counts.as<int32_t>();
     P.overflow = b->flags.as<int32_t>();
@@ -492,6 +495,7 @@ qc_status qc_cta_launch_async(qc_ctx *ctx, int32_t m, qc_graph *const *graphs, c
     P.tables = L->tables.as<double>();
     P.n_max = n_max;
     P.c = c;
+    P.sparse_degree = SPARSE_DEGREE;
     P.hist = L->hist.as<int32_t>();
     P.n_clusters = L->counts.as<int32_t>();
     P.overflow = L->flags.as<int32_t>();
@@ -609,46 +613,72 @@ qc_status qc_batch_create(qc_ctx *ctx, int32_t n_graphs, qc_graph *const *graphs
             qc_set_error(ctx, "qc_batch_create: no kernel configuration fits n = %d", b->n_max);
             return QC_ERR_INVALID_ARG;
         }
-        // QCGRAPH_BATCH_CONFIG="threads,chunk_words" fixes the choice when it is a
-        // candidate (reproducible profiling), else the autotuner decides
+        // a choice is stored as shape index + 16 x threshold index
+        const int n_sd = (int)(sizeof(SPARSE_CANDIDATES) / sizeof(SPARSE_CANDIDATES[0]));
+        // QCGRAPH_BATCH_CONFIG="threads,chunk_words[,sparse_degree]" fixes the choice when
+        // it names candidates (reproducible profiling), else the autotuner decides
         if (const char *env = getenv("QCGRAPH_BATCH_CONFIG")) {
-            int t = 0, c = 0;
-            if (sscanf(env, "%d,%d", &t, &c) == 2)
+            int t = 0, c = 0, sd = SPARSE_DEGREE;
+            const int got = sscanf(env, "%d,%d,%d", &t, &c, &sd);
+            int sdi = -1;
+            for (int j = 0; j < n_sd; ++j)
+                if (SPARSE_CANDIDATES[j] == sd) sdi = j;
+            if (got >= 2 && sdi >= 0)
                 for (size_t i = 0; i < cands.size(); ++i)
-                    if (cands[i].first == t && cands[i].second == c) choice = (int)i;
+                    if (cands[i].first == t && cands[i].second == c) choice = (int)i + 16 * sdi;
         }
-        if (choice < 0 || choice >= (int)cands.size()) {
+        if (choice < 0 || choice % 16 >= (int)cands.size() || choice / 16 >= n_sd) {
+            // first the tile shape at the default threshold, then the threshold for that shape
             qc_event_pair ev;
             QC_TRY(ev.create(ctx));
-            float best = 1e30f;
-            choice = 0;
-            for (size_t i = 0; i < cands.size(); ++i) {
-                float ms = 0.f;
+            auto time_one = [&](int t, int c, int sd, float *ms) -> qc_status {
+                *ms = 1e30f;
                 for (int rep = 0; rep < 2; ++rep) {       // first run warms up
                     QC_CUDA_TRY(ctx, cudaEventRecord(ev.a, stream));
-                    qc_status st = batch_enqueue(b, stream, cands[i].first, cands[i].second);
-                    if (st != QC_OK) {
-                        ms = 1e30f;
-                        break;
+                    if (batch_enqueue(b, stream, t, c, sd) != QC_OK) {
+                        *ms = 1e30f;
+                        return QC_OK;
                     }
                     QC_CUDA_TRY(ctx, cudaEventRecord(ev.b, stream));
                     QC_CUDA_TRY(ctx, cudaEventSynchronize(ev.b));
-                    QC_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ev.a, ev.b));
+                    QC_CUDA_TRY(ctx, cudaEventElapsedTime(ms, ev.a, ev.b));
                 }
+                return QC_OK;
+            };
+            int default_sdi = 0;
+            for (int j = 0; j < n_sd; ++j)
+                if (SPARSE_CANDIDATES[j] == SPARSE_DEGREE) default_sdi = j;
+            float best = 1e30f;
+            int shape = 0;
+            for (size_t i = 0; i < cands.size(); ++i) {
+                float ms = 0.f;
+                QC_TRY(time_one(cands[i].first, cands[i].second, SPARSE_DEGREE, &ms));
                 if (ms < best) {
                     best = ms;
-                    choice = (int)i;
+                    shape = (int)i;
                 }
             }
+            int sdi = default_sdi;
+            for (int j = 0; j < n_sd; ++j) {
+                if (j == default_sdi) continue;
+                float ms = 0.f;
+                QC_TRY(time_one(cands[shape].first, cands[shape].second, SPARSE_CANDIDATES[j], &ms));
+                if (ms < best) {
+                    best = ms;
+                    sdi = j;
+                }
+            }
+            choice = shape + 16 * sdi;
             std::lock_guard<std::mutex> lk(ctx->tune_mu);
             ctx->tune[key] = choice;
         }
-        b->threads = cands[choice].first;
-        b->c = cands[choice].second;
+        b->threads = cands[choice % 16].first;
+        b->c = cands[choice % 16].second;
+        b->sparse_degree = SPARSE_CANDIDATES[choice / 16];
         // capture the batched solve
         QC_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
         QC_CUDA_TRY(ctx, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-        qc_status st = batch_enqueue(b, b->cap_stream, b->threads, b->c);
+        qc_status st = batch_enqueue(b, b->cap_stream, b->threads, b->c, b->sparse_degree);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
         if (st != QC_OK) return st;
@@ -704,10 +734,11 @@ qc_status qc_batch_run(qc_batch *b, int32_t *n_clusters_out, void *stream_) {
 
 void qc_batch_destroy(qc_batch *b) { delete b; }
 
-qc_status qc_batch_config(const qc_batch *b, int32_t *threads, int32_t *chunk_words) {
+qc_status qc_batch_config(const qc_batch *b, int32_t *threads, int32_t *chunk_words, int32_t *sparse_degree) {
     if (!b || !threads || !chunk_words) return QC_ERR_INVALID_ARG;
     *threads = b->n_cta > 0 ? b->threads : 0;
     *chunk_words = b->n_cta > 0 ? b->c : 0;
+    if (sparse_degree) *sparse_degree = b->n_cta > 0 ? b->sparse_degree : 0;
     return QC_OK;
 }
 

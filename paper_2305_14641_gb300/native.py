@@ -94,7 +94,7 @@ SIGNATURES = [
                                        ctypes.c_void_p, c_int64_p, ctypes.c_void_p, c_void_pp]),
     ("qc_batch_run", ctypes.c_int, [ctypes.c_void_p, c_int32_p, ctypes.c_void_p]),
     ("qc_batch_destroy", None, [ctypes.c_void_p]),
-    ("qc_batch_config", ctypes.c_int, [ctypes.c_void_p, c_int32_p, c_int32_p]),
+    ("qc_batch_config", ctypes.c_int, [ctypes.c_void_p, c_int32_p, c_int32_p, c_int32_p]),
     ("qc_solve_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, c_void_pp, c_double_p,
                                       ctypes.c_void_p, c_int64_p, ctypes.c_void_p]),
     ("qc_server_create", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qc_server_config), c_void_pp]),

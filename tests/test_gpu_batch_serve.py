@@ -58,14 +58,14 @@ def test_batch_planted(qc, ctx):
     check_batch(qc, ctx, graphs, sigmas)
 
 
-@pytest.mark.parametrize("threads,words", [(256, 1), (512, 4)])
-def test_batch_fixed_config(qc, ctx, monkeypatch, threads, words):
+@pytest.mark.parametrize("threads,words,degree", [(256, 1, 24), (512, 4, 48), (512, 2, 12)])
+def test_batch_fixed_config(qc, ctx, monkeypatch, threads, words, degree):
     # every kernel configuration the autotuner may pick gives the oracle's labels
-    monkeypatch.setenv("QCGRAPH_BATCH_CONFIG", f"{threads},{words}")
+    monkeypatch.setenv("QCGRAPH_BATCH_CONFIG", f"{threads},{words},{degree}")
     graphs, sigmas = gg.planted_batch(48)
     Gs = [qc.Graph.from_graph(ctx, g) for g in graphs]
     plan = qc.BatchPlan(ctx, Gs, sigmas)
-    assert plan.config() == {"threads": threads, "chunk_words": words}
+    assert plan.config() == {"threads": threads, "chunk_words": words, "sparse_degree": degree}
     counts = plan.run()
     for k, (g, s) in enumerate(zip(graphs, sigmas)):
         ref = oracle.solve(g, [s])
