@@ -9,8 +9,9 @@
 //   2. the all-source bitset BFS, a chunk of c source words at a time, with the
 //      chunk's bitset columns of every node held in shared memory (two buffers of
 //      n x c words): one warp per node ORs its neighbours' words, lanes over the
-//      neighbour list; per-node counts of new sources go to a per-CTA histogram in
-//      global memory, level by level;
+//      neighbour list (a thread per node for graphs of low mean degree); per-node
+//      counts of new sources go to a per-CTA histogram in global memory, level by
+//      level;
 //   3. the potential of Eq. 7 / Algorithm 1 from the histogram with host-computed
 //      binary64 weights for the graph's sigma (same expressions and ascending-
 //      distance order as the single-graph path);
@@ -20,9 +21,10 @@
 // single-graph path on the host side.  Graphs too large for a CTA's shared
 // memory take the single-graph path too.
 //
-// The plan picks the CTA size and the chunk width c with a small autotuner that
-// times the candidates on the batch itself and caches the winner per
-// (largest n, mean degree) bucket in the context.
+// The plan picks the CTA size, the chunk width c and the thread-per-node degree
+// threshold with a small autotuner that times the candidates on the batch
+// itself and caches the winner per (largest n, mean degree) bucket in the
+// context.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
