@@ -15,10 +15,11 @@
 // its own row dist[v][.], i.e. over the lengths *from* v, as in the hop path.
 // A warp owns a node v.  It first checks whether any neighbour changed any
 // distance in the previous pass or so far in this one (chgv[u] = pass of u's
-// last change) and skips v if none did; otherwise, group by group (32 sources
-// each), it reads only the neighbours whose group changed since the previous
-// pass (chg[u][g]), so quiet parts of the graph cost one int per neighbour and
-// pass.  Testing ">= previous pass" rather than "== previous pass" matters: a
+// last change) and skips v if none did; otherwise, GU groups of 32 sources at a
+// time, it reads only the neighbours whose group changed since the previous
+// pass (chg[u][g]), NB such neighbours at a time, so a lane keeps up to GU x NB
+// distances in flight and quiet parts of the graph cost one int per neighbour
+// and pass.  Testing ">= previous pass" rather than "== previous pass" matters: a
 // neighbour that changes again in this pass must not hide its earlier change.  Updates are
 // in place: a value only ever falls to another path's length, every change is
 // seen by the neighbours in the next pass, and a pass without change ends the
@@ -46,6 +47,8 @@
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int GU = 4;              // source groups a warp relaxes together
+constexpr int NB = 4;              // changed neighbours a warp reads together
 
 struct SsspParams {
     int32_t n;
@@ -96,56 +99,75 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
                 stirred = *(volatile int32_t *)(p.chgv + p.col_idx[e]) >= pass - 1;
             if (!__any_sync(FULL, stirred)) continue;
             bool v_fell = false;
-            for (int g = 0; g < p.KG; ++g) {
-            const int k = g * 32 + lane;
-            double *dv = p.dist + (size_t)v * p.K + k;
-            const double mine = *(volatile double *)dv;
-            double best = mine;
-            for (int e0 = beg; e0 < end; e0 += 32) {
-                const int e = e0 + lane;
-                int u = 0;
-                double wt = 0.0;
-                bool fresh = false;
-                if (e < end) {
-                    u = p.col_idx[e];
-                    wt = p.w[e];
-                    fresh = *(volatile int32_t *)(p.chg + (size_t)u * p.KG + g) >= pass - 1;
-                }
-                unsigned mask = __ballot_sync(FULL, fresh);
-                while (mask) {
-                    // up to four changed neighbours in flight
-                    int ub[4];
-                    double wb[4], db[4];
-                    int cnt = 0;
+            // GU source groups at a time, and up to NB changed neighbours at a time,
+            // so that a lane has up to GU x NB distances in flight
+            for (int g0 = 0; g0 < p.KG; g0 += GU) {
+                double mine[GU], best[GU];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (mask) {
-                            const int b = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            ub[q] = __shfl_sync(FULL, u, b);
-                            wb[q] = __shfl_sync(FULL, wt, b);
-                            cnt = q + 1;
-                        } else {
-                            ub[q] = v;
-                            wb[q] = 0.0;
+                for (int q = 0; q < GU; ++q) {
+                    mine[q] = (g0 + q < p.KG) ? *(volatile const double *)(p.dist + (size_t)v * p.K + (g0 + q) * 32 + lane)
+                                              : INF;
+                    best[q] = mine[q];
+                }
+                for (int e0 = beg; e0 < end; e0 += 32) {
+                    const int e = e0 + lane;
+                    int u = 0;
+                    double wt = 0.0;
+                    if (e < end) {
+                        u = p.col_idx[e];
+                        wt = p.w[e];
+                    }
+                    unsigned fm[GU];
+                    unsigned any_fresh = 0u;
+#pragma unroll
+                    for (int q = 0; q < GU; ++q) {
+                        const bool fresh = e < end && g0 + q < p.KG &&
+                                           *(volatile const int32_t *)(p.chg + (size_t)u * p.KG + g0 + q) >= pass - 1;
+                        fm[q] = __ballot_sync(FULL, fresh);
+                        any_fresh |= fm[q];
+                    }
+                    while (any_fresh) {
+                        int ub[NB], bb[NB];
+                        double wb[NB];
+#pragma unroll
+                        for (int i = 0; i < NB; ++i) {
+                            bb[i] = -1;
+                            if (any_fresh) {
+                                bb[i] = __ffs(any_fresh) - 1;
+                                any_fresh &= any_fresh - 1;
+                            }
+                            const int src = bb[i] < 0 ? 0 : bb[i];
+                            ub[i] = __shfl_sync(FULL, u, src);
+                            wb[i] = __shfl_sync(FULL, wt, src);
                         }
-                    }
+                        double db[NB][GU];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        db[q] = (q < cnt) ? *(volatile const double *)(p.dist + (size_t)ub[q] * p.K + k) : INF;
+                        for (int i = 0; i < NB; ++i)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const double c = __dadd_rn(db[q], wb[q]);
-                        if (c < best) best = c;
+                            for (int q = 0; q < GU; ++q)
+                                db[i][q] = (bb[i] >= 0 && ((fm[q] >> bb[i]) & 1u))
+                                               ? *(volatile const double *)(p.dist + (size_t)ub[i] * p.K +
+                                                                            (g0 + q) * 32 + lane)
+                                               : INF;
+#pragma unroll
+                        for (int i = 0; i < NB; ++i)
+#pragma unroll
+                            for (int q = 0; q < GU; ++q) {
+                                const double c = __dadd_rn(db[i][q], wb[i]);
+                                if (c < best[q]) best[q] = c;
+                            }
                     }
                 }
-            }
-            const bool fell = best < mine;
-            if (fell) *(volatile double *)dv = best;
-            if (__any_sync(FULL, fell)) {
-                v_fell = true;
-                if (lane == 0) *(volatile int32_t *)(p.chg + (size_t)v * p.KG + g) = pass;
-            }
+#pragma unroll
+                for (int q = 0; q < GU; ++q) {
+                    if (g0 + q >= p.KG) break;
+                    const bool fell = best[q] < mine[q];
+                    if (fell) *(volatile double *)(p.dist + (size_t)v * p.K + (g0 + q) * 32 + lane) = best[q];
+                    if (__any_sync(FULL, fell)) {
+                        v_fell = true;
+                        if (lane == 0) *(volatile int32_t *)(p.chg + (size_t)v * p.KG + g0 + q) = pass;
+                    }
+                }
             }
             if (v_fell) {
                 any = true;
