@@ -31,8 +31,8 @@
 //
 // Potential: for node v, sum1 = sum_j d^2 e^{-d^2 / 2 sigma^2} and
 // sum2 = sum_j e^{...} over the j that v reaches (the self term adds 1 to
-// sum2), d = dist[v][j - s0] of each batch, with CUDA's binary64 exp of
-// d^2 x (-1 / 2 sigma^2) and separately rounded multiplies and adds.  The sums run over each batch's
+// sum2), d = dist[v][j - s0] of each batch, with a table-driven binary64
+// exp (below) of d^2 x 1 / (2 sigma^2) and separately rounded multiplies and adds.  The sums run over each batch's
 // sources in a fixed pattern and over the batches in order, so the result is
 // the same on every run; it differs from the oracle's sequential sum over j
 // only by rounding (relative 1e-15 or so).
@@ -55,6 +55,7 @@ struct SsspParams {
     const int32_t *row_ptr;
     const int32_t *col_idx;
     const double *w;
+    const int32_t *order;          // nodes, heaviest degree bucket first
     double *dist;                  // [n][K]
     int32_t *chg;                  // [n][KG] pass of the last change of each group
     int32_t *chgv;                 // [n] pass of the last change of any group
@@ -83,7 +84,10 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
     }
     for (int v = tid; v < p.n; v += nthreads) p.chgv[v] = (v >= p.s0 && v < p.s0 + p.ns) ? 0 : -1;
     if (!qcdev::grid_barrier(p.bar, p.status)) return;
-    const int items = p.n;
+    // an item is (node, block of GU source groups), heaviest nodes first, so that
+    // no pass ends waiting on one warp that took a hub late
+    const int NGB = (p.KG + GU - 1) / GU;
+    const int items = p.n * NGB;
     int pass = 1;
     for (; pass <= p.max_pass; ++pass) {
         bool any = false;
@@ -92,7 +96,9 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
             if (lane == 0) it = atomicAdd(p.pass_ctr + pass, 1);
             it = __shfl_sync(FULL, it, 0);
             if (it >= items) break;
-            const int v = it;
+            const int oi = it / NGB;
+            const int v = p.order[oi];
+            const int gb = it - oi * NGB;
             const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
             bool stirred = false;
             for (int e = beg + lane; e < end && !stirred; e += 32)
@@ -101,7 +107,8 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
             bool v_fell = false;
             // GU source groups at a time, and up to NB changed neighbours at a time,
             // so that a lane has up to GU x NB distances in flight
-            for (int g0 = 0; g0 < p.KG; g0 += GU) {
+            {
+                const int g0 = gb * GU;
                 double mine[GU], best[GU];
 #pragma unroll
                 for (int q = 0; q < GU; ++q) {
@@ -184,38 +191,80 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
     }
 }
 
+// exp(-t) for t >= 0 by the table-driven method of Tang (ACM TOMS 15(2), 1989):
+// t = a + b/64 + r with integers a, b (0 <= b < 64) and 0 <= r < 1/64, so
+// exp(-t) = exp(-a) exp(-b/64) exp(-r), the first two from tables built on the
+// host with the C library's exp and the last from its Taylor series to degree 6
+// (truncation below 1e-16 relative).  About 4 ulp in all, far inside the 1e-12
+// the potential is held to, for a third of the binary64 work of a general exp.
+// Below exp(-745) (the smallest subnormal) it returns 0.
+struct ExpTables {
+    double hi[746];                // exp(-a), a = 0 .. 745
+    double lo[64];                 // exp(-b / 64), b = 0 .. 63
+};
+
+__device__ __forceinline__ double exp_neg(double t, const ExpTables &T) {
+    if (!(t < 745.0)) return 0.0;
+    const int k = (int)(t * 64.0);                        // t * 64 is exact; truncation = floor here
+    const double r = t - (double)k * (1.0 / 64.0);        // exact (Sterbenz) or r = t when k = 0
+    const double y = -r;
+    double p = 1.0 / 720.0;
+    p = fma(p, y, 1.0 / 120.0);
+    p = fma(p, y, 1.0 / 24.0);
+    p = fma(p, y, 1.0 / 6.0);
+    p = fma(p, y, 0.5);
+    p = fma(p, y, 1.0);
+    p = fma(p, y, 1.0);
+    return T.hi[k >> 6] * T.lo[k & 63] * p;
+}
+
 // acc[s][v] += (sum1, sum2) over the batch's sources for node v: a warp per node,
-// lane l takes sources l, l + 32, ... in order, then a butterfly over the lanes
-// (every lane ends with the same total) and one add into the running sums, so
-// the result is the same on every run.
+// lane l takes sources l, l + 32, ... in order (each distance read once for up
+// to SGRP sigma values), then a butterfly over the lanes (every lane ends with
+// the same total) and one add into the running sums, so the result is the same
+// on every run.
+constexpr int SGRP = 8;
 __global__ void wpot_accumulate(int32_t n, int32_t K, int32_t ns, const double *dist, int32_t S,
-                                const double *den, double2 *acc) {
+                                const double *den, double2 *acc, const __grid_constant__ ExpTables T) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int v = warp; v < n; v += nwarps) {
         const double *row = dist + (size_t)v * K;
-        for (int s = 0; s < S; ++s) {
-            const double nr = -1.0 / den[s];       // one division per node and sigma, not per pair
-            double s1 = 0.0, s2 = 0.0;
+        for (int s0 = 0; s0 < S; s0 += SGRP) {
+            double inv[SGRP], s1[SGRP], s2[SGRP];
+#pragma unroll
+            for (int j = 0; j < SGRP; ++j) {
+                inv[j] = (s0 + j < S) ? 1.0 / den[s0 + j] : 0.0;   // one division per node and sigma
+                s1[j] = 0.0;
+                s2[j] = 0.0;
+            }
             for (int k = lane; k < ns; k += 32) {
                 const double d = row[k];
                 if (!(d < 1e308)) continue;                        // unreachable (+inf)
                 const double d2 = __dmul_rn(d, d);
-                const double e = exp(__dmul_rn(d2, nr));
-                s1 = __dadd_rn(s1, __dmul_rn(d2, e));
-                s2 = __dadd_rn(s2, e);
+#pragma unroll
+                for (int j = 0; j < SGRP; ++j) {
+                    if (s0 + j < S) {
+                        const double e = exp_neg(__dmul_rn(d2, inv[j]), T);
+                        s1[j] = __dadd_rn(s1[j], __dmul_rn(d2, e));
+                        s2[j] = __dadd_rn(s2[j], e);
+                    }
+                }
             }
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                s1 = __dadd_rn(s1, __shfl_xor_sync(FULL, s1, off));
-                s2 = __dadd_rn(s2, __shfl_xor_sync(FULL, s2, off));
-            }
-            if (lane == 0) {
-                double2 a = acc[(size_t)s * n + v];
-                a.x = __dadd_rn(a.x, s1);
-                a.y = __dadd_rn(a.y, s2);
-                acc[(size_t)s * n + v] = a;
+            for (int j = 0; j < SGRP; ++j) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    s1[j] = __dadd_rn(s1[j], __shfl_xor_sync(FULL, s1[j], off));
+                    s2[j] = __dadd_rn(s2[j], __shfl_xor_sync(FULL, s2[j], off));
+                }
+                if (lane == 0 && s0 + j < S) {
+                    double2 a = acc[(size_t)(s0 + j) * n + v];
+                    a.x = __dadd_rn(a.x, s1[j]);
+                    a.y = __dadd_rn(a.y, s2[j]);
+                    acc[(size_t)(s0 + j) * n + v] = a;
+                }
             }
         }
     }
@@ -334,9 +383,13 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
     const int32_t n = g->n;
     const int32_t K = sources_per_batch(ctx, n);
     const int32_t KG = K / 32;
+    QC_TRY(qc_graph_prepare(g, stream));     // the degree order of the nodes
     const int32_t max_pass = n + 1;     // a lightest path has at most n - 1 arcs
     std::vector<double> den(n_sigma);
     for (int32_t s = 0; s < n_sigma; ++s) den[s] = 2.0 * (sigmas[s] * sigmas[s]);
+    ExpTables etab;
+    for (int a = 0; a < 746; ++a) etab.hi[a] = std::exp(-(double)a);
+    for (int b = 0; b < 64; ++b) etab.lo[b] = std::exp(-(double)b / 64.0);
     qc_buffer dist, chg, chgv, ctl, acc, dden;
     QC_TRY(dist.allocate(ctx, sizeof(double) * (size_t)n * K, stream));
     QC_TRY(chg.allocate(ctx, sizeof(int32_t) * (size_t)n * KG, stream));
@@ -354,7 +407,7 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
         return QC_ERR_CUDA;
     }
     int blocks = per_sm * qc_coop_sms(ctx);
-    const int want = qc_ceil_div(n, 8);
+    const int want = qc_ceil_div((int64_t)n * ((KG + GU - 1) / GU), 8);
     if (blocks > want) blocks = want;
     if (blocks < 1) blocks = 1;
     qc_pinned pin(ctx);
@@ -367,6 +420,7 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
         p.row_ptr = g->row_ptr.as<int32_t>();
         p.col_idx = g->col_idx.as<int32_t>();
         p.w = g->weights.as<double>();
+        p.order = g->order.as<int32_t>();
         p.dist = dist.as<double>();
         p.chg = chg.as<int32_t>();
         p.chgv = chgv.as<int32_t>();
@@ -395,7 +449,7 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
             return QC_ERR_CUDA;
         }
         wpot_accumulate<<<pblocks, 256, 0, stream>>>(n, K, p.ns, dist.as<double>(), n_sigma, dden.as<double>(),
-                                                     acc.as<double2>());
+                                                     acc.as<double2>(), etab);
         QC_LAUNCHED(ctx);
     }
     const int fb = std::max(1, std::min(qc_ceil_div((int64_t)n_sigma * n, 256), 2 * ctx->num_sms));
