@@ -263,7 +263,9 @@ typedef struct {
     int32_t large_workers;     /* threads running the single-graph path (0 = 4) */
     float large_sm_share;      /* share of the SMs the single-graph path's persistent
                                   kernels may fill, leaving the rest to batched launches
-                                  (0 = 0.4); applies to the whole context */
+                                  (0 = 0.4); applies to the whole context until
+                                  qc_server_destroy restores its previous share, so
+                                  give a server a context of its own */
 } qc_server_config;
 
 typedef struct {

@@ -113,6 +113,7 @@ struct qc_server {
     std::thread sched;
     std::vector<std::thread> large;
     std::vector<cudaStream_t> large_streams;
+    float saved_share = 1.0f;          // the context's SM share before the server set its own
 
     size_t estimate(int32_t n, int64_t nnz, bool is_large) const {
         const size_t csr = 4 * ((size_t)n + 1) + 4 * (size_t)nnz;
@@ -385,6 +386,7 @@ qc_status qc_server_create(qc_ctx *ctx, const qc_server_config *cfg, qc_server *
     const int nl = (cfg && cfg->large_workers > 0) ? cfg->large_workers : 4;
     const float share = (cfg && cfg->large_sm_share > 0.f && cfg->large_sm_share <= 1.f) ? cfg->large_sm_share
                                                                                           : 0.4f;
+    s->saved_share = ctx->coop_sm_share.load();
     ctx->coop_sm_share = share;
     QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     // batched launches of small requests first: highest stream priority
@@ -520,6 +522,7 @@ void qc_server_destroy(qc_server *s) {
         if (r->g) qc_graph_destroy(r->g);
         r->labels_dev.release();
     }
+    s->ctx->coop_sm_share = s->saved_share;
     delete s;
 }
 
