@@ -401,8 +401,9 @@ def bench_ours(args, graph, sigmas, spec):
                          "launches": kstats["launches"],
                          "bytes_model": f"pull-all: per level and chunk of source words, 8*wn*(E+3N) "
                                         f"bitset bytes + CSR + one histogram row (W = {(n + 63) // 64} "
-                                        f"words in chunks sized to half of L2); saturated rows are "
-                                        f"skipped and each chunk's bitsets stay in L2, so the DRAM "
+                                        f"words in chunks of at most 256, the two bitset buffers near "
+                                        f"four times L2); saturated rows are skipped and a row gathered "
+                                        f"for several neighbours is mostly read from L2, so the DRAM "
                                         f"traffic is far below the model",
                          "avg_launch_ms": (kstats["total_ms"] / kstats["launches"]
                                            if kstats["launches"] else None)},

@@ -454,26 +454,6 @@ double qc_bfs_level_model_bytes(int64_t n, int64_t nnz, int64_t wn) {
            4.0 * (double)n;
 }
 
-// Words of sources per chunk: as many as keep both bitset buffers within about
-// half of L2 (they are re-read once per neighbour per level), at most 512.
-// QCGRAPH_CHUNK_WORDS overrides the choice (tests use it to force many chunks).
-int32_t qc_bfs_chunk_words(const qc_ctx *ctx, int32_t n) {
-    const int64_t W = (n + 63) / 64;
-    int64_t wc;
-    if (const char *env = getenv("QCGRAPH_CHUNK_WORDS")) {
-        wc = atoll(env);
-        if (wc < 1) wc = 1;
-    } else {
-        const size_t target = ctx->l2_bytes ? ctx->l2_bytes / 2 : (size_t)48 << 20;
-        wc = (int64_t)(target / (2 * 8 * (size_t)n));
-        if (wc > 2) wc &= ~int64_t(1);
-        if (wc < 2) wc = 2;
-    }
-    if (wc > 512) wc = 512;
-    if (wc > W) wc = W;
-    return (int32_t)wc;
-}
-
 qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
     qc_range range("qc.bfs");
     qc_ctx *ctx = g->ctx;

@@ -1,6 +1,8 @@
 // Context, memory accounting, error reporting, graph upload.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 
 #include "qc_internal.h"
@@ -87,6 +89,35 @@ void qc_record_kernel(qc_ctx *ctx, const char *kernel, double ms, double model_b
     st.launches += 1;
     st.total_ms += ms;
     st.model_bytes += model_bytes;
+}
+
+// Words of sources per BFS chunk.  Every level of a chunk ends at a grid barrier
+// after a tail of the last rows, a cost that does not grow with the chunk's
+// width, while a row's gather reads R contiguous 16-byte segments per
+// neighbour, so wide chunks stay efficient after their bitsets leave L2.
+// Measured on GB300 (SBM graphs of mean degree 20, n = 2^15 .. 2^19), the
+// fastest width keeps the two bitset buffers near four times L2, between 64
+// and 256 words; below that the per-level fixed cost dominates (sizing the
+// buffers to half of L2 ran 2-3x slower at n >= 2^18).  The width is a
+// multiple of 64 words (whole 32-segment tiles) chosen so that the chunks
+// split the W words evenly.  QCGRAPH_CHUNK_WORDS overrides the choice (tests
+// use it to force many chunks).
+int32_t qc_bfs_chunk_words(const qc_ctx *ctx, int32_t n) {
+    const int64_t W = ((int64_t)n + 63) / 64;
+    int64_t wc;
+    if (const char *env = getenv("QCGRAPH_CHUNK_WORDS")) {
+        wc = atoll(env);
+        if (wc < 1) wc = 1;
+    } else {
+        const size_t l2 = ctx->l2_bytes ? ctx->l2_bytes : (size_t)96 << 20;
+        int64_t target = (int64_t)(4 * l2 / (2 * 8 * (size_t)(n > 0 ? n : 1)));
+        target = std::min<int64_t>(std::max<int64_t>(target, 64), 256);
+        const int64_t chunks = (W + target - 1) / target;
+        wc = ((W + chunks - 1) / chunks + 63) / 64 * 64;
+    }
+    if (wc > 512) wc = 512;
+    if (wc > W) wc = W;
+    return (int32_t)(wc > 0 ? wc : 1);
 }
 
 extern "C" {

@@ -185,8 +185,9 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream);
 qc_status qc_graph_prepare_status(qc_graph *g, int32_t host_status);
 // hist[0][v] = 1, hist[1][v] = deg(v)
 qc_status qc_fill_first_rows(qc_graph *g, cudaStream_t stream);
-// bfs.cu helpers shared with the batched paths
+// bfs.cu helper shared with the batched paths
 double qc_bfs_level_model_bytes(int64_t n, int64_t nnz, int64_t wn);
+// context.cu: words of sources per BFS chunk (also sizes the server's memory estimate)
 int32_t qc_bfs_chunk_words(const qc_ctx *ctx, int32_t n);
 
 // ---- entry points implemented per translation unit ---------------------------------
