@@ -39,6 +39,15 @@
 // with one coalesced load and broadcast by shuffle; each lane keeps min(4, G)
 // loads in flight and stops once its segment has found every missing source.
 //
+// Change masks (sparse graphs with rows of more than 16 segments): while the
+// frontier is sparse, a level also records for each (node, tile) which
+// segments gained bits, and the next level reads only those segments of its
+// neighbours, skipping neighbours whose tile gained nothing.  This is exact:
+// vis_{l-2}[u] is within vis_{l-1}[v] for every neighbour u of v (the
+// recurrence above), so a segment of u that did not change at level l-1
+// cannot add anything to v at level l.  The first level whose predecessor
+// found many bits reads (and writes) no masks, and neither do the levels after it.
+//
 // One persistent cooperative launch runs the set-up and every level of a
 // chunk, separated by a grid barrier whose spin is bounded (on expiry the kernel
 // records a timeout and returns).  If the histogram runs out of rows the kernel
@@ -76,6 +85,10 @@ struct BfsParams {
     const int32_t *wmajor;      // component holding most of a word's sources
     const unsigned long long *wmask;   // bits of those sources
     ulonglong2 *buf[2];         // vis_l in buf[l & 1], [n][R]
+    uint32_t *fmask[2];         // [n * T] node-major: bit q of (v, t) set if segment 32t + q of
+                                // v's row gained bits at level l (fmask[l & 1]); null below 17 segments
+    int32_t mask_ratio;         // read only masked segments at level l when level l-1 found fewer than
+                                // (64 wn n) / mask_ratio new bits; 0: never
     int32_t R;                  // 16-byte segments per row in this chunk
     int32_t T;                  // tiles per row
     int32_t w0, wn, W;          // chunk = words [w0, w0 + wn) of W
@@ -86,6 +99,7 @@ struct BfsParams {
     int32_t first_chunk;        // write hist rows 0 and 1
     int32_t start_level;        // 2: fresh chunk, run the level-1 set-up first
     int32_t *level_new;         // [rows]
+    unsigned long long *level_bits;   // [rows] new bits found at each level (level 1: set-up bits)
     int32_t *light_ctr;         // [rows] light list positions taken so far at each level
     int32_t *heavy_ctr;         // [rows] block items taken so far at each level
     int32_t *wl[2];             // worklists of light items: level l reads wl[l & 1]
@@ -148,6 +162,8 @@ __device__ void init_fill(const BfsParams &p) {
         out[s] = make_ulonglong2(w[0], w[1]);
     }
     for (int i = tid; i < p.n * p.T; i += nthreads) p.sat[i] = NOT_SAT;
+    if (p.fmask[1])
+        for (int i = tid; i < p.n * p.T; i += nthreads) p.fmask[1][i] = 0u;
     if (p.first_chunk)
         for (int v = tid; v < p.n; v += nthreads) {
             p.hist[v] = 1;
@@ -161,27 +177,48 @@ __device__ void init_bits(const BfsParams &p) {
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     unsigned long long *words = reinterpret_cast<unsigned long long *>(p.buf[1]);
     const int stride = 2 * p.R;
+    uint32_t *fm = p.fmask[1];
+    int set = 0;
     for (int v = warp; v < p.n; v += nwarps) {
         unsigned long long *row = words + (size_t)v * stride;
         const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
         for (int e = beg + lane; e <= end; e += 32) {
             const int u = (e == end) ? v : p.col_idx[e];
             const int k = (u >> 6) - p.w0;
-            if (k >= 0 && k < p.wn) atomicOr(row + k, 1ull << (u & 63));
+            if (k >= 0 && k < p.wn) {
+                atomicOr(row + k, 1ull << (u & 63));
+                // segment k / 2 = tile k / 64, bit (k / 2) % 32
+                if (fm) atomicOr(fm + (size_t)v * p.T + (k >> 6), 1u << ((k >> 1) & 31));
+                ++set;
+            }
         }
     }
+    set = __reduce_add_sync(FULL, set);
+    if (lane == 0 && set) atomicAdd(p.level_bits + 1, (unsigned long long)set);
 }
 
 // ---- levels >= 2: pull ------------------------------------------------------------
+
+// New bits found by the block at the current level.
+__shared__ unsigned int block_found;
+// Per warp: ids and change masks of the neighbours a G = 32 gather reads.
+__shared__ int2 pack[WARPS][32];
 
 // OR of the rows of neighbours [j_first, end) of one node, taking 32-neighbour
 // chunks j_first, j_first + stride, ... (stride = 32 x the warps sharing the row).
 // Lane (slot, q) accumulates segment q; it stops once acc | own is all ones.
 // When `have0` is set, myu0 already holds the first chunk's ids (prefetched).
-template <int G>
-__device__ __forceinline__ ulonglong2 gather_or(const BfsParams &p, const ulonglong2 *vin, int j_first,
-                                                int end, int stride, int q, bool qok, ulonglong2 own,
+// At a masked level (MASKS, G = 32: lane = segment of tile t) only the
+// neighbours whose tile changed at the previous level are read, packed (id and
+// change mask) into the warp's slots in shared memory, each only in the
+// segments whose bit is set: a segment of u that gained nothing at level l-1
+// equals u's segment at level l-2, which the recurrence already put into v's
+// row at level l-1.
+template <int G, bool MASKS>
+__device__ __forceinline__ ulonglong2 gather_or(const BfsParams &p, const int level, int j_first, int end,
+                                                int stride, int q, bool qok, ulonglong2 own, bool masked, int t,
                                                 bool have0 = false, int myu0 = 0) {
+    const ulonglong2 *vin = p.buf[(level - 1) & 1];
     constexpr int SLOTS = 32 / G;
     constexpr int U = G < 4 ? G : 4;
     const int lane = threadIdx.x & 31;
@@ -193,31 +230,59 @@ __device__ __forceinline__ ulonglong2 gather_or(const BfsParams &p, const ulongl
         if (!__any_sync(FULL, act)) break;
         const int cnt = min(32, end - j0);
         const int myu = (have0 && j0 == j_first) ? myu0 : ((lane < cnt) ? p.col_idx[j0 + lane] : 0);
-        for (int m = 0; m < cnt; m += SLOTS * U) {
-            ulonglong2 x[U];
+        if (G == 32 && MASKS && masked) {
+            const uint32_t fm = (lane < cnt) ? p.fmask[(level - 1) & 1][(size_t)myu * p.T + t] : 0u;
+            const unsigned nz = __ballot_sync(FULL, fm != 0u);
+            const int live = __popc(nz);
+            int2 *slots = pack[threadIdx.x >> 5];
+            if (fm) slots[__popc(nz & ((1u << lane) - 1u))] = make_int2(myu, (int)fm);
+            __syncwarp();
+            for (int m = 0; m < live; m += U) {
+                ulonglong2 x[U];
 #pragma unroll
-            for (int k = 0; k < U; ++k) {
-                const int tt = m + k * SLOTS + slot;
-                const int u = __shfl_sync(FULL, myu, tt & 31);
-                x[k] = (act && qok && tt < cnt) ? vin[(size_t)u * p.R + q] : zero;
-            }
+                for (int k = 0; k < U; ++k) {
+                    const int2 e = (m + k < live) ? slots[m + k] : make_int2(0, 0);
+                    x[k] = (act && qok && ((e.y >> lane) & 1)) ? vin[(size_t)e.x * p.R + q] : zero;
+                }
 #pragma unroll
-            for (int k = 0; k < U; ++k) {
-                acc.x |= x[k].x;
-                acc.y |= x[k].y;
+                for (int k = 0; k < U; ++k) {
+                    acc.x |= x[k].x;
+                    acc.y |= x[k].y;
+                }
+                act = act && !seg_full(make_ulonglong2(acc.x | own.x, acc.y | own.y));
+                if (!__any_sync(FULL, act)) break;
             }
-            act = act && !seg_full(make_ulonglong2(acc.x | own.x, acc.y | own.y));
-            if (!__any_sync(FULL, act)) break;
+            __syncwarp();
+        } else {
+            for (int m = 0; m < cnt; m += SLOTS * U) {
+                ulonglong2 x[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    const int tt = m + k * SLOTS + slot;
+                    const int u = __shfl_sync(FULL, myu, tt & 31);
+                    x[k] = (act && qok && tt < cnt) ? vin[(size_t)u * p.R + q] : zero;
+                }
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    acc.x |= x[k].x;
+                    acc.y |= x[k].y;
+                }
+                act = act && !seg_full(make_ulonglong2(acc.x | own.x, acc.y | own.y));
+                if (!__any_sync(FULL, act)) break;
+            }
         }
     }
     return acc;
 }
 
-// Finish one item: combine the slots, write the row segment, count, mark saturation.
-template <int G>
+
+// Finish one item: combine the slots, write the row segment, count, mark
+// saturation; at a masked level of a MASKS launch, also record which segments of
+// the tile gained bits and add the bits found to the block's count.
+template <int G, bool MASKS>
 __device__ __forceinline__ void finish_item(const BfsParams &p, ulonglong2 acc, const ulonglong2 own,
                                             ulonglong2 *orow, int q, bool qok, int v, int sidx,
-                                            int32_t *hrow, int level, bool &any_new) {
+                                            int32_t *hrow, int level, bool masked, bool &any_new) {
     const int lane = threadIdx.x & 31;
     const int slot = lane / G;
 #pragma unroll
@@ -234,12 +299,21 @@ __device__ __forceinline__ void finish_item(const BfsParams &p, ulonglong2 acc, 
         count = __popcll(nw.x) + __popcll(nw.y);
         full = seg_full(o);
     }
+    if constexpr (G == 32 && MASKS) {
+        if (masked) {
+            const unsigned changed = __ballot_sync(FULL, count != 0);
+            if (lane == 0) p.fmask[level & 1][(size_t)v * p.T + (q >> 5)] = changed;
+        }
+    }
     count = __reduce_add_sync(FULL, count);
     full = __all_sync(FULL, full);
     if (lane == 0) {
         if (count) {
             if (p.T > 1) atomicAdd(hrow + v, count);
             else hrow[v] += count;
+            if constexpr (MASKS) {
+                if (masked) atomicAdd(&block_found, (unsigned)count);
+            }
             any_new = true;
         }
         if (full) p.sat[sidx] = level;
@@ -249,7 +323,9 @@ __device__ __forceinline__ void finish_item(const BfsParams &p, ulonglong2 acc, 
 // Heavy rows (the first order[n] nodes, rows of 32 segments or more): one block
 // per (node, tile) item; warp w takes neighbour chunks w, w + 8, ...; the
 // partial ORs meet in shared memory and warp 0 finishes.
-__device__ void heavy_items(const BfsParams &p, const int level, bool &any_new, ulonglong2 (*red)[32]) {
+template <bool MASKS>
+__device__ void heavy_items(const BfsParams &p, const int level, const bool masked, bool &any_new,
+                            ulonglong2 (*red)[32]) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const ulonglong2 *vin = p.buf[(level - 1) & 1];
@@ -278,7 +354,7 @@ __device__ void heavy_items(const BfsParams &p, const int level, bool &any_new, 
         }
         const ulonglong2 own = qok ? vin[(size_t)v * p.R + q] : make_ulonglong2(ONES, ONES);
         const int beg = inf.y, end = inf.z;
-        red[wib][lane] = gather_or<32>(p, vin, beg + 32 * wib, end, 32 * WARPS, q, qok, own);
+        red[wib][lane] = gather_or<32, MASKS>(p, level, beg + 32 * wib, end, 32 * WARPS, q, qok, own, masked, t);
         __syncthreads();
         if (wib == 0) {
             ulonglong2 acc = red[0][lane];
@@ -286,7 +362,7 @@ __device__ void heavy_items(const BfsParams &p, const int level, bool &any_new, 
                 acc.x |= red[w][lane].x;
                 acc.y |= red[w][lane].y;
             }
-            finish_item<32>(p, acc, own, orow, q, qok, v, it, hrow, level, any_new);
+            finish_item<32, MASKS>(p, acc, own, orow, q, qok, v, it, hrow, level, masked, any_new);
         }
     }
 }
@@ -295,9 +371,9 @@ __device__ void heavy_items(const BfsParams &p, const int level, bool &any_new, 
 // runs the items a ballot marks (copy-ones items first, then pull items); the
 // pull items go to the next level's worklist.  The first pull level of a
 // launch lists every light item in order; later levels read the worklist.
-template <int G>
+template <int G, bool MASKS>
 __device__ __forceinline__ void light_items(const BfsParams &p, const int level, const bool from_list,
-                                            const bool make_list, bool &any_new) {
+                                            const bool make_list, const bool masked, bool &any_new) {
     const int lane = threadIdx.x & 31;
     const int slot = lane / G;
     const int ql = lane % G;
@@ -339,33 +415,69 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
         }
         const unsigned pulls = __ballot_sync(FULL, pull);
         mask = pulls;
-        // item state; the next item's own segment and first neighbour ids are
-        // requested before the current item's gathers, so the two overlap
-        struct Item {
-            int v, t, sidx, beg, end, myu;
-            ulonglong2 own;
-        };
-        auto fetch = [&](int b, Item &x) {
-            x.v = __shfl_sync(FULL, v_l, b);
-            x.t = __shfl_sync(FULL, t_l, b);
-            x.sidx = __shfl_sync(FULL, it, b);
-            x.beg = __shfl_sync(FULL, beg_l, b);
-            x.end = __shfl_sync(FULL, end_l, b);
-            const int q = x.t * 32 + ql;
-            x.own = (q < p.R) ? vin[(size_t)x.v * p.R + q] : make_ulonglong2(ONES, ONES);
-            x.myu = (lane < x.end - x.beg) ? p.col_idx[x.beg + lane] : 0;
-        };
-        Item cur, nxt;
-        if (mask) fetch(__ffs(mask) - 1, cur);
-        while (mask) {
-            mask &= mask - 1;
-            if (mask) fetch(__ffs(mask) - 1, nxt);
-            const int q = cur.t * 32 + ql;
-            const bool qok = q < p.R;
-            const ulonglong2 acc = gather_or<G>(p, vin, cur.beg, cur.end, 32, q, qok, cur.own, true, cur.myu);
-            finish_item<G>(p, acc, cur.own, vout + (size_t)cur.v * p.R, q, qok, cur.v, cur.sidx, hrow, level,
-                           any_new);
-            cur = nxt;
+        if constexpr (MASKS) {
+            // item state: the next item's own segment and first neighbour ids are
+            // requested before the current item's gathers, so the two overlap; the
+            // rest is shuffled again from the lane b that holds it when needed
+            struct Item {
+                int b, myu;
+                ulonglong2 own;
+            };
+            auto fetch = [&](int b, Item &x) {
+                x.b = b;
+                const int v = __shfl_sync(FULL, v_l, b);
+                const int q = __shfl_sync(FULL, t_l, b) * 32 + ql;
+                const int beg = __shfl_sync(FULL, beg_l, b);
+                const int len = __shfl_sync(FULL, end_l, b) - beg;
+                x.own = (q < p.R) ? vin[(size_t)v * p.R + q] : make_ulonglong2(ONES, ONES);
+                x.myu = (lane < len) ? p.col_idx[beg + lane] : 0;
+            };
+            Item cur, nxt;
+            if (mask) fetch(__ffs(mask) - 1, cur);
+            while (mask) {
+                mask &= mask - 1;
+                if (mask) fetch(__ffs(mask) - 1, nxt);
+                const int v = __shfl_sync(FULL, v_l, cur.b);
+                const int t = __shfl_sync(FULL, t_l, cur.b);
+                const int q = t * 32 + ql;
+                const bool qok = q < p.R;
+                const ulonglong2 acc = gather_or<G, true>(p, level, __shfl_sync(FULL, beg_l, cur.b),
+                                                          __shfl_sync(FULL, end_l, cur.b), 32, q, qok, cur.own,
+                                                          masked, t, true, cur.myu);
+                finish_item<G, true>(p, acc, cur.own, vout + (size_t)v * p.R, q, qok, v,
+                                     __shfl_sync(FULL, it, cur.b), hrow, level, masked, any_new);
+                cur = nxt;
+            }
+        } else {
+            // item state; the next item's own segment and first neighbour ids are
+            // requested before the current item's gathers, so the two overlap
+            struct Item {
+                int v, t, sidx, beg, end, myu;
+                ulonglong2 own;
+            };
+            auto fetch = [&](int b, Item &x) {
+                x.v = __shfl_sync(FULL, v_l, b);
+                x.t = __shfl_sync(FULL, t_l, b);
+                x.sidx = __shfl_sync(FULL, it, b);
+                x.beg = __shfl_sync(FULL, beg_l, b);
+                x.end = __shfl_sync(FULL, end_l, b);
+                const int q = x.t * 32 + ql;
+                x.own = (q < p.R) ? vin[(size_t)x.v * p.R + q] : make_ulonglong2(ONES, ONES);
+                x.myu = (lane < x.end - x.beg) ? p.col_idx[x.beg + lane] : 0;
+            };
+            Item cur, nxt;
+            if (mask) fetch(__ffs(mask) - 1, cur);
+            while (mask) {
+                mask &= mask - 1;
+                if (mask) fetch(__ffs(mask) - 1, nxt);
+                const int q = cur.t * 32 + ql;
+                const bool qok = q < p.R;
+                const ulonglong2 acc =
+                    gather_or<G, false>(p, level, cur.beg, cur.end, 32, q, qok, cur.own, false, 0, true, cur.myu);
+                finish_item<G, false>(p, acc, cur.own, vout + (size_t)cur.v * p.R, q, qok, cur.v, cur.sidx, hrow,
+                                      level, masked, any_new);
+                cur = nxt;
+            }
         }
         if (make_list && pulls) {
             int at = 0;
@@ -377,9 +489,16 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
     }
 }
 
-template <int G>
+// MASKS: the variant that keeps change masks (G = 32 only), for graphs whose
+// early frontiers are sparse; the plain variant reads every segment of every
+// neighbour.
+template <int G, bool MASKS>
 __global__ void __launch_bounds__(256, G == 32 ? 3 : 4) bfs_persistent(const BfsParams p) {
     __shared__ ulonglong2 red[WARPS][32];
+    if constexpr (MASKS) {
+        if (threadIdx.x == 0) block_found = 0u;
+        __syncthreads();
+    }
     int level = p.start_level;
     const bool stamp = p.stamp && blockIdx.x == 0 && threadIdx.x == 0;
     if (stamp) p.stamp[level - 1] = global_ns();
@@ -390,6 +509,11 @@ __global__ void __launch_bounds__(256, G == 32 ? 3 : 4) bfs_persistent(const Bfs
         if (!grid_barrier(p.bar, p.status)) return;
         if (stamp) p.stamp[2] = global_ns();
     }
+    // masks of the previous level are complete: the set-up writes level 1's, and
+    // a masked level writes its own; after the first level that is not masked
+    // none are written again (the frontiers only fill up from there), and a
+    // relaunch from a later level starts without them
+    bool masks_ok = p.start_level == 2;
     for (;; ++level) {
         if (level >= p.rows) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -398,13 +522,29 @@ __global__ void __launch_bounds__(256, G == 32 ? 3 : 4) bfs_persistent(const Bfs
             }
             return;
         }
+        // a MASKS launch reads and writes change masks at this level while the
+        // previous one found few bits (most segments unchanged)
+        bool masked = false;
+        if constexpr (MASKS) {
+            masked = masks_ok &&
+                     *(volatile unsigned long long *)(p.level_bits + level - 1) * (unsigned long long)p.mask_ratio <
+                         64ull * (unsigned long long)p.wn * (unsigned long long)p.n;
+            masks_ok = masked;
+        }
         bool any_new = false;
-        if (G == 32) heavy_items(p, level, any_new, red);
+        if (G == 32) heavy_items<MASKS>(p, level, masked, any_new, red);
         // the first pull levels touch nearly every item: scan them all; from the
         // third on, each level lists what it pulled for the next
-        light_items<G>(p, level, level >= p.start_level + LIST_AFTER + 1, level >= p.start_level + LIST_AFTER,
-                       any_new);
+        light_items<G, MASKS>(p, level, level >= p.start_level + LIST_AFTER + 1,
+                              level >= p.start_level + LIST_AFTER, masked, any_new);
         if (__syncthreads_or(any_new) && threadIdx.x == 0) p.level_new[level] = 1;
+        if constexpr (MASKS) {
+            // a count past 2^32 in one block only misjudges the density estimate
+            if (threadIdx.x == 0) {
+                if (block_found) atomicAdd(p.level_bits + level, (unsigned long long)block_found);
+                block_found = 0u;
+            }
+        }
         if (!grid_barrier(p.bar, p.status)) return;
         if (stamp) p.stamp[level + 1] = global_ns();
         if (*(volatile int32_t *)(p.level_new + level) == 0) break;
@@ -414,14 +554,14 @@ __global__ void __launch_bounds__(256, G == 32 ? 3 : 4) bfs_persistent(const Bfs
 
 typedef void (*bfs_fn)(const BfsParams);
 
-bfs_fn pick(int R, int *G) {
-    if (R <= 1) { *G = 1; return bfs_persistent<1>; }
-    if (R <= 2) { *G = 2; return bfs_persistent<2>; }
-    if (R <= 4) { *G = 4; return bfs_persistent<4>; }
-    if (R <= 8) { *G = 8; return bfs_persistent<8>; }
-    if (R <= 16) { *G = 16; return bfs_persistent<16>; }
+bfs_fn pick(int R, bool masks, int *G) {
+    if (R <= 1) { *G = 1; return bfs_persistent<1, false>; }
+    if (R <= 2) { *G = 2; return bfs_persistent<2, false>; }
+    if (R <= 4) { *G = 4; return bfs_persistent<4, false>; }
+    if (R <= 8) { *G = 8; return bfs_persistent<8, false>; }
+    if (R <= 16) { *G = 16; return bfs_persistent<16, false>; }
     *G = 32;
-    return bfs_persistent<32>;
+    return masks ? bfs_persistent<32, true> : bfs_persistent<32, false>;
 }
 
 // Grow hist to at least `rows` levels (new rows zeroed), keeping the old rows.
@@ -478,16 +618,29 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
     const int32_t wc = qc_bfs_chunk_words(ctx, n);
     const int32_t R_max = (wc + 1) / 2;
     const int32_t T_max = R_max >= 32 ? (R_max + 31) / 32 : 1;
-    qc_buffer visA, visB, sat, ctl, wl;
+    qc_buffer visA, visB, sat, ctl, wl, fmask;
     const size_t vis_bytes = sizeof(ulonglong2) * (size_t)R_max * (size_t)n;
     QC_TRY(visA.allocate(ctx, vis_bytes, stream));
     QC_TRY(visB.allocate(ctx, vis_bytes, stream));
+    // Change masks (rows of more than 16 segments) pay off when the frontiers of the
+    // first pull levels are sparse: a tree-like graph of mean degree d reaches about
+    // d^2 of its n nodes in two hops, so the variant with masks is taken when
+    // d^2 * mask_ratio < n (a level then reads masked segments while the previous
+    // level found fewer than 64 wn n / mask_ratio new bits).  Measured on GB300:
+    // SBM of mean degree 20 with n = 2^16 and 2^18, 4.5 % and 9 % faster; a
+    // DC-SBM of n = 2^14 and mean degree 16, 10 % slower (only its level 2 is sparse).
+    // QCGRAPH_MASK_RATIO overrides the ratio (0: never).
+    int32_t mask_ratio = 128;
+    if (const char *env = getenv("QCGRAPH_MASK_RATIO")) mask_ratio = std::max(0, atoi(env));
+    const double mean_deg = (double)g->nnz / (double)n;
+    const bool masks = mask_ratio > 0 && R_max > 16 && mean_deg * mean_deg * mask_ratio < (double)n;
+    if (masks) QC_TRY(fmask.allocate(ctx, 2 * sizeof(uint32_t) * (size_t)n * T_max, stream));
     QC_TRY(sat.allocate(ctx, sizeof(int32_t) * (size_t)n * T_max, stream));
     QC_TRY(wl.allocate(ctx, 2 * sizeof(int32_t) * (size_t)n * T_max, stream));
     // control block: status (2 ints), barrier (2 uints), pad, then level_new, the
     // per-level work counters (light, heavy) and worklist lengths, each with room for
-    // any depth (<= n + 1)
-    const size_t ctl_ints = 8 + 4 * ((size_t)n + 2);
+    // any depth (<= n + 1), then the per-level bit counts (64-bit, at an even offset)
+    const size_t ctl_ints = 8 + 6 * ((size_t)n + 2);
     QC_TRY(ctl.allocate(ctx, sizeof(int32_t) * ctl_ints, stream));
     qc_pinned pin(ctx);
     QC_TRY(pin.acquire());
@@ -507,7 +660,7 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
         const int32_t R = (wn + 1) / 2;
         const int32_t T = R >= 32 ? (R + 31) / 32 : 1;
         int G = 32;
-        bfs_fn fn = pick(R, &G);
+        bfs_fn fn = pick(R, masks, &G);
         int per_sm = 0;
         QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, 256, 0));
         if (per_sm < 1) {
@@ -532,6 +685,10 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
             p.wmask = g->wmask.as<unsigned long long>();
             p.buf[0] = visB.as<ulonglong2>();
             p.buf[1] = visA.as<ulonglong2>();
+            const bool with_masks = masks && G == 32;
+            p.fmask[0] = with_masks ? fmask.as<uint32_t>() : nullptr;
+            p.fmask[1] = with_masks ? fmask.as<uint32_t>() + (size_t)n * T_max : nullptr;
+            p.mask_ratio = mask_ratio;
             p.R = R;
             p.T = T;
             p.w0 = w0;
@@ -549,6 +706,7 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
             p.light_ctr = p.level_new + (n + 2);
             p.heavy_ctr = p.light_ctr + (n + 2);
             p.wl_count = p.heavy_ctr + (n + 2);
+            p.level_bits = reinterpret_cast<unsigned long long *>(p.wl_count + (n + 2));
             p.wl[0] = wl.as<int32_t>();
             p.wl[1] = wl.as<int32_t>() + (size_t)n * T_max;
             p.stamp = timing ? stamps.as<unsigned long long>() : nullptr;

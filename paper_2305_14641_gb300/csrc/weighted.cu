@@ -310,7 +310,8 @@ __global__ void check_weights(int32_t n, const int32_t *row_ptr, const int32_t *
 
 int32_t sources_per_batch(const qc_ctx *ctx, int32_t n) {
     int64_t K;
-    if (const char *env = getenv("QCGRAPH_SSSP_SOURCES")) {
+    const char *env = getenv("QCGRAPH_SSSP_SOURCES");
+    if (env) {
         K = atoll(env);
     } else {
         const size_t target = ctx->l2_bytes ? ctx->l2_bytes / 2 : (size_t)48 << 20;
@@ -318,7 +319,7 @@ int32_t sources_per_batch(const qc_ctx *ctx, int32_t n) {
     }
     K = (K / 32) * 32;
     if (K < 32) K = 32;
-    if (K > 1024) K = 1024;
+    if (!env && K > 1024) K = 1024;
     const int64_t cover = ((int64_t)n + 31) / 32 * 32;
     return (int32_t)std::min<int64_t>(K, cover);
 }

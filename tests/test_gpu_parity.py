@@ -109,6 +109,24 @@ def test_forced_source_chunks(qc, ctx, chunk, monkeypatch):
     assert_solution_matches(qc, ctx, graph, [0.9, 2.2])
 
 
+@pytest.mark.parametrize("ratio,chunk", [("1", "96"), ("1", "40"), ("128", "96"), ("0", "96")])
+def test_change_masks(qc, ctx, ratio, chunk, monkeypatch):
+    """The variant with change masks (rows of more than 16 segments on sparse
+    graphs): ratio 1 takes it and reads masked segments at every level, 128 is
+    the default rule (masked levels only while the frontier is sparse), 0 never
+    takes it.  Chunks of 96 words give rows of two tiles and a ragged second
+    chunk (45 words, one tile); 40 words give one-tile rows of 20 segments."""
+    monkeypatch.setenv("QCGRAPH_MASK_RATIO", ratio)
+    monkeypatch.setenv("QCGRAPH_CHUNK_WORDS", chunk)
+    graph = gg.planted_partition(9000, 30, 0.012, 0.0002, gg.rng(25, int(chunk)))
+    assert_solution_matches(qc, ctx, graph, [0.7, 1.6])
+    # a path: one new bit per level over 4199 levels (the histogram grows and the
+    # kernel is relaunched from the level where it stopped)
+    assert_solution_matches(qc, ctx, gg.path(4200), [3.0])
+    # directed: rows are out-arcs, weak components
+    assert_solution_matches(qc, ctx, gg.directed_erdos_renyi(6000, 3.0 / 6000, gg.rng(26, int(chunk))), [1.2])
+
+
 def test_planted_and_dcsbm_mid(qc, ctx):
     g1 = gg.planted_partition(4000, 16, 0.02, 0.0005, gg.rng(23))
     g2 = gg.dcsbm(3000, 8, 2.5, 10.0, 200.0, 0.1, gg.rng(24))
