@@ -4,8 +4,8 @@
 // real, so the potential of Algorithm 1 is summed pair by pair instead of
 // through integer distance bins.
 //
-// Shortest paths: sources are processed K at a time (K a multiple of 32, sized
-// so that the distance block fits in about half of L2).  dist[v][k] (node-major,
+// Shortest paths: sources are processed K at a time (K a multiple of 32, the
+// distance block near eight times L2).  dist[v][k] (node-major,
 // binary64) holds the best length found from source s0 + k to v.  One
 // persistent cooperative launch relaxes, pass after pass,
 //     dist[v][k] = min(dist[v][k], min_{u in row v} dist[u][k] + w(v, u))
@@ -308,19 +308,25 @@ __global__ void check_weights(int32_t n, const int32_t *row_ptr, const int32_t *
     if (lane == 0 && bad) atomicOr(err, bad);
 }
 
+// Sources per shortest-path launch.  Each pass of a launch ends at a grid
+// barrier whose cost does not grow with K, so wide blocks win even after the
+// distance block leaves L2: measured on GB300 (the DC-SBM of N = 16384), the
+// shortest paths took 126 ms with K = 512 (half of L2), 110 ms with 1024 and
+// 103 ms from 4096 up.  K is sized for a distance block near eight times L2 and
+// split evenly over the n sources, a multiple of 32.  QCGRAPH_SSSP_SOURCES
+// overrides it.
 int32_t sources_per_batch(const qc_ctx *ctx, int32_t n) {
-    int64_t K;
-    const char *env = getenv("QCGRAPH_SSSP_SOURCES");
-    if (env) {
-        K = atoll(env);
-    } else {
-        const size_t target = ctx->l2_bytes ? ctx->l2_bytes / 2 : (size_t)48 << 20;
-        K = (int64_t)(target / (8 * (size_t)n));
-    }
-    K = (K / 32) * 32;
-    if (K < 32) K = 32;
-    if (!env && K > 1024) K = 1024;
     const int64_t cover = ((int64_t)n + 31) / 32 * 32;
+    int64_t K;
+    if (const char *env = getenv("QCGRAPH_SSSP_SOURCES")) {
+        K = atoll(env) / 32 * 32;
+    } else {
+        const size_t l2 = ctx->l2_bytes ? ctx->l2_bytes : (size_t)96 << 20;
+        const int64_t target = std::max<int64_t>((int64_t)(8 * l2 / (8 * (size_t)std::max(n, 1))), 32);
+        const int64_t batches = (cover + target - 1) / target;
+        K = ((cover + batches - 1) / batches + 31) / 32 * 32;
+    }
+    if (K < 32) K = 32;
     return (int32_t)std::min<int64_t>(K, cover);
 }
 
