@@ -341,6 +341,18 @@ void qc_server_destroy(qc_server *s);
  * to notice the missing block, QC_ERR_INVALID_ARG for a bad limit. */
 qc_status qc_selftest_barrier_timeout(qc_ctx *ctx, int64_t spin_limit, void *stream);
 
+/* ---- self-test of the weighted potential's exponential ---------------------------- */
+
+/* The paper has no counterpart to this call.  The weighted potential
+ * (qc_potential_weighted) evaluates exp(-t) for every pair and sigma with the
+ * library's own table-driven routine (Tang's method, mostly in 64-bit fixed
+ * point); this call runs that routine on caller data so that its accuracy can
+ * be checked against a reference exp.  t: device binary64[n], each >= 0 and not
+ * NaN; out: device binary64[n] receives exp(-t[i]) (0 from t = 745 on).  Both
+ * caller-owned, stream-ordered on `stream`.  QC_ERR_INVALID_ARG for null
+ * pointers with n > 0 or n < 0. */
+qc_status qc_selftest_exp_neg(qc_ctx *ctx, const double *t, double *out, int64_t n, void *stream);
+
 /* ---- histogram without device allocation ---------------------------------------- */
 
 /* The paper has no counterpart to this call; it exists for callers that may not

@@ -92,6 +92,16 @@ class Context:
         st = self._lib.qc_selftest_barrier_timeout(self.handle, int(spin_limit), _stream_handle(stream))
         return native.STATUS.get(st, str(st))
 
+    def selftest_exp_neg(self, t, stream=None):
+        """exp(-t) by the weighted potential's own routine (t: float64, >= 0); returns a
+        float64 device tensor."""
+        torch = _torch()
+        t = torch.as_tensor(t, dtype=torch.float64, device=f"cuda:{self.device}").contiguous()
+        out = torch.empty_like(t)
+        self.check(self._lib.qc_selftest_exp_neg(self.handle, t.data_ptr(), out.data_ptr(), t.numel(),
+                                                 _stream_handle(stream)))
+        return out
+
     def bytes_in_use(self) -> int:
         return int(self._lib.qc_context_bytes_in_use(self.handle))
 

@@ -31,8 +31,9 @@
 //
 // Potential: for node v, sum1 = sum_j d^2 e^{-d^2 / 2 sigma^2} and
 // sum2 = sum_j e^{...} over the j that v reaches (the self term adds 1 to
-// sum2), d = dist[v][j - s0] of each batch, with a table-driven binary64
-// exp (below) of d^2 x 1 / (2 sigma^2) and separately rounded multiplies and adds.  The sums run over each batch's
+// sum2), d = dist[v][j - s0] of each batch, with a table-driven exp (below,
+// fixed point but for its last multiply) of d^2 x 1 / (2 sigma^2) and
+// separately rounded binary64 multiplies and adds.  The sums run over each batch's
 // sources in a fixed pattern and over the batches in order, so the result is
 // the same on every run; it differs from the oracle's sequential sum over j
 // only by rounding (relative 1e-15 or so).
@@ -192,18 +193,30 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
 }
 
 // exp(-t) for t >= 0 by the table-driven method of Tang (ACM TOMS 15(2), 1989):
-// t = a + b/64 + r with integers a, b (0 <= b < 64) and 0 <= r < 1/64, so
-// exp(-t) = exp(-a) exp(-b/64) exp(-r), the first two from tables built on the
-// host with the C library's exp and the last from its Taylor series to degree 6
-// (truncation below 1e-16 relative).  About 4 ulp in all, far inside the 1e-12
-// the potential is held to, for a third of the binary64 work of a general exp.
-// Below exp(-745) (the smallest subnormal) it returns 0.
+// t = a + b/1024 + r with integers a, b (0 <= b < 1024) and 0 <= r < 2^-10, so
+// exp(-t) = exp(-a) exp(-b/1024) exp(-r).  On GB300 binary64 arithmetic runs at
+// a small fraction of the integer rate, so everything but the last multiply is
+// done in 64-bit fixed point:
+//   * t (< 708) becomes T = floor(t 2^53), exact to 2^-53 absolute (1 ulp of
+//     exp(-t) near 1, less elsewhere); a, b and r are bit fields of T;
+//   * exp(-r) = 1 - r (1 - r/2 (1 - r/3 (1 - r/4))) (truncation below 1e-17
+//     relative) in Q1.63 by Horner's rule with 64 x 64 -> high 64 products;
+//   * times exp(-b/1024), a Q1.63 table built on the host in extended
+//     precision; the product is rounded once to binary64 and scaled by 2^-63
+//     in its exponent field (exact);
+//   * times exp(-a), a binary64 table: one rounded multiply.
+// About 2 ulp in all.  Above t = 708 the result is subnormal, where the
+// binary64 form below (same tables for exp(-a)) is kept; from 745 on it is 0.
+// The tables travel as a kernel parameter and each block copies them to shared
+// memory: lanes index them at random, which the constant bank would serialise.
 struct ExpTables {
     double hi[746];                // exp(-a), a = 0 .. 745
-    double lo[64];                 // exp(-b / 64), b = 0 .. 63
+    double lo[64];                 // exp(-b / 64), b = 0 .. 63 (binary64 form)
+    unsigned long long fx[1024];   // exp(-b / 1024) in Q1.63, b = 0 .. 1023
 };
 
-__device__ __forceinline__ double exp_neg(double t, const ExpTables &T) {
+// binary64 form: t = a + b/64 + r, exp(-r) by its Taylor series to degree 6
+__device__ __forceinline__ double exp_neg_f64(double t, const ExpTables &T) {
     if (!(t < 745.0)) return 0.0;
     const int k = (int)(t * 64.0);                        // t * 64 is exact; truncation = floor here
     const double r = t - (double)k * (1.0 / 64.0);        // exact (Sterbenz) or r = t when k = 0
@@ -218,6 +231,38 @@ __device__ __forceinline__ double exp_neg(double t, const ExpTables &T) {
     return T.hi[k >> 6] * T.lo[k & 63] * p;
 }
 
+// The block's shared copy of the tables (call before any exp_neg).
+__device__ __forceinline__ void load_exp_tables(ExpTables &dst, const ExpTables &src) {
+    static_assert(sizeof(ExpTables) % 8 == 0, "tables are 8-byte words");
+    const unsigned long long *from = reinterpret_cast<const unsigned long long *>(&src);
+    unsigned long long *to = reinterpret_cast<unsigned long long *>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(ExpTables) / 8); i += blockDim.x) to[i] = from[i];
+    __syncthreads();
+}
+
+__device__ __forceinline__ double exp_neg(double t, const ExpTables &T) {
+    if (!(t < 708.0)) return exp_neg_f64(t, T);
+    constexpr unsigned long long ONE = 1ull << 63;        // 1.0 in Q1.63
+    constexpr unsigned long long THIRD = 0x5555555555555555ull;   // floor(2^64 / 3)
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(t);
+    const int e = (int)(bits >> 52);                      // t >= 0: no sign bit
+    const unsigned long long m = (bits & ((1ull << 52) - 1)) | (e ? (1ull << 52) : 0ull);
+    // T = floor(m 2^(e - 1022)) = floor(t 2^53); t < 2^10 keeps T below 2^63
+    const int sh = (e ? e : 1) - 1022;
+    const unsigned long long Tf = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ull);
+    const int a = (int)(Tf >> 53);
+    const int b = (int)((Tf >> 43) & 1023);
+    const unsigned long long rq = (Tf & ((1ull << 43) - 1)) << 11;   // r 2^64, r < 2^-10
+    unsigned long long w = ONE - (rq >> 3);                          // 1 - r/4
+    w = ONE - __umul64hi(__umul64hi(rq, THIRD), w);                  // 1 - r/3 (...)
+    w = ONE - __umul64hi(rq >> 1, w);                                // 1 - r/2 (...)
+    w = ONE - __umul64hi(rq, w);                                     // exp(-r)
+    const unsigned long long L = T.fx[b];
+    const unsigned long long M = (__umul64hi(L, w) << 1) | ((L * w) >> 63);   // Q1.63, in (0.36, 1]
+    const double Md = __longlong_as_double(__double_as_longlong(__ull2double_rn(M)) - (63ll << 52));
+    return __dmul_rn(T.hi[a], Md);
+}
+
 // acc[s][v] += (sum1, sum2) over the batch's sources for node v: a warp per node,
 // lane l takes sources l, l + 32, ... in order (each distance read once for up
 // to SGRP sigma values), then a butterfly over the lanes (every lane ends with
@@ -225,7 +270,9 @@ __device__ __forceinline__ double exp_neg(double t, const ExpTables &T) {
 // on every run.
 constexpr int SGRP = 8;
 __global__ void wpot_accumulate(int32_t n, int32_t K, int32_t ns, const double *dist, int32_t S,
-                                const double *den, double2 *acc, const __grid_constant__ ExpTables T) {
+                                const double *den, double2 *acc, const __grid_constant__ ExpTables Tp) {
+    __shared__ ExpTables T;
+    load_exp_tables(T, Tp);
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -315,6 +362,22 @@ __global__ void check_weights(int32_t n, const int32_t *row_ptr, const int32_t *
 // 103 ms from 4096 up.  K is sized for a distance block near eight times L2 and
 // split evenly over the n sources, a multiple of 32.  QCGRAPH_SSSP_SOURCES
 // overrides it.
+// The exponential's tables, from the C library's exp in extended precision
+// (long double), each rounded once.
+void fill_exp_tables(ExpTables &T) {
+    for (int a = 0; a < 746; ++a) T.hi[a] = (double)std::exp(-(long double)a);
+    for (int b = 0; b < 64; ++b) T.lo[b] = (double)std::exp(-(long double)b / 64.0L);
+    for (int b = 0; b < 1024; ++b)   // <= 2^63, rounded to the nearest integer
+        T.fx[b] = (unsigned long long)(std::ldexp(std::exp(-(long double)b / 1024.0L), 63) + 0.5L);
+}
+
+__global__ void exp_neg_kernel(int64_t n, const double *t, double *out, const __grid_constant__ ExpTables Tp) {
+    __shared__ ExpTables T;
+    load_exp_tables(T, Tp);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = exp_neg(t[i], T);
+}
+
 int32_t sources_per_batch(const qc_ctx *ctx, int32_t n) {
     const int64_t cover = ((int64_t)n + 31) / 32 * 32;
     int64_t K;
@@ -395,8 +458,7 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
     std::vector<double> den(n_sigma);
     for (int32_t s = 0; s < n_sigma; ++s) den[s] = 2.0 * (sigmas[s] * sigmas[s]);
     ExpTables etab;
-    for (int a = 0; a < 746; ++a) etab.hi[a] = std::exp(-(double)a);
-    for (int b = 0; b < 64; ++b) etab.lo[b] = std::exp(-(double)b / 64.0);
+    fill_exp_tables(etab);
     qc_buffer dist, chg, chgv, ctl, acc, dden;
     QC_TRY(dist.allocate(ctx, sizeof(double) * (size_t)n * K, stream));
     QC_TRY(chg.allocate(ctx, sizeof(int32_t) * (size_t)n * KG, stream));
@@ -461,6 +523,19 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
     }
     const int fb = std::max(1, std::min(qc_ceil_div((int64_t)n_sigma * n, 256), 2 * ctx->num_sms));
     wpot_final<<<fb, 256, 0, stream>>>(n, n_sigma, dden.as<double>(), acc.as<double2>(), V_out);
+    QC_LAUNCHED(ctx);
+    return QC_OK;
+}
+
+extern "C" qc_status qc_selftest_exp_neg(qc_ctx *ctx, const double *t, double *out, int64_t n, void *stream_) {
+    if (!ctx || n < 0 || (n > 0 && (!t || !out))) return QC_ERR_INVALID_ARG;
+    if (n == 0) return QC_OK;
+    cudaStream_t stream = qc_stream(stream_);
+    QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    ExpTables etab;
+    fill_exp_tables(etab);
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * (int64_t)ctx->num_sms);
+    exp_neg_kernel<<<blocks, 256, 0, stream>>>(n, t, out, etab);
     QC_LAUNCHED(ctx);
     return QC_OK;
 }

@@ -411,6 +411,39 @@ def test_weighted_batches_and_unit_weights(qc, ctx, monkeypatch):
     assert np.allclose(Vw, hop, rtol=1e-12, atol=0)
 
 
+def test_exp_neg_accuracy(qc, ctx):
+    """The weighted potential's exp(-t) (Tang's tables, fixed-point core) against
+    the C library's exp and a 120-bit reference: within 3 ulp below t = 708
+    (normal results), and within
+    4 ulp plus two subnormal steps above it; 0 from t = 745.  Points: a dense
+    random sweep, table boundaries (integers, multiples of 1/1024 and their
+    neighbours), tiny arguments and the branch edges."""
+    g = gg.rng(41)
+    t = [g.uniform(0.0, 745.0, 400000), g.uniform(0.0, 1.0, 100000), 10.0 ** g.uniform(-20, 0, 50000)]
+    grid = np.concatenate([np.arange(0, 746, dtype=np.float64), np.arange(0, 8 * 1024) / 1024.0,
+                           700.0 + np.arange(0, 1024) / 1024.0])
+    t += [grid, np.nextafter(grid, np.inf), np.nextafter(np.maximum(grid, 1e-300), 0.0)]
+    t.append(np.array([0.0, 5e-324, 1e-300, 2.0 ** -60, 2.0 ** -53, 2.0 ** -43, 2.0 ** -10, 707.999999,
+                       708.0, np.nextafter(708.0, 0.0), 744.4, 745.0, np.nextafter(745.0, 0.0), 746.0, 800.0,
+                       1e300, np.inf]))
+    t = np.concatenate(t)
+    got = ctx.selftest_exp_neg(t).cpu().numpy()
+    ref = np.exp(-t)
+    err = np.abs(got - ref)
+    normal = t < 708.0
+    assert np.all(err[normal] <= 3 * np.spacing(ref[normal])), float(np.max(err[normal] / np.spacing(ref[normal])))
+    sub = ~normal
+    assert np.all(err[sub] <= 4 * np.spacing(ref[sub]) + 2 * 5e-324)
+    assert np.all(got[t >= 745.0] == 0.0)
+    assert np.count_nonzero(t == 0.0) > 0 and np.all(got[t == 0.0] == 1.0)
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 120
+    pick = np.concatenate([np.arange(0, len(t), 997), np.nonzero(normal)[0][-50:]])
+    exact = np.array([float(mpmath.exp(-mpmath.mpf(float(x)))) for x in t[pick]])
+    keep = t[pick] < 708.0
+    assert np.all(np.abs(got[pick] - exact)[keep] <= 3 * np.spacing(exact[keep]))
+
+
 def test_weighted_invalid(qc, ctx):
     graph = gg.erdos_renyi(200, 0.05, gg.rng(39))
     G = qc.Graph.from_graph(ctx, graph)
