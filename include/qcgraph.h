@@ -341,17 +341,25 @@ void qc_server_destroy(qc_server *s);
  * to notice the missing block, QC_ERR_INVALID_ARG for a bad limit. */
 qc_status qc_selftest_barrier_timeout(qc_ctx *ctx, int64_t spin_limit, void *stream);
 
-/* ---- self-test of the weighted potential's exponential ---------------------------- */
+/* ---- self-test of the weighted potential's arithmetic ----------------------------- */
 
-/* The paper has no counterpart to this call.  The weighted potential
- * (qc_potential_weighted) evaluates exp(-t) for every pair and sigma with the
- * library's own table-driven routine (Tang's method, mostly in 64-bit fixed
- * point); this call runs that routine on caller data so that its accuracy can
- * be checked against a reference exp.  t: device binary64[n], each >= 0 and not
- * NaN; out: device binary64[n] receives exp(-t[i]) (0 from t = 745 on).  Both
- * caller-owned, stream-ordered on `stream`.  QC_ERR_INVALID_ARG for null
- * pointers with n > 0 or n < 0. */
-qc_status qc_selftest_exp_neg(qc_ctx *ctx, const double *t, double *out, int64_t n, void *stream);
+/* The paper has no counterpart to this call.  The weighted path does its
+ * binary64 work largely on the integer pipe (GB300 issues binary64 operations
+ * at a small fraction of its integer rate), with two routines of its own; this
+ * call runs one of them elementwise on caller data so that it can be checked
+ * against the hardware's or a reference's results:
+ *   QC_ARITH_EXP_NEG  out[i] = exp(-x[i]) (Tang's table-driven method, mostly in
+ *                     64-bit fixed point; about 2 ulp; 0 from x = 745 on);
+ *                     x[i] >= 0 and not NaN; y unused (may be null).
+ *   QC_ARITH_ADD_POS  out[i] = x[i] + y[i] rounded to nearest even, as the
+ *                     shortest-path relaxation computes it; x[i], y[i] >= 0
+ *                     (+inf allowed), not NaN.
+ * x, y, out: device binary64[n], caller-owned, stream-ordered on `stream`.
+ * QC_ERR_INVALID_ARG for an unknown op, n < 0, or a null pointer that op reads
+ * or writes (n > 0). */
+enum { QC_ARITH_EXP_NEG = 0, QC_ARITH_ADD_POS = 1 };
+qc_status qc_selftest_arith(qc_ctx *ctx, int32_t op, const double *x, const double *y, double *out, int64_t n,
+                            void *stream);
 
 /* ---- histogram without device allocation ---------------------------------------- */
 

@@ -92,15 +92,25 @@ class Context:
         st = self._lib.qc_selftest_barrier_timeout(self.handle, int(spin_limit), _stream_handle(stream))
         return native.STATUS.get(st, str(st))
 
+    def _selftest_arith(self, op: int, x, y, stream):
+        torch = _torch()
+        dev = f"cuda:{self.device}"
+        x = torch.as_tensor(x, dtype=torch.float64, device=dev).contiguous()
+        y = None if y is None else torch.as_tensor(y, dtype=torch.float64, device=dev).contiguous()
+        out = torch.empty_like(x)
+        self.check(self._lib.qc_selftest_arith(self.handle, op, x.data_ptr(), 0 if y is None else y.data_ptr(),
+                                               out.data_ptr(), x.numel(), _stream_handle(stream)))
+        return out
+
     def selftest_exp_neg(self, t, stream=None):
         """exp(-t) by the weighted potential's own routine (t: float64, >= 0); returns a
         float64 device tensor."""
-        torch = _torch()
-        t = torch.as_tensor(t, dtype=torch.float64, device=f"cuda:{self.device}").contiguous()
-        out = torch.empty_like(t)
-        self.check(self._lib.qc_selftest_exp_neg(self.handle, t.data_ptr(), out.data_ptr(), t.numel(),
-                                                 _stream_handle(stream)))
-        return out
+        return self._selftest_arith(0, t, None, stream)
+
+    def selftest_add_pos(self, x, y, stream=None):
+        """x + y (float64, >= 0) by the shortest-path relaxation's own adder; returns a
+        float64 device tensor."""
+        return self._selftest_arith(1, x, y, stream)
 
     def bytes_in_use(self) -> int:
         return int(self._lib.qc_context_bytes_in_use(self.handle))

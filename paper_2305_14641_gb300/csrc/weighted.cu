@@ -68,15 +68,56 @@ struct SsspParams {
     int32_t *pass_new;             // [max_pass + 1] some value fell
 };
 
-__global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
+// x + y for x, y >= 0 (x may be +inf), rounded to nearest even like the
+// hardware add, but on the integer pipe: GB300 issues binary64 adds at a small
+// fraction of its integer rate.  Mantissas carry three extra bits (guard,
+// round and a sticky bit that collects everything shifted out), the standard
+// construction for a correctly rounded sum; a zero or subnormal y and an
+// infinite x go to the hardware add.  Non-negative binary64 values order like
+// their bit patterns, so the relaxation compares them as integers.
+__device__ __forceinline__ unsigned long long add_pos(unsigned long long a, unsigned long long b) {
+    constexpr unsigned long long MANT = (1ull << 52) - 1, IMPL = 1ull << 52;
+    if (a < b) {
+        const unsigned long long t = a;
+        a = b;
+        b = t;
+    }
+    const int ea = (int)(a >> 52), eb = (int)(b >> 52);
+    if (ea == 2047 || eb == 0)
+        return (unsigned long long)__double_as_longlong(
+            __dadd_rn(__longlong_as_double((long long)a), __longlong_as_double((long long)b)));
+    const int d = ea - eb;
+    if (d >= 54) return a;                      // b is below half an ulp of a
+    const unsigned long long ma = ((a & MANT) | IMPL) << 3;
+    const unsigned long long mb0 = ((b & MANT) | IMPL) << 3;
+    const unsigned long long mb = (mb0 >> d) | (unsigned long long)((mb0 & ((1ull << d) - 1)) != 0);
+    unsigned long long s = ma + mb;             // below 2^57
+    int e = ea;
+    if (s >> 56) {
+        s = (s >> 1) | (s & 1ull);
+        ++e;
+    }
+    const unsigned low = (unsigned)(s & 7ull);
+    s >>= 3;
+    if (low > 4u || (low == 4u && (s & 1ull))) ++s;
+    if (s >> 53) {
+        s >>= 1;
+        ++e;
+    }
+    if (e >= 2047) return 0x7ff0000000000000ull;
+    return ((unsigned long long)e << 52) | (s & MANT);
+}
+
+// Three blocks per SM (80 registers, a few spills) beat two blocks without
+// spills (104 registers): 68 against 82 ms for the DC-SBM of N = 16384.
+__global__ void __launch_bounds__(256, 3) sssp_persistent(const SsspParams p) {
     const int lane = threadIdx.x & 31;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nthreads = gridDim.x * blockDim.x;
-    const double INF = __longlong_as_double(0x7ff0000000000000ll);
     // pass 0: each source at distance 0 from itself
     for (long long i = tid; i < (long long)p.n * p.K; i += nthreads) {
         const int v = (int)(i / p.K), k = (int)(i - (long long)v * p.K);
-        p.dist[i] = (k < p.ns && v == p.s0 + k) ? 0.0 : INF;
+        p.dist[i] = (k < p.ns && v == p.s0 + k) ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
     }
     for (long long i = tid; i < (long long)p.n * p.KG; i += nthreads) {
         const int v = (int)(i / p.KG), g = (int)(i - (long long)v * p.KG);
@@ -110,20 +151,23 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
             // so that a lane has up to GU x NB distances in flight
             {
                 const int g0 = gb * GU;
-                double mine[GU], best[GU];
+                const unsigned long long *dist = reinterpret_cast<const unsigned long long *>(p.dist);
+                constexpr unsigned long long INFB = 0x7ff0000000000000ull;
+                unsigned long long mine[GU], best[GU];
 #pragma unroll
                 for (int q = 0; q < GU; ++q) {
-                    mine[q] = (g0 + q < p.KG) ? *(volatile const double *)(p.dist + (size_t)v * p.K + (g0 + q) * 32 + lane)
-                                              : INF;
+                    mine[q] = (g0 + q < p.KG) ? *(volatile const unsigned long long *)(dist + (size_t)v * p.K +
+                                                                                      (g0 + q) * 32 + lane)
+                                              : INFB;
                     best[q] = mine[q];
                 }
                 for (int e0 = beg; e0 < end; e0 += 32) {
                     const int e = e0 + lane;
                     int u = 0;
-                    double wt = 0.0;
+                    unsigned long long wt = 0ull;
                     if (e < end) {
                         u = p.col_idx[e];
-                        wt = p.w[e];
+                        wt = (unsigned long long)__double_as_longlong(p.w[e]);
                     }
                     unsigned fm[GU];
                     unsigned any_fresh = 0u;
@@ -136,7 +180,7 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
                     }
                     while (any_fresh) {
                         int ub[NB], bb[NB];
-                        double wb[NB];
+                        unsigned long long wb[NB];
 #pragma unroll
                         for (int i = 0; i < NB; ++i) {
                             bb[i] = -1;
@@ -148,20 +192,21 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
                             ub[i] = __shfl_sync(FULL, u, src);
                             wb[i] = __shfl_sync(FULL, wt, src);
                         }
-                        double db[NB][GU];
+                        unsigned long long db[NB][GU];
 #pragma unroll
                         for (int i = 0; i < NB; ++i)
 #pragma unroll
                             for (int q = 0; q < GU; ++q)
                                 db[i][q] = (bb[i] >= 0 && ((fm[q] >> bb[i]) & 1u))
-                                               ? *(volatile const double *)(p.dist + (size_t)ub[i] * p.K +
-                                                                            (g0 + q) * 32 + lane)
-                                               : INF;
+                                               ? *(volatile const unsigned long long *)(dist + (size_t)ub[i] * p.K +
+                                                                                        (g0 + q) * 32 + lane)
+                                               : INFB;
 #pragma unroll
                         for (int i = 0; i < NB; ++i)
 #pragma unroll
                             for (int q = 0; q < GU; ++q) {
-                                const double c = __dadd_rn(db[i][q], wb[i]);
+                                if (db[i][q] >= best[q]) continue;   // w > 0: no shorter path through u
+                                const unsigned long long c = add_pos(db[i][q], wb[i]);
                                 if (c < best[q]) best[q] = c;
                             }
                     }
@@ -170,7 +215,9 @@ __global__ void __launch_bounds__(256) sssp_persistent(const SsspParams p) {
                 for (int q = 0; q < GU; ++q) {
                     if (g0 + q >= p.KG) break;
                     const bool fell = best[q] < mine[q];
-                    if (fell) *(volatile double *)(p.dist + (size_t)v * p.K + (g0 + q) * 32 + lane) = best[q];
+                    if (fell)
+                        *(volatile unsigned long long *)(reinterpret_cast<unsigned long long *>(p.dist) +
+                                                         (size_t)v * p.K + (g0 + q) * 32 + lane) = best[q];
                     if (__any_sync(FULL, fell)) {
                         v_fell = true;
                         if (lane == 0) *(volatile int32_t *)(p.chg + (size_t)v * p.KG + g0 + q) = pass;
@@ -378,6 +425,12 @@ __global__ void exp_neg_kernel(int64_t n, const double *t, double *out, const __
         out[i] = exp_neg(t[i], T);
 }
 
+__global__ void add_pos_kernel(int64_t n, const double *x, const double *y, double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __longlong_as_double((long long)add_pos((unsigned long long)__double_as_longlong(x[i]),
+                                                         (unsigned long long)__double_as_longlong(y[i])));
+}
+
 int32_t sources_per_batch(const qc_ctx *ctx, int32_t n) {
     const int64_t cover = ((int64_t)n + 31) / 32 * 32;
     int64_t K;
@@ -527,15 +580,21 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
     return QC_OK;
 }
 
-extern "C" qc_status qc_selftest_exp_neg(qc_ctx *ctx, const double *t, double *out, int64_t n, void *stream_) {
-    if (!ctx || n < 0 || (n > 0 && (!t || !out))) return QC_ERR_INVALID_ARG;
+extern "C" qc_status qc_selftest_arith(qc_ctx *ctx, int32_t op, const double *x, const double *y, double *out,
+                                       int64_t n, void *stream_) {
+    if (!ctx || n < 0 || (op != QC_ARITH_EXP_NEG && op != QC_ARITH_ADD_POS)) return QC_ERR_INVALID_ARG;
+    if (n > 0 && (!x || !out || (op == QC_ARITH_ADD_POS && !y))) return QC_ERR_INVALID_ARG;
     if (n == 0) return QC_OK;
     cudaStream_t stream = qc_stream(stream_);
     QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    ExpTables etab;
-    fill_exp_tables(etab);
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * (int64_t)ctx->num_sms);
-    exp_neg_kernel<<<blocks, 256, 0, stream>>>(n, t, out, etab);
+    if (op == QC_ARITH_EXP_NEG) {
+        ExpTables etab;
+        fill_exp_tables(etab);
+        exp_neg_kernel<<<blocks, 256, 0, stream>>>(n, x, out, etab);
+    } else {
+        add_pos_kernel<<<blocks, 256, 0, stream>>>(n, x, y, out);
+    }
     QC_LAUNCHED(ctx);
     return QC_OK;
 }

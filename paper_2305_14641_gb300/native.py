@@ -108,8 +108,8 @@ SIGNATURES = [
     ("qc_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qc_server_stats)]),
     ("qc_server_destroy", None, [ctypes.c_void_p]),
     ("qc_selftest_barrier_timeout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
-    ("qc_selftest_exp_neg", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
-                                           ctypes.c_void_p]),
+    ("qc_selftest_arith", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     ("qc_histogram_static_scratch", ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                                    c_int32_p, ctypes.c_void_p]),
