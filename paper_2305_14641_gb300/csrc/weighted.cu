@@ -109,7 +109,7 @@ __device__ __forceinline__ unsigned long long add_pos(unsigned long long a, unsi
 }
 
 // Three blocks per SM (80 registers, a few spills) beat two blocks without
-// spills (104 registers): 68 against 82 ms for the DC-SBM of N = 16384.
+// spills (104 registers): 68 against 81-90 ms for the DC-SBM of N = 16384.
 __global__ void __launch_bounds__(256, 3) sssp_persistent(const SsspParams p) {
     const int lane = threadIdx.x & 31;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
