@@ -32,8 +32,8 @@
 // Potential: for node v, sum1 = sum_j d^2 e^{-d^2 / 2 sigma^2} and
 // sum2 = sum_j e^{...} over the j that v reaches (the self term adds 1 to
 // sum2), d = dist[v][j - s0] of each batch, with a table-driven exp (below,
-// fixed point but for its last multiply) of d^2 x 1 / (2 sigma^2) and
-// separately rounded binary64 multiplies and adds.  The sums run over each batch's
+// in integer arithmetic) of d^2 x 1 / (2 sigma^2), sum1 by fused multiply-adds
+// and sum2 by binary64 adds.  The sums run over each batch's
 // sources in a fixed pattern and over the batches in order, so the result is
 // the same on every run; it differs from the oracle's sequential sum over j
 // only by rounding (relative 1e-15 or so).
@@ -249,10 +249,11 @@ __global__ void __launch_bounds__(256, 3) sssp_persistent(const SsspParams p) {
 //   * exp(-r) = 1 - r (1 - r/2 (1 - r/3 (1 - r/4))) (truncation below 1e-17
 //     relative) in Q1.63 by Horner's rule with 64 x 64 -> high 64 products;
 //   * times exp(-b/1024), a Q1.63 table built on the host in extended
-//     precision; the product is rounded once to binary64 and scaled by 2^-63
-//     in its exponent field (exact);
-//   * times exp(-a), a binary64 table: one rounded multiply.
-// About 2 ulp in all.  Above t = 708 the result is subnormal, where the
+//     precision;
+//   * times exp(-a), a binary64 table: the 53 x 64-bit mantissa product is
+//     rounded once to nearest (ties to even) and given exp(-a)'s exponent,
+//     all in integer arithmetic.
+// About 1 ulp in all.  Above t = 708 the result is subnormal, where the
 // binary64 form below (same tables for exp(-a)) is kept; from 745 on it is 0.
 // The tables travel as a kernel parameter and each block copies them to shared
 // memory: lanes index them at random, which the constant bank would serialise.
@@ -306,8 +307,23 @@ __device__ __forceinline__ double exp_neg(double t, const ExpTables &T) {
     w = ONE - __umul64hi(rq, w);                                     // exp(-r)
     const unsigned long long L = T.fx[b];
     const unsigned long long M = (__umul64hi(L, w) << 1) | ((L * w) >> 63);   // Q1.63, in (0.36, 1]
-    const double Md = __longlong_as_double(__double_as_longlong(__ull2double_rn(M)) - (63ll << 52));
-    return __dmul_rn(T.hi[a], Md);
+    // exp(-a) M: the mantissa product (hi:lo, below 2^127) rounded once to 53 bits
+    constexpr unsigned long long MANT = (1ull << 52) - 1;
+    const unsigned long long hb = (unsigned long long)__double_as_longlong(T.hi[a]);   // normal for a <= 707
+    const unsigned long long Ha = ((hb & MANT) | (1ull << 52)) << 11;                 // in [2^63, 2^64)
+    const unsigned long long hi = __umul64hi(Ha, M);                                   // in (2^60.5, 2^63)
+    const unsigned long long lo = Ha * M;
+    const int top = 63 - __clzll((long long)hi);                                       // 60 .. 62
+    const int sr = top - 52;
+    unsigned long long mant = hi >> sr;
+    const unsigned long long rest = hi & ((1ull << sr) - 1), half = 1ull << (sr - 1);
+    if (rest > half || (rest == half && (lo != 0 || (mant & 1)))) ++mant;   // to nearest, ties to even
+    int eb = (int)(hb >> 52) + top - 62;
+    if (mant >> 53) {
+        mant >>= 1;
+        ++eb;
+    }
+    return __longlong_as_double((long long)(((unsigned long long)eb << 52) | (mant & MANT)));
 }
 
 // acc[s][v] += (sum1, sum2) over the batch's sources for node v: a warp per node,
@@ -316,7 +332,8 @@ __device__ __forceinline__ double exp_neg(double t, const ExpTables &T) {
 // the same total) and one add into the running sums, so the result is the same
 // on every run.
 constexpr int SGRP = 8;
-__global__ void wpot_accumulate(int32_t n, int32_t K, int32_t ns, const double *dist, int32_t S,
+// Three blocks per SM (80 registers) by a hair over two (92 registers).
+__global__ void __launch_bounds__(256, 3) wpot_accumulate(int32_t n, int32_t K, int32_t ns, const double *dist, int32_t S,
                                 const double *den, double2 *acc, const __grid_constant__ ExpTables Tp) {
     __shared__ ExpTables T;
     load_exp_tables(T, Tp);
@@ -341,7 +358,7 @@ __global__ void wpot_accumulate(int32_t n, int32_t K, int32_t ns, const double *
                 for (int j = 0; j < SGRP; ++j) {
                     if (s0 + j < S) {
                         const double e = exp_neg(__dmul_rn(d2, inv[j]), T);
-                        s1[j] = __dadd_rn(s1[j], __dmul_rn(d2, e));
+                        s1[j] = fma(d2, e, s1[j]);
                         s2[j] = __dadd_rn(s2[j], e);
                     }
                 }
