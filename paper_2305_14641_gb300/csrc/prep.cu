@@ -233,7 +233,9 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
     QC_TRY(bins.allocate(ctx, sizeof(int32_t) * 64, stream));
     const int tb = 256;
     const int nb = qc_ceil_div(n, tb) < 4 * ctx->num_sms ? qc_ceil_div(n, tb) : 4 * ctx->num_sms;
-    const int wb = qc_ceil_div(n, 8) < 8 * ctx->num_sms ? qc_ceil_div(n, 8) : 8 * ctx->num_sms;
+    // components: one thread per node is all the link phases use; more blocks only
+    // make each of the kernel's grid barriers dearer
+    const int wb = qc_ceil_div(n, 256) < 8 * ctx->num_sms ? qc_ceil_div(n, 256) : 8 * ctx->num_sms;
     const int32_t *rp = g->row_ptr.as<int32_t>();
     const int32_t *ci = g->col_idx.as<int32_t>();
     {
