@@ -341,15 +341,15 @@ void qc_server_destroy(qc_server *s);
  * to notice the missing block, QC_ERR_INVALID_ARG for a bad limit. */
 qc_status qc_selftest_barrier_timeout(qc_ctx *ctx, int64_t spin_limit, void *stream);
 
-/* ---- self-test of the weighted potential's arithmetic ----------------------------- */
+/* ---- self-test of the weighted path's arithmetic ---------------------------------- */
 
 /* The paper has no counterpart to this call.  The weighted path does its
  * binary64 work largely on the integer pipe (GB300 issues binary64 operations
- * at a small fraction of its integer rate), with two routines of its own; this
+ * at a small fraction of its integer rate), with routines of its own; this
  * call runs one of them elementwise on caller data so that it can be checked
  * against the hardware's or a reference's results:
- *   QC_ARITH_EXP_NEG  out[i] = exp(-x[i]) (Tang's table-driven method, mostly in
- *                     64-bit fixed point; about 2 ulp; 0 from x = 745 on);
+ *   QC_ARITH_EXP_NEG  out[i] = exp(-x[i]) (Tang's table-driven method in 64-bit
+ *                     fixed point; about 1 ulp; 0 from x = 745 on);
  *                     x[i] >= 0 and not NaN; y unused (may be null).
  *   QC_ARITH_ADD_POS  out[i] = x[i] + y[i] rounded to nearest even, as the
  *                     shortest-path relaxation computes it; x[i], y[i] >= 0

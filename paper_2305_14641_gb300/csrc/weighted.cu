@@ -42,6 +42,7 @@
 #include <cstdlib>
 #include <vector>
 
+#include "qc_binary64.cuh"
 #include "qc_device.cuh"
 #include "qc_internal.h"
 
@@ -68,45 +69,9 @@ struct SsspParams {
     int32_t *pass_new;             // [max_pass + 1] some value fell
 };
 
-// x + y for x, y >= 0 (x may be +inf), rounded to nearest even like the
-// hardware add, but on the integer pipe: GB300 issues binary64 adds at a small
-// fraction of its integer rate.  Mantissas carry three extra bits (guard,
-// round and a sticky bit that collects everything shifted out), the standard
-// construction for a correctly rounded sum; a zero or subnormal y and an
-// infinite x go to the hardware add.  Non-negative binary64 values order like
-// their bit patterns, so the relaxation compares them as integers.
-__device__ __forceinline__ unsigned long long add_pos(unsigned long long a, unsigned long long b) {
-    constexpr unsigned long long MANT = (1ull << 52) - 1, IMPL = 1ull << 52;
-    if (a < b) {
-        const unsigned long long t = a;
-        a = b;
-        b = t;
-    }
-    const int ea = (int)(a >> 52), eb = (int)(b >> 52);
-    if (ea == 2047 || eb == 0)
-        return (unsigned long long)__double_as_longlong(
-            __dadd_rn(__longlong_as_double((long long)a), __longlong_as_double((long long)b)));
-    const int d = ea - eb;
-    if (d >= 54) return a;                      // b is below half an ulp of a
-    const unsigned long long ma = ((a & MANT) | IMPL) << 3;
-    const unsigned long long mb0 = ((b & MANT) | IMPL) << 3;
-    const unsigned long long mb = (mb0 >> d) | (unsigned long long)((mb0 & ((1ull << d) - 1)) != 0);
-    unsigned long long s = ma + mb;             // below 2^57
-    int e = ea;
-    if (s >> 56) {
-        s = (s >> 1) | (s & 1ull);
-        ++e;
-    }
-    const unsigned low = (unsigned)(s & 7ull);
-    s >>= 3;
-    if (low > 4u || (low == 4u && (s & 1ull))) ++s;
-    if (s >> 53) {
-        s >>= 1;
-        ++e;
-    }
-    if (e >= 2047) return 0x7ff0000000000000ull;
-    return ((unsigned long long)e << 52) | (s & MANT);
-}
+// The relaxation adds and compares on the integer pipe (qc_binary64.cuh):
+// non-negative binary64 values order like their bit patterns.
+using qcfp::add_pos;
 
 // Three blocks per SM (80 registers, a few spills) beat two blocks without
 // spills (104 registers): 68 against 81-90 ms for the DC-SBM of N = 16384.
@@ -444,8 +409,7 @@ __global__ void exp_neg_kernel(int64_t n, const double *t, double *out, const __
 
 __global__ void add_pos_kernel(int64_t n, const double *x, const double *y, double *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = __longlong_as_double((long long)add_pos((unsigned long long)__double_as_longlong(x[i]),
-                                                         (unsigned long long)__double_as_longlong(y[i])));
+        out[i] = qcfp::as_double(qcfp::add_pos(qcfp::bits_of(x[i]), qcfp::bits_of(y[i])));
 }
 
 int32_t sources_per_batch(const qc_ctx *ctx, int32_t n) {
