@@ -341,23 +341,19 @@ void qc_server_destroy(qc_server *s);
  * to notice the missing block, QC_ERR_INVALID_ARG for a bad limit. */
 qc_status qc_selftest_barrier_timeout(qc_ctx *ctx, int64_t spin_limit, void *stream);
 
-/* ---- self-test of the weighted path's arithmetic ---------------------------------- */
+/* ---- self-test of the weighted path's exponential --------------------------------- */
 
-/* The paper has no counterpart to this call.  The weighted path does its
- * binary64 work largely on the integer pipe (GB300 issues binary64 operations
- * at a small fraction of its integer rate), with routines of its own; this
- * call runs one of them elementwise on caller data so that it can be checked
- * against the hardware's or a reference's results:
+/* The paper has no counterpart to this call.  The weighted potential evaluates
+ * exp(-t) for every pair and sigma with a routine of its own that runs on the
+ * integer pipe (GB300 issues binary64 operations at a small fraction of its
+ * integer rate); this call runs it elementwise on caller data so that it can be
+ * checked against a reference exp:
  *   QC_ARITH_EXP_NEG  out[i] = exp(-x[i]) (Tang's table-driven method in 64-bit
  *                     fixed point; about 1 ulp; 0 from x = 745 on);
  *                     x[i] >= 0 and not NaN; y unused (may be null).
- *   QC_ARITH_ADD_POS  out[i] = x[i] + y[i] rounded to nearest even, as the
- *                     shortest-path relaxation computes it; x[i], y[i] >= 0
- *                     (+inf allowed), not NaN.
- * x, y, out: device binary64[n], caller-owned, stream-ordered on `stream`.
- * QC_ERR_INVALID_ARG for an unknown op, n < 0, or a null pointer that op reads
- * or writes (n > 0). */
-enum { QC_ARITH_EXP_NEG = 0, QC_ARITH_ADD_POS = 1 };
+ * x, out: device binary64[n], caller-owned, stream-ordered on `stream`.
+ * QC_ERR_INVALID_ARG for another op, n < 0, or a null x or out with n > 0. */
+enum { QC_ARITH_EXP_NEG = 0 };
 qc_status qc_selftest_arith(qc_ctx *ctx, int32_t op, const double *x, const double *y, double *out, int64_t n,
                             void *stream);
 

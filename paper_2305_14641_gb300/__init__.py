@@ -107,11 +107,6 @@ class Context:
         float64 device tensor."""
         return self._selftest_arith(0, t, None, stream)
 
-    def selftest_add_pos(self, x, y, stream=None):
-        """x + y (float64, >= 0) by the shortest-path relaxation's own adder; returns a
-        float64 device tensor."""
-        return self._selftest_arith(1, x, y, stream)
-
     def bytes_in_use(self) -> int:
         return int(self._lib.qc_context_bytes_in_use(self.handle))
 

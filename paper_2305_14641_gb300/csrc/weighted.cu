@@ -42,7 +42,6 @@
 #include <cstdlib>
 #include <vector>
 
-#include "qc_binary64.cuh"
 #include "qc_device.cuh"
 #include "qc_internal.h"
 
@@ -69,9 +68,13 @@ struct SsspParams {
     int32_t *pass_new;             // [max_pass + 1] some value fell
 };
 
-// The relaxation adds and compares on the integer pipe (qc_binary64.cuh):
-// non-negative binary64 values order like their bit patterns.
-using qcfp::add_pos;
+// The relaxation compares on the integer pipe: non-negative binary64 values
+// order like their bit patterns, and a neighbour already at or above the best
+// length cannot improve it (w > 0), so most candidates cost an integer compare;
+// the rest take one binary64 add.  (An integer-pipe adder, bit-exact, made the
+// kernel ALU-bound: 72 against 52 ms for the DC-SBM of N = 16384.)
+__device__ __forceinline__ double as_double(unsigned long long b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ unsigned long long bits_of(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 // Three blocks per SM (80 registers, a few spills) beat two blocks without
 // spills (104 registers): 68 against 81-90 ms for the DC-SBM of N = 16384.
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(256, 3) sssp_persistent(const SsspParams p) {
 #pragma unroll
                             for (int q = 0; q < GU; ++q) {
                                 if (db[i][q] >= best[q]) continue;   // w > 0: no shorter path through u
-                                const unsigned long long c = add_pos(db[i][q], wb[i]);
+                                const unsigned long long c = bits_of(__dadd_rn(as_double(db[i][q]), as_double(wb[i])));
                                 if (c < best[q]) best[q] = c;
                             }
                     }
@@ -253,16 +256,10 @@ __device__ __forceinline__ void load_exp_tables(ExpTables &dst, const ExpTables 
     __syncthreads();
 }
 
-__device__ __forceinline__ double exp_neg(double t, const ExpTables &T) {
-    if (!(t < 708.0)) return exp_neg_f64(t, T);
+// exp(-t) from Tf = floor(t 2^53), t < 708.
+__device__ __forceinline__ double exp_neg_fixed(unsigned long long Tf, const ExpTables &T) {
     constexpr unsigned long long ONE = 1ull << 63;        // 1.0 in Q1.63
     constexpr unsigned long long THIRD = 0x5555555555555555ull;   // floor(2^64 / 3)
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(t);
-    const int e = (int)(bits >> 52);                      // t >= 0: no sign bit
-    const unsigned long long m = (bits & ((1ull << 52) - 1)) | (e ? (1ull << 52) : 0ull);
-    // T = floor(m 2^(e - 1022)) = floor(t 2^53); t < 2^10 keeps T below 2^63
-    const int sh = (e ? e : 1) - 1022;
-    const unsigned long long Tf = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ull);
     const int a = (int)(Tf >> 53);
     const int b = (int)((Tf >> 43) & 1023);
     const unsigned long long rq = (Tf & ((1ull << 43) - 1)) << 11;   // r 2^64, r < 2^-10
@@ -291,6 +288,35 @@ __device__ __forceinline__ double exp_neg(double t, const ExpTables &T) {
     return __longlong_as_double((long long)(((unsigned long long)eb << 52) | (mant & MANT)));
 }
 
+__device__ __forceinline__ double exp_neg(double t, const ExpTables &T) {
+    if (!(t < 708.0)) return exp_neg_f64(t, T);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(t);
+    const int e = (int)(bits >> 52);                      // t >= 0: no sign bit
+    const unsigned long long m = (bits & ((1ull << 52) - 1)) | (e ? (1ull << 52) : 0ull);
+    // Tf = floor(m 2^(e - 1022)) = floor(t 2^53); t < 2^10 keeps it below 2^63
+    const int sh = (e ? e : 1) - 1022;
+    return exp_neg_fixed(sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ull), T);
+}
+
+// exp(-d2 x inv) for d2 >= 0 and a normal inv > 0 given by its mantissa mi
+// (with the leading bit) and ri = 2097 - its exponent field: Tf comes straight
+// from the exact 106-bit product of the mantissas, with no binary64 multiply
+// (GB300's binary64 pipe is the pair sums' limit).  Products of t >= 2^9, and
+// d2 zero or subnormal, take the binary64 route.
+__device__ __forceinline__ double exp_neg_product(unsigned long long d2b, unsigned long long mi, int ri,
+                                                  double inv, const ExpTables &T) {
+    if (d2b == 0) return 1.0;
+    const int ed = (int)(d2b >> 52);
+    const int r = ri - ed;                                // Tf = (md mi) >> r
+    if (ed == 0 || r < 44) return exp_neg(__dmul_rn(__longlong_as_double((long long)d2b), inv), T);
+    if (r >= 128) return 1.0;                             // Tf = 0: t < 2^-53
+    const unsigned long long md = (d2b & ((1ull << 52) - 1)) | (1ull << 52);
+    const unsigned long long hi = __umul64hi(md, mi), lo = md * mi;
+    const unsigned long long Tf = r >= 64 ? (hi >> (r - 64)) : ((hi << (64 - r)) | (lo >> r));
+    if (Tf >= (708ull << 53)) return exp_neg(__dmul_rn(__longlong_as_double((long long)d2b), inv), T);
+    return exp_neg_fixed(Tf, T);
+}
+
 // acc[s][v] += (sum1, sum2) over the batch's sources for node v: a warp per node,
 // lane l takes sources l, l + 32, ... in order (each distance read once for up
 // to SGRP sigma values), then a butterfly over the lanes (every lane ends with
@@ -309,9 +335,14 @@ __global__ void __launch_bounds__(256, 3) wpot_accumulate(int32_t n, int32_t K, 
         const double *row = dist + (size_t)v * K;
         for (int s0 = 0; s0 < S; s0 += SGRP) {
             double inv[SGRP], s1[SGRP], s2[SGRP];
+            unsigned long long im[SGRP];
+            int ir[SGRP];
 #pragma unroll
             for (int j = 0; j < SGRP; ++j) {
-                inv[j] = (s0 + j < S) ? 1.0 / den[s0 + j] : 0.0;   // one division per node and sigma
+                inv[j] = (s0 + j < S) ? 1.0 / den[s0 + j] : 1.0;   // one division per node and sigma
+                const unsigned long long ib = (unsigned long long)__double_as_longlong(inv[j]);
+                im[j] = (ib & ((1ull << 52) - 1)) | (1ull << 52);
+                ir[j] = 2097 - (int)(ib >> 52);
                 s1[j] = 0.0;
                 s2[j] = 0.0;
             }
@@ -319,10 +350,11 @@ __global__ void __launch_bounds__(256, 3) wpot_accumulate(int32_t n, int32_t K, 
                 const double d = row[k];
                 if (!(d < 1e308)) continue;                        // unreachable (+inf)
                 const double d2 = __dmul_rn(d, d);
+                const unsigned long long d2b = (unsigned long long)__double_as_longlong(d2);
 #pragma unroll
                 for (int j = 0; j < SGRP; ++j) {
                     if (s0 + j < S) {
-                        const double e = exp_neg(__dmul_rn(d2, inv[j]), T);
+                        const double e = exp_neg_product(d2b, im[j], ir[j], inv[j], T);
                         s1[j] = fma(d2, e, s1[j]);
                         s2[j] = __dadd_rn(s2[j], e);
                     }
@@ -405,11 +437,6 @@ __global__ void exp_neg_kernel(int64_t n, const double *t, double *out, const __
     load_exp_tables(T, Tp);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = exp_neg(t[i], T);
-}
-
-__global__ void add_pos_kernel(int64_t n, const double *x, const double *y, double *out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = qcfp::as_double(qcfp::add_pos(qcfp::bits_of(x[i]), qcfp::bits_of(y[i])));
 }
 
 int32_t sources_per_batch(const qc_ctx *ctx, int32_t n) {
@@ -563,19 +590,16 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
 
 extern "C" qc_status qc_selftest_arith(qc_ctx *ctx, int32_t op, const double *x, const double *y, double *out,
                                        int64_t n, void *stream_) {
-    if (!ctx || n < 0 || (op != QC_ARITH_EXP_NEG && op != QC_ARITH_ADD_POS)) return QC_ERR_INVALID_ARG;
-    if (n > 0 && (!x || !out || (op == QC_ARITH_ADD_POS && !y))) return QC_ERR_INVALID_ARG;
+    (void)y;
+    if (!ctx || n < 0 || op != QC_ARITH_EXP_NEG) return QC_ERR_INVALID_ARG;
+    if (n > 0 && (!x || !out)) return QC_ERR_INVALID_ARG;
     if (n == 0) return QC_OK;
     cudaStream_t stream = qc_stream(stream_);
     QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * (int64_t)ctx->num_sms);
-    if (op == QC_ARITH_EXP_NEG) {
-        ExpTables etab;
-        fill_exp_tables(etab);
-        exp_neg_kernel<<<blocks, 256, 0, stream>>>(n, x, out, etab);
-    } else {
-        add_pos_kernel<<<blocks, 256, 0, stream>>>(n, x, y, out);
-    }
+    ExpTables etab;
+    fill_exp_tables(etab);
+    exp_neg_kernel<<<blocks, 256, 0, stream>>>(n, x, out, etab);
     QC_LAUNCHED(ctx);
     return QC_OK;
 }

@@ -444,33 +444,6 @@ def test_exp_neg_accuracy(qc, ctx):
     assert np.all(np.abs(got[pick] - exact)[keep] <= 3 * np.spacing(exact[keep]))
 
 
-def test_add_pos_bit_exact(qc, ctx):
-    """The relaxation's integer-pipe binary64 adder equals IEEE round-to-nearest-even
-    addition bit for bit: random magnitudes, equal and distant exponents, carries,
-    exact ties (odd and even), subnormals, zeros and infinities."""
-    g = gg.rng(42)
-    n = 1 << 20
-    x = np.exp(g.uniform(-40, 40, n))
-    y = x * np.exp(g.uniform(-45, 45, n))            # exponent gaps up to ~65 binades
-    near = x * (1.0 + g.integers(-8, 8, n) * 2.0 ** -52)
-    ones = np.ones(n)
-    # ties: y is exactly half an ulp of x (or 1.5 ulp), with x's last bit odd or even
-    tie_x = np.nextafter(ones, 2.0) * 2.0 ** g.integers(-30, 30, n).astype(np.float64)
-    tie_x[::2] = 2.0 ** g.integers(-30, 30, n // 2).astype(np.float64)
-    tie_y = np.spacing(tie_x) * np.where(g.random(n) < 0.5, 0.5, 1.5)
-    special_x = np.array([0.0, 0.0, 5e-324, 1e-310, 2.2250738585072014e-308, 1.0, 1.0, np.inf, np.inf, 1e308, 1.7e308,
-                          3.0, 2.0 ** 53, 2.0 ** 53])
-    special_y = np.array([0.0, 1.0, 5e-324, 1e-310, 2.2250738585072014e-308, 0.0, np.inf, 1.0, np.inf, 1e308, 1.7e308,
-                          2.0 ** -52, 1.0, 3.0])
-    xs = np.concatenate([x, y, near, tie_x, tie_y, special_x])
-    ys = np.concatenate([y, x, x, tie_y, tie_x, special_y])
-    got = ctx.selftest_add_pos(xs, ys).cpu().numpy()
-    with np.errstate(over="ignore"):
-        want = xs + ys                                # 1e308 + 1e308 overflows to inf on purpose
-    bad = got.view(np.uint64) != want.view(np.uint64)
-    assert not bad.any(), (int(bad.sum()), xs[bad][:3], ys[bad][:3], got[bad][:3], want[bad][:3])
-
-
 def test_weighted_invalid(qc, ctx):
     graph = gg.erdos_renyi(200, 0.05, gg.rng(39))
     G = qc.Graph.from_graph(ctx, graph)
