@@ -627,8 +627,8 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
     // d^2 of its n nodes in two hops, so the variant with masks is taken when
     // d^2 * mask_ratio < n (a level then reads masked segments while the previous
     // level found fewer than 64 wn n / mask_ratio new bits).  Measured on GB300:
-    // SBM of mean degree 20 with n = 2^16 and 2^18, 4.5 % and 9 % faster; a
-    // DC-SBM of n = 2^14 and mean degree 16, 10 % slower (only its level 2 is sparse).
+    // SBM of mean degree 20 with n = 2^16 and 2^18, 7 % and 11 % faster; a
+    // DC-SBM of n = 2^14 and mean degree 16, 5 % slower (only its level 2 is sparse).
     // QCGRAPH_MASK_RATIO overrides the ratio (0: never).
     int32_t mask_ratio = 128;
     if (const char *env = getenv("QCGRAPH_MASK_RATIO")) mask_ratio = std::max(0, atoi(env));
