@@ -372,12 +372,16 @@ qc_status qc_selftest_arith(qc_ctx *ctx, int32_t op, const double *x, const doub
  * device int32[max_levels * n], level-major; every row is written (rows past D
  * are zero).  D_out: host, receives D (-1 on failure).  Synchronises `stream`.
  *
+ * max_levels: rows of hist_out; D + 1 rows suffice (D the largest finite
+ * distance), so a graph with a path of n nodes needs at most n rows.
+ *
  * Set-up: the first call on a device (with that device current) looks up the
  * array's device address; make that first call outside any stream capture.
+ * `stream` must belong to the current device.
  * All calls share the one array: calls that overlap on the GPU (other streams
  * or threads) race and give wrong results.
  * Errors: QC_ERR_INVALID_ARG (n < 1 or n > 262144, max_levels < 2 or fewer
- * rows than D + 1 needs, null pointers), QC_ERR_CUDA. */
+ * than D + 1, null pointers, a stream of another device), QC_ERR_CUDA. */
 qc_status qc_histogram_static_scratch(int32_t n, int64_t nnz, const int32_t *row_ptr,
                                       const int32_t *col_idx, int32_t *hist_out,
                                       int32_t max_levels, int32_t *D_out, void *stream);

@@ -64,6 +64,8 @@ __global__ void sa_init(int32_t n, const int32_t *row_ptr, const int32_t *col_id
 }
 
 // next = (OR of neighbours' rows) & ~own; out = own | next; hist[level][v] += popc(next).
+// hist_row may be null: the pass then only reports (in *flag) whether anything
+// is new, for the level just past the caller's last histogram row.
 __global__ void sa_level(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                          const ulonglong2 *vin, ulonglong2 *vout, int32_t R, int32_t *hist_row,
                          int32_t *flag) {
@@ -95,7 +97,7 @@ __global__ void sa_level(int32_t n, const int32_t *row_ptr, const int32_t *col_i
         }
         count = __reduce_add_sync(FULL, count);
         if (lane == 0 && count) {
-            hist_row[v] += count;
+            if (hist_row) hist_row[v] += count;
             any_new = true;
         }
     }
@@ -132,6 +134,12 @@ extern "C" qc_status qc_histogram_static_scratch(int32_t n, int64_t nnz, const i
         return QC_ERR_INVALID_ARG;
     *D_out = -1;
     cudaStream_t stream = qc_stream(stream_);
+    // the array's address is looked up on the current device, so the stream must
+    // belong to that device too
+    int dev = 0, stream_dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaStreamGetDevice(stream, &stream_dev) != cudaSuccess)
+        return QC_ERR_CUDA;
+    if (stream_dev != dev) return QC_ERR_INVALID_ARG;
     void *base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return QC_ERR_CUDA;
 
@@ -164,17 +172,21 @@ extern "C" qc_status qc_histogram_static_scratch(int32_t n, int64_t nnz, const i
         if (cudaGetLastError() != cudaSuccess) return QC_ERR_CUDA;
         ulonglong2 *in = visA, *out = visB;
         for (int32_t level = 2;; ++level) {
-            if (level >= max_levels) return QC_ERR_INVALID_ARG;   // hist_out too short
+            // The BFS ends with a pass that finds nothing new, one level past D.
+            // When that level has no row in hist_out (D = max_levels - 1), the pass
+            // runs without a row: if it does find new sources, hist_out is too short.
+            const bool past_rows = level >= max_levels;
             if (cudaMemsetAsync(flag, 0, sizeof(int32_t), stream) != cudaSuccess) return QC_ERR_CUDA;
             const int blocks = qc_ceil_div(n, 8) < 4096 ? qc_ceil_div(n, 8) : 4096;
             sa_level<<<blocks, 256, 0, stream>>>(n, row_ptr, col_idx, in, out, R,
-                                                 hist_out + (size_t)level * n, flag);
+                                                 past_rows ? nullptr : hist_out + (size_t)level * n, flag);
             if (cudaGetLastError() != cudaSuccess) return QC_ERR_CUDA;
             int32_t h_flag = 0;
             if (cudaMemcpyAsync(&h_flag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
                 cudaStreamSynchronize(stream) != cudaSuccess)
                 return QC_ERR_CUDA;
             if (!h_flag) break;
+            if (past_rows) return QC_ERR_INVALID_ARG;   // a distance of max_levels or more
             if (level > D) D = level;
             ulonglong2 *t = in;
             in = out;

@@ -4,9 +4,9 @@ plugin limited to the buffers it is handed).  Its bitsets live in a fixed array
 inside the library, so the call itself allocates nothing.
 
 Checked through the C ABI against the regular entry point (qc_graph_histogram)
-on the same inputs, twice in a row, so that the second call also shows that
-what the first left in the shared array does not leak into the result.  This
-file is collected last on purpose.
+and against the oracle's histograms on the same inputs, twice in a row, so that
+the second call also shows that what the first left in the shared array does
+not leak into the result.  This file is collected last on purpose.
 """
 import ctypes
 
@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -60,13 +61,33 @@ def test_matches_regular_entry_point_twice(env, name, make):
     g = qc.Graph.from_graph(ctx, graph)
     ref = g.histogram()
     g.close()
-    max_levels = ref.shape[0] + 3
-    for call in range(2):
-        st, D, out, _ = static_histogram(lib, graph, max_levels)
-        assert st == 0, (name, call, st)
-        assert D == ref.shape[0] - 1, (name, call)
-        assert torch.equal(out[:D + 1], ref), (name, call)
-        assert int(out[D + 1:].abs().sum()) == 0, (name, call)
+    expect = oracle.histograms(graph).T          # level-major [(D+1), n]
+    assert np.array_equal(ref.cpu().numpy(), expect), name
+    for max_levels in (ref.shape[0] + 3, ref.shape[0]):
+        for call in range(2):
+            st, D, out, _ = static_histogram(lib, graph, max_levels)
+            assert st == 0, (name, max_levels, call, st)
+            assert D == ref.shape[0] - 1, (name, call)
+            assert torch.equal(out[:D + 1], ref), (name, call)
+            assert np.array_equal(out[:D + 1].cpu().numpy(), expect), (name, call)
+            assert int(out[D + 1:].abs().sum()) == 0, (name, call)
+
+
+@pytest.mark.parametrize("graph,rows", [(gg.complete(40), 2), (gg.path(50), 50), (gg.path(2), 2),
+                                        (gg.star(300, 7), 3)], ids=["K40", "P50", "P2", "S300"])
+def test_exactly_d_plus_one_rows(env, graph, rows):
+    """D + 1 rows are enough (the pass that finds nothing runs without a row);
+    D rows are too few and the call says so."""
+    qc, lib, ctx = env
+    expect = oracle.histograms(graph).T
+    assert expect.shape[0] == rows
+    for _ in range(2):
+        st, D, out, _ = static_histogram(lib, graph, rows)
+        assert st == 0 and D == rows - 1, (graph.name, st, D)
+        assert np.array_equal(out.cpu().numpy(), expect), graph.name
+    if rows > 2:
+        st, D, _, _ = static_histogram(lib, graph, rows - 1)
+        assert st == 1 and D == -1, graph.name
 
 
 def test_back_to_back_different_graphs(env):
@@ -74,6 +95,7 @@ def test_back_to_back_different_graphs(env):
     qc, lib, ctx = env
     big = gg.planted_partition(6000, 12, 0.01, 0.0005, gg.rng(33))
     small = gg.erdos_renyi(300, 0.02, gg.rng(34))
+    expect = {id(big): oracle.histograms(big).T, id(small): oracle.histograms(small).T}
     for graph in (big, small, big):
         g = qc.Graph.from_graph(ctx, graph)
         ref = g.histogram()
@@ -81,6 +103,7 @@ def test_back_to_back_different_graphs(env):
         st, D, out, _ = static_histogram(lib, graph, ref.shape[0] + 1)
         assert st == 0 and D == ref.shape[0] - 1
         assert torch.equal(out[:D + 1], ref)
+        assert np.array_equal(out[:D + 1].cpu().numpy(), expect[id(graph)])
 
 
 def test_allocates_nothing_and_rejects_out_of_range(env):
@@ -92,6 +115,16 @@ def test_allocates_nothing_and_rejects_out_of_range(env):
     # too few histogram rows for the graph's largest distance
     st, D, _, _ = static_histogram(lib, gg.path(50), 10)
     assert st == 1 and D == -1
+    # a stream of the current device is accepted (the legacy default stream too)
+    rp = torch.tensor(graph.row_ptr, device="cuda")
+    ci = torch.tensor(graph.col_idx, device="cuda")
+    out = torch.zeros((64, graph.n), dtype=torch.int32, device="cuda")
+    Dc = ctypes.c_int32(-5)
+    side = torch.cuda.Stream()
+    for handle in (0, side.cuda_stream):
+        torch.cuda.synchronize()
+        assert lib.qc_histogram_static_scratch(graph.n, graph.nnz, rp.data_ptr(), ci.data_ptr(), out.data_ptr(),
+                                               64, ctypes.byref(Dc), handle) == 0
     # more nodes than the fixed array supports
     big = gg.Graph(262145, np.zeros(262146, dtype=np.int32), np.zeros(0, dtype=np.int32))
     st, D, _, _ = static_histogram(lib, big, 2)
