@@ -29,7 +29,7 @@ __all__ = [
     "Graph", "rng", "csr_from_pairs", "block_sizes", "planted_partition",
     "sbm_mean_degree", "dcsbm", "complete", "path", "star", "two_cliques_bridge",
     "erdos_renyi", "relabel", "planted128", "dcsbm16384", "sbm262144", "planted_batch",
-    "sbm_request_stream", "sigma_sweep16", "Request", "csr_from_arcs", "directed_cycle",
+    "sbm_request_stream", "sigma_sweep16", "planted_batch_graph", "Request", "csr_from_arcs", "directed_cycle",
     "directed_path", "directed_erdos_renyi", "directed_planted_partition", "edge_weights",
 ]
 
@@ -368,19 +368,25 @@ def sbm262144(n: int = 262144, k: int = 256) -> tuple[Graph, list[float]]:
     return planted_partition(n, k, p_in, p_out, rng(2, 3), name=f"sbm-{n}"), [1.5]
 
 
+def planted_batch_graph(gi: int, seed: int = 3, n_min: int = 32, n_max: int = 2048) -> tuple[Graph, float]:
+    """Graph gi of the planted-partition batch and its sigma, from stream (seed, 4, gi)."""
+    g = rng(seed, 4, gi)
+    n = int(math.floor(math.exp(g.uniform(math.log(n_min), math.log(n_max)))))
+    k = int(g.integers(2, 17))
+    k = min(k, n)
+    p_in = float(g.uniform(0.1, 0.5))
+    sigma = float(g.uniform(0.5, 3.0))
+    return planted_partition(n, k, p_in, 0.02, g, name=f"batch-{gi}"), sigma
+
+
 def planted_batch(count: int = 4096, seed: int = 3, n_min: int = 32, n_max: int = 2048,
                   ) -> tuple[list[Graph], list[float]]:
     """Batch of planted-partition graphs: N = floor(exp(U(ln n_min, ln n_max))), k ~ U{2..16},
-    p_in ~ U(0.1, 0.5), p_out = 0.02, sigma ~ U(0.5, 3.0); graph g draws from stream (seed, g)."""
+    p_in ~ U(0.1, 0.5), p_out = 0.02, sigma ~ U(0.5, 3.0); graph g draws from stream (seed, 4, g)."""
     graphs, sigmas = [], []
     for gi in range(count):
-        g = rng(seed, 4, gi)
-        n = int(math.floor(math.exp(g.uniform(math.log(n_min), math.log(n_max)))))
-        k = int(g.integers(2, 17))
-        k = min(k, n)
-        p_in = float(g.uniform(0.1, 0.5))
-        sigma = float(g.uniform(0.5, 3.0))
-        graphs.append(planted_partition(n, k, p_in, 0.02, g, name=f"batch-{gi}"))
+        graph, sigma = planted_batch_graph(gi, seed, n_min, n_max)
+        graphs.append(graph)
         sigmas.append(sigma)
     return graphs, sigmas
 

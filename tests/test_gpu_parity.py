@@ -140,47 +140,47 @@ def test_dcsbm16384_full(qc, ctx):
     assert_solution_matches(qc, ctx, graph, sigmas)
 
 
-def test_sbm262144_full_size_sampled(qc, ctx):
-    """SBM N=262144 (5.24M directed edges) at full size.  The oracle's per-source
-    BFS is too slow for every node, so: histogram rows of sampled nodes (random,
-    first, last, extreme degrees) bit-exact against the oracle; invariants at every
-    node (h(0) = 1, h(1) = degree, row sum = component size); potentials of every
-    node against the oracle's potential of the GPU histogram, and of the sampled
-    nodes against the oracle's own histograms; labels bit-exact against the
-    oracle's descent and roots run on those potentials."""
-    from scipy.sparse import csr_matrix
-    from scipy.sparse.csgraph import connected_components
+def full_size_golden(name):
+    """The oracle's stored results for a full-size workload (tests/golden/full_size.json,
+    written by tests/golden/make_full_size.py from oracle/ alone)."""
+    import json
+    path = os.path.join(os.path.dirname(__file__), "golden", "full_size.json")
+    data = json.load(open(path))
+    assert name in data, f"{name} missing from {path}: run tests/golden/make_full_size.py"
+    return data[name]
+
+
+def sha256(a):
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def test_sbm262144_full_size(qc, ctx):
+    """SBM N=262144 (5.24M directed edges), sigma 1.5, at full size: the whole
+    histogram (every node, every distance), every potential and every label equal
+    the oracle's, stored as SHA-256 digests of the oracle's arrays.  Should they
+    differ, sampled rows are compared with the oracle directly to say where."""
     graph, sigmas = gg.sbm262144()
-    n = graph.n
+    gold = full_size_golden("sbm262144")
+    csr = np.concatenate([graph.row_ptr.astype("<i4"), graph.col_idx.astype("<i4")])
+    assert sha256(csr) == gold["csr_sha256"], "input graph differs from the one the oracle ran on"
     g = qc.Graph.from_graph(ctx, graph)
     hist = g.histogram().cpu().numpy()
-    D = hist.shape[0] - 1
-    deg = np.diff(graph.row_ptr)
-    assert np.all(hist[0] == 1) and np.array_equal(hist[1], deg)
-    a = csr_matrix((np.ones(graph.nnz), graph.col_idx, graph.row_ptr), shape=(n, n))
-    _, comp = connected_components(a, directed=False)
-    assert np.array_equal(hist.sum(axis=0, dtype=np.int64), np.bincount(comp)[comp])
-    rs = gg.rng(30)
-    nodes = np.unique(np.concatenate([rs.choice(n, 60, replace=False),
-                                      [0, n - 1, int(np.argmax(deg)), int(np.argmin(deg))]])).astype(np.int32)
-    ref_h = oracle.histograms(graph, nodes, threads=oracle.default_threads(), cap=D + 1)
-    cols = ref_h.shape[1]
-    assert cols <= D + 1
-    assert np.array_equal(hist[:cols, nodes].T, ref_h)
-    assert not hist[cols:, nodes].any()
     V = g.potential(sigmas)
-    Vh = V.cpu().numpy()
-    for k, s in enumerate(sigmas):
-        assert np.array_equal(Vh[k], oracle.potential(np.ascontiguousarray(hist.T), s))
-        assert np.array_equal(Vh[k, nodes], oracle.potential(ref_h, s))
     labels, counts = g.ggd_labels(V)
-    labels = labels.cpu().numpy()
-    for k in range(len(sigmas)):
-        p, _ = oracle.ggd_parent(graph, Vh[k])
-        lab, roots = oracle.find_centers(p)
-        assert np.array_equal(labels[k], lab)
-        assert counts[k] == roots
+    Vh, lab = V.cpu().numpy(), labels.cpu().numpy()
     g.close()
+    ok = (hist.shape[0] - 1 == gold["D"] and sha256(hist.astype("<i4")) == gold["hist_sha256"])
+    if not ok:
+        rs = gg.rng(30)
+        nodes = np.unique(np.concatenate([rs.choice(graph.n, 60, replace=False), [0, graph.n - 1]])).astype(np.int32)
+        ref_h = oracle.histograms(graph, nodes, threads=oracle.default_threads(), cap=hist.shape[0] + 1)
+        bad = [int(v) for k, v in enumerate(nodes) if not np.array_equal(hist[:ref_h.shape[1], v], ref_h[k])]
+        raise AssertionError(f"histogram differs from the oracle's (D {hist.shape[0] - 1} vs {gold['D']}); "
+                             f"sampled nodes that differ: {bad[:10]}")
+    assert sha256(Vh[0].astype("<f8")) == gold["V_sha256"], "potential not bit-identical to the oracle's"
+    assert sha256(lab[0].astype("<i4")) == gold["labels_sha256"], "labels differ from the oracle's"
+    assert counts[0] == gold["n_clusters"]
 
 
 def test_sigma_reuse_and_edge_values(qc, ctx):
