@@ -18,7 +18,11 @@ partitions).
 Prints one JSON line.  `value` is clusterings/s (one clustering = one label
 vector for one (graph, sigma) pair) over all ranks, timed on the device with
 CUDA events, inputs resident in HBM, L2 flushed (256 MiB write) before every
-timed step.  `e2e` is the same metric through the public API with host
+timed step.  On one GPU the default line also carries the rest of the headline
+metric: `batch4096` (the batched plan against the plain one-graph-at-a-time
+form, labels compared) and `serve` (p50/p99 latency of the Poisson request
+stream, throughput against serial plain solves, labels compared); --no-extra
+leaves them out.  `e2e` is the same metric through the public API with host
 buffers: pinned host CSR -> device, solve, labels back to pinned host memory.
 `--impl reference` times the CPU oracle (test infrastructure, plain C) on the
 same workload instead.  With --gpus N > 1 each rank runs an independent replica
@@ -285,20 +289,24 @@ def bench_ours(args, graph, sigmas, spec):
     labels = torch.empty((S, n), dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def step():
+    def solve_step():
         g.drop_histogram()
         g.solve(sigmas, V_out=V, labels_out=labels, counts=False)
+
+    plan = None
+    if args.step == "plan":
+        # the whole step (BFS from the resident CSR, 16 potentials, descent, roots)
+        # captured once into CUDA graphs and replayed
+        plan = qc.SweepPlan(g, sigmas, V=V, labels=labels)
+        step = plan.run
+    else:
+        step = solve_step
 
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
 
     # timed region: K steps, each bracketed by events after an L2 flush
-    ctx.set_timing(True)
-    ctx.kernel_stats("bfs_level", reset=True)
-    for lvl in range(n + 2):
-        if ctx.kernel_stats(f"bfs_pass_{lvl}", reset=True)["launches"] == 0 and lvl > 2:
-            break
     launches0 = ctx.launch_count()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -315,7 +323,19 @@ def bench_ours(args, graph, sigmas, spec):
     if world > 1:
         torch.distributed.barrier()
     launches = ctx.launch_count() - launches0
+    # the BFS kernel's own figures: the same steps through the single-graph path in
+    # timing mode (CUDA events around each BFS launch, device timestamps per level)
+    ctx.set_timing(True)
+    ctx.kernel_stats("bfs_level", reset=True)
+    for lvl in range(n + 2):
+        if ctx.kernel_stats(f"bfs_pass_{lvl}", reset=True)["launches"] == 0 and lvl > 2:
+            break
+    for k in range(min(args.steps, 20)):
+        flush.fill_(k & 0xff)
+        solve_step()
+    torch.cuda.synchronize()
     kstats = ctx.kernel_stats("bfs_level", reset=True)
+    kstats_steps = min(args.steps, 20)
     # per-level device time inside the BFS launch (globaltimer stamps at each grid barrier);
     # level 1 is the set-up that writes the rows of levels 0-1
     level_us = {}
@@ -325,10 +345,14 @@ def bench_ours(args, graph, sigmas, spec):
             break
         level_us[lvl] = round(1000.0 * st["total_ms"] / st["launches"], 2)
     ctx.set_timing(False)
+    ctx_l2 = {"stream": ctx.l2_read_gbs(48 << 20), "random512": ctx.l2_read_gbs(48 << 20, random_segments=True)}
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = max_over_ranks(float(sum(step_ms)), dev)
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(S, args.steps, world, total_ms)
+    plan_info = plan.info() if plan is not None else None
+    if plan is not None:
+        plan.close()
 
     # end to end through the public API with host buffers
     rp_h = torch.from_numpy(graph.row_ptr).pin_memory()
@@ -362,11 +386,17 @@ def bench_ours(args, graph, sigmas, spec):
 
     if rank == 0:
         peak, peak_kind = measured_peak_gbs()
-        achieved = (kstats["model_bytes"] / (kstats["total_ms"] / 1000.0) / 1e9
-                    if kstats["total_ms"] > 0 else None)
+        avg_ms = kstats["total_ms"] / kstats["launches"] if kstats["launches"] else None
+        min_per_launch = kstats["min_bytes"] / kstats["launches"] if kstats["launches"] else None
+        achieved = (min_per_launch / (avg_ms / 1000.0) / 1e9) if avg_ms else None
         traffic = profile_traffic(spec["profile"])
+        l2_read = profile_value("l2_read_bytes_per_launch", spec["profile"])
+        # L2 read throughput measured live by the library's probe (48 MiB buffer, resident in L2)
+        l2_peak = ctx_l2["stream"]
+        l2_peak_random = ctx_l2["random512"]
+        l2_achieved = (l2_read / (avg_ms / 1000.0) / 1e9) if (l2_read and avg_ms) else None
         edges = gteps_edges(graph)
-        bfs_ms = kstats["total_ms"] / args.steps
+        bfs_ms = kstats["total_ms"] / kstats_steps
         cpu = None
         if not args.no_cpu_baseline:
             import oracle
@@ -384,29 +414,39 @@ def bench_ours(args, graph, sigmas, spec):
             "config": {"workload": spec["desc"], "n": n, "nnz": graph.nnz, "sigmas": S,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "256 MiB buffer written between timed steps",
-                       "allocator": "stream-ordered CUDA pool (cudaMallocAsync)"},
+                       "allocator": "stream-ordered CUDA pool (cudaMallocAsync)",
+                       "step": ("sweep plan: BFS, potentials, descent and roots captured in CUDA graphs, "
+                                "replayed from the resident CSR" if plan_info else
+                                "single-graph path (qc_solve) after dropping the cached histogram"),
+                       "captured": plan_info["captured"] if plan_info else None},
             "gteps": edges * world * args.steps / (total_ms / 1000.0) / 1e9,
             "bfs_gteps": (edges / (bfs_ms / 1000.0) / 1e9) if bfs_ms > 0 else None,
             "roofline": {"kernel": "bfs_persistent", "bound": "hbm", "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
                          "traffic": traffic,
-                         # the level at which the kernel actually works: bytes it reads from L2
-                         # per launch and L2 throughput as a share of its peak, from the same
-                         # ncu capture as `traffic`
-                         "l2_read_bytes": profile_value("l2_read_bytes_per_launch", spec["profile"]),
-                         "l2_throughput_frac": profile_value("l2_throughput_frac", spec["profile"]),
+                         "bytes_per_launch": min_per_launch,
+                         "bytes_model": "compulsory HBM bytes per launch (a lower bound): CSR, node order, row "
+                                        "bounds, components and per-word masks read once, histogram rows written "
+                                        "once, and per level the open (node, tile) rows read and written beyond "
+                                        "what L2 holds (counted on the device); the bitset buffers of this "
+                                        "workload fit in L2, so they add nothing",
                          "model_bytes_per_launch": (kstats["model_bytes"] / kstats["launches"]
                                                     if kstats["launches"] else None),
-                         "launches": kstats["launches"],
-                         "bytes_model": f"pull-all: per level and chunk of source words, 8*wn*(E+3N) "
-                                        f"bitset bytes + CSR + one histogram row (W = {(n + 63) // 64} "
-                                        f"words in chunks of at most 256, the two bitset buffers near "
-                                        f"four times L2); saturated rows are skipped and a row gathered "
-                                        f"for several neighbours is mostly read from L2, so the DRAM "
-                                        f"traffic is far below the model",
-                         "avg_launch_ms": (kstats["total_ms"] / kstats["launches"]
-                                           if kstats["launches"] else None)},
+                         "model": "pull-all upper bound: per level 8*wn*(E+3N) bitset bytes + CSR + one "
+                                  "histogram row",
+                         "launches": kstats["launches"], "avg_launch_ms": avg_ms,
+                         # where the kernel works: bytes it reads from L2 per launch (ncu, same capture as
+                         # `traffic`) over its launch time, against an L2-resident copy measured live
+                         "l2": {"achieved": l2_achieved, "peak": l2_peak, "unit": "GB/s",
+                                "frac": (l2_achieved / l2_peak) if l2_achieved else None,
+                                "peak_random512": l2_peak_random,
+                                "frac_random512": (l2_achieved / l2_peak_random) if l2_achieved else None,
+                                "read_bytes_per_launch": l2_read,
+                                "ncu_l2_throughput_frac": profile_value("l2_throughput_frac", spec["profile"]),
+                                "peak_kind": "measured live: a 48 MiB buffer read through L2 only, streamed "
+                                             "(peak) and as random 512-byte segments one per warp "
+                                             "(peak_random512, the gather pattern)"}},
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
             "bfs_level_us": level_us,
@@ -414,9 +454,14 @@ def bench_ours(args, graph, sigmas, spec):
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
     g.close()
     ctx.close()
+    if rank == 0:
+        if world == 1 and not args.no_extra:
+            # the rest of the headline metric: batched vs plain, and the served form's latency
+            line["batch4096"] = batch_summary(args)
+            line["serve"] = serve_summary(args)
+        print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -428,8 +473,9 @@ SERVE_WORKLOAD = ("serve: Poisson arrivals at 200 requests/s of SBM graphs, N lo
                   "mean degree 12, 4-64 blocks, mixing 0.1, sigma U(0.5, 3.0), seed 4, 100 GB admission budget")
 
 
-def bench_batch(args):
-    """Batched plan vs the plain form (one graph at a time through qc_solve)."""
+def batch_summary(args) -> dict:
+    """Batched plan vs the plain form (one graph at a time through qc_solve), with
+    the labels of every plain-solved graph compared with the batched ones."""
     import torch
     import paper_2305_14641_gb300 as qc
     graphs, sigmas = gg.planted_batch(args.batch_graphs)
@@ -444,8 +490,10 @@ def bench_batch(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     times = []
+    launches0 = ctx.launch_count()
+    steps = max(3, min(args.steps, 20))
     with ClockSampler(0) as clocks:
-        for k in range(args.steps):
+        for k in range(steps):
             flush.fill_(k & 0xff)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -453,42 +501,59 @@ def bench_batch(args):
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
-    batched = len(graphs) * args.steps / (sum(times) / 1000.0)
+    launches = (ctx.launch_count() - launches0) // steps
+    batched = len(graphs) * steps / (sum(times) / 1000.0)
+    batched_labels = plan.labels.cpu().numpy()
     # plain form: every graph through the single-graph path, one after another
     m = min(len(graphs), args.plain_graphs)
     for G, s in zip(Gs[:8], sigmas[:8]):
         G.solve([s], counts=False)
     torch.cuda.synchronize()
+    plain_labels = []
     t0 = time.perf_counter()
     for G, s in zip(Gs[:m], sigmas[:m]):
         G.drop_histogram()
-        G.solve([s], counts=False)
+        plain_labels.append(G.solve([s], counts=False)[1])
     torch.cuda.synchronize()
     plain = m / (time.perf_counter() - t0)
-    line = {"metric": "clusterings/s", "workload": BATCH_WORKLOAD, "graphs": len(graphs),
-            "nodes": int(sum(g.n for g in graphs)), "directed_edges": int(sum(g.nnz for g in graphs)),
-            "batched": batched, "ms_per_batch": sum(times) / len(times), "plain": plain,
-            "kernel_config": plan.config(),
-            "plain_sample_graphs": m, "batched_over_plain": batched / plain, "plan_seconds": plan_s,
-            "steps": args.steps, "clocks": clocks.summary()}
-    print(json.dumps(line), flush=True)
+    same = all(np.array_equal(lab.cpu().numpy()[0], batched_labels[plan.offsets[k]:plan.offsets[k] + graphs[k].n])
+               for k, lab in enumerate(plain_labels))
+    out = {"metric": "clusterings/s", "workload": BATCH_WORKLOAD, "graphs": len(graphs),
+           "nodes": int(sum(g.n for g in graphs)), "directed_edges": int(sum(g.nnz for g in graphs)),
+           "batched": batched, "ms_per_batch": sum(times) / len(times), "plain": plain,
+           "batched_over_plain": batched / plain, "labels_identical_on_plain_sample": bool(same),
+           "kernel_config": plan.config(), "gpu_launches_per_batch": launches,
+           "plain_sample_graphs": m, "plan_seconds": plan_s, "steps": steps, "clocks": clocks.summary()}
     plan.close()
+    for G in Gs:
+        G.close()
+    ctx.close()
+    return out
 
 
-def bench_serve(args):
-    """Open-loop Poisson stream through the server (p50/p99 latency), closed-loop
-    throughput, and the same requests solved serially with the plain form."""
+def bench_batch(args):
+    print(json.dumps(batch_summary(args)), flush=True)
+
+
+def serve_summary(args) -> dict:
+    """Open-loop Poisson stream through the server (p50/p99 latency over the
+    requests after the warm-up ones), closed-loop throughput, and the same requests
+    solved serially with the plain form (FIFO), whose labels must equal the served
+    ones.  The serial run also records its BFS device time, which bounds what any
+    form can reach while the large requests' BFS launches fill the GPU."""
     import threading as th
+    import torch
     import paper_2305_14641_gb300 as qc
     reqs = gg.sbm_request_stream(args.requests)
+    t_gen = time.perf_counter()
     graphs = [r.graph() for r in reqs]
-    lat, results = {}, {}
+    t_gen = time.perf_counter() - t_gen
+    lat, results, served_labels = {}, {}, {}
     with qc.Server(0, large_workers=args.large_workers, large_sm_share=args.large_sm_share) as srv:
         # warm up: a few requests of each kind
         for g, r in list(zip(graphs, reqs))[:8]:
             srv.wait(srv.submit(g.row_ptr, g.col_idx, r.sigma))
         ids = []
-        t_start = None
 
         def collector():
             for i in range(len(reqs)):
@@ -497,6 +562,7 @@ def bench_serve(args):
                 res = srv.wait(ids[i])
                 lat[i] = res["latency_ms"]
                 results[i] = (res["n_clusters"], res["admit_ms"], res["batch_size"], res["start_ms"])
+                served_labels[i] = res["labels"]
 
         col = th.Thread(target=collector)
         col.start()
@@ -519,24 +585,39 @@ def bench_serve(args):
         closed = len(reqs) / (time.perf_counter() - t0)
     # serial plain solves of the same requests (FIFO), device-resident after upload
     ctx = qc.Context(0)
-    t0 = time.perf_counter()
-    service = []
-    for g, r in zip(graphs, reqs):
-        s0 = time.perf_counter()
+    for g, r in list(zip(graphs, reqs))[:8]:
         G = qc.Graph.from_graph(ctx, g)
         G.solve([r.sigma], counts=True)
         G.close()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.kernel_stats("bfs_level", reset=True)
+    same = True
+    t0 = time.perf_counter()
+    service = []
+    for i, (g, r) in enumerate(zip(graphs, reqs)):
+        s0 = time.perf_counter()
+        G = qc.Graph.from_graph(ctx, g)
+        _, lab, _ = G.solve([r.sigma], counts=True)
+        G.close()
         service.append(time.perf_counter() - s0)
-    serial = len(reqs) / (time.perf_counter() - t0)
+        same = same and np.array_equal(lab.cpu().numpy()[0], served_labels[i])
+    serial_wall = time.perf_counter() - t0
+    serial = len(reqs) / serial_wall
+    bfs = ctx.kernel_stats("bfs_level", reset=True)
+    ctx.set_timing(False)
+    ctx.close()
     # latency of the serial plain form under the same arrivals (FIFO queue simulation)
     free_at, serial_lat = 0.0, []
     for r, sv in zip(reqs, service):
         start = max(r.arrival_s, free_at)
         free_at = start + sv
         serial_lat.append(1000.0 * (free_at - r.arrival_s))
+    warm = min(args.serve_warmup, len(reqs) - 1)
+    keep = list(range(warm, len(reqs)))
     L = np.array([lat[i] for i in range(len(reqs))])
-    big = [i for i in range(len(reqs)) if results[i][2] == 0]
-    small = [i for i in range(len(reqs)) if results[i][2] > 0]
+    big = [i for i in keep if results[i][2] == 0]
+    small = [i for i in keep if results[i][2] > 0]
 
     def split(idx):
         if not idx:
@@ -547,22 +628,35 @@ def bench_serve(args):
                 "p99_ms": float(np.percentile(L[idx], 99)), "mean_wait_ms": float(wait.mean()),
                 "mean_run_ms": float(run.mean()),
                 "mean_serial_service_ms": float(1000 * np.mean([service[i] for i in idx]))}
-    line = {"metric": "clusterings/s", "workload": SERVE_WORKLOAD, "requests": len(reqs),
-            "large_workers": args.large_workers, "large_sm_share": args.large_sm_share,
+    bfs_s = bfs["total_ms"] / 1000.0
+    return {"metric": "clusterings/s", "workload": SERVE_WORKLOAD, "requests": len(reqs),
+            "warmup_requests": warm, "large_workers": args.large_workers,
+            "large_sm_share": args.large_sm_share,
             "served_open_loop_per_s": len(reqs) / open_wall,
-            "p50_ms": float(np.percentile(L, 50)), "p99_ms": float(np.percentile(L, 99)),
+            "p50_ms": float(np.percentile(L[keep], 50)), "p99_ms": float(np.percentile(L[keep], 99)),
             "served_closed_loop_per_s": closed, "serial_plain_per_s": serial,
             "served_over_serial_plain": closed / serial,
-            "serial_plain_p50_ms": float(np.percentile(serial_lat, 50)),
-            "serial_plain_p99_ms": float(np.percentile(serial_lat, 99)),
+            "serial_plain_p50_ms": float(np.percentile(np.array(serial_lat)[keep], 50)),
+            "serial_plain_p99_ms": float(np.percentile(np.array(serial_lat)[keep], 99)),
+            "labels_identical_served_vs_plain": bool(same),
+            # the serial run's BFS launches alone (CUDA events); every request's BFS still has
+            # to run in any form, so requests / this time caps the served rate unless BFS
+            # launches of different requests overlap on the GPU
+            "serial_plain_bfs_device_s": bfs_s, "serial_plain_wall_s": serial_wall,
+            "serial_plain_bfs_share": bfs_s / serial_wall if serial_wall > 0 else None,
+            "ceiling_over_serial_if_bfs_serialised": (serial_wall / bfs_s) if bfs_s > 0 else None,
             "batched_requests": split(small), "worker_requests": split(big),
             "server_stats": {k: int(v) for k, v in st_open.items()}, "clocks": clocks.summary(),
+            "generate_seconds": t_gen,
             "slowest": [{"n": reqs[i].n, "latency_ms": round(float(L[i]), 3),
                          "admit_ms": round(results[i][1], 3), "start_ms": round(results[i][3], 3),
                          "batch_size": results[i][2],
                          "serial_service_ms": round(1000 * service[i], 3)}
-                        for i in np.argsort(-L)[:12]]}
-    print(json.dumps(line), flush=True)
+                        for i in sorted(keep, key=lambda i: -L[i])[:8]]}
+
+
+def bench_serve(args):
+    print(json.dumps(serve_summary(args)), flush=True)
 
 
 def _device_steps(step, steps, flush, stream):
@@ -767,12 +861,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--step", choices=["plan", "solve"], default="plan",
+                    help="default workload: replay the captured sweep plan, or the single-graph path")
     ap.add_argument("--workload", choices=["dcsbm16384", "sbm262144", "directed16384", "batch4096", "serve",
                                            "adjacency16384", "weighted16384", "fig3", "quality"],
                     default="dcsbm16384")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--plain-graphs", type=int, default=512)
-    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--requests", type=int, default=4000)
+    ap.add_argument("--serve-warmup", type=int, default=200,
+                    help="requests at the start of the stream left out of the latency figures")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload only: leave out the batch4096 and serve sub-lines")
     ap.add_argument("--large-workers", type=int, default=4)
     ap.add_argument("--large-sm-share", type=float, default=0.4)
     args = ap.parse_args()

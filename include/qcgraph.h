@@ -47,7 +47,7 @@ typedef enum {
     QC_ERR_OOM = 3,            /* the allocator returned no memory */
     QC_ERR_BUDGET = 4,         /* the request would exceed the context's memory budget */
     QC_ERR_CUDA = 5,           /* a CUDA runtime error, or no usable GPU */
-    QC_ERR_TIMEOUT = 6,        /* a device-side wait gave up (bounded spin ran out) */
+    QC_ERR_TIMEOUT = 6,        /* a device-side wait gave up (its time limit ran out) */
     QC_ERR_CANCELLED = 7,      /* a served request was cancelled */
     QC_ERR_NOT_READY = 8       /* a served request has not completed yet */
 } qc_status;
@@ -56,6 +56,7 @@ typedef struct qc_ctx qc_ctx;
 typedef struct qc_graph qc_graph;
 typedef struct qc_batch qc_batch;
 typedef struct qc_server qc_server;
+typedef struct qc_sweep qc_sweep;
 
 /* Device-memory provider.  alloc returns `bytes` of device memory usable on
  * `stream` (NULL on failure); free returns it.  Both may be called from any
@@ -83,15 +84,24 @@ void qc_context_destroy(qc_ctx *ctx);
 size_t qc_context_bytes_in_use(const qc_ctx *ctx);
 /* Per-kernel timing, for measurement.  When enabled, the library brackets every
  * launch of its dominant kernels with CUDA events on the launching stream and
- * accumulates their durations and the modelled bytes each launch must move
- * (for the BFS, per level pass over a chunk of wn source words:
- * 8 wn (E + 3N) bitset bytes + the CSR + one histogram row).  Names: "bfs_level"
- * per launch, "bfs_pass_<l>" per level from device timestamps.  Off by
- * default. */
+ * accumulates their durations with two byte counts per launch:
+ *   model_bytes  the pull-all model of the BFS: per level pass over a chunk of
+ *                wn source words, 8 wn (E + 3N) bitset bytes + the CSR + one
+ *                histogram row (an upper bound: saturated rows are skipped);
+ *   min_bytes    the bytes the launch must move between HBM and the GPU at
+ *                the least: its inputs read once (CSR, node order and row
+ *                bounds, components, per-word masks), its histogram rows
+ *                written once, and, for each level, the bitset rows still
+ *                open at that level (read and written, 32 bytes per 16-byte
+ *                segment, counted on the device) beyond what L2 can hold.
+ * Names: "bfs_level" per launch, "bfs_pass_<l>" per level from device
+ * timestamps.  Off by default; it adds one counter update per warp and item
+ * run to the BFS. */
 typedef struct {
     uint64_t launches;
     double total_ms;        /* sum of event-measured launch durations */
-    double model_bytes;     /* sum of modelled algorithmic bytes */
+    double model_bytes;     /* sum of modelled pull-all bytes */
+    double min_bytes;       /* sum of compulsory HBM bytes */
 } qc_kernel_stats;
 qc_status qc_context_set_timing(qc_ctx *ctx, int enable);
 /* kernel: "bfs_level" (the bitset BFS level step).  reset != 0 clears the
@@ -222,6 +232,39 @@ qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, int32_t n_sig
 qc_status qc_solve(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
                    int32_t *labels_out, int32_t *n_clusters_out, void *stream);
 
+/* ---- one graph, a fixed sigma sweep, replayed ---------------------------------- */
+
+/* A solve plan for one graph and a fixed list of sigma values: Algorithm 4 for
+ * each sigma (the hop-distance histogram of every node behind Algorithm 1, the
+ * potentials of Eq. 7, Graph Gradient Descent of Algorithm 2 and the roots of
+ * Algorithm 3), queued once into CUDA graphs together with every buffer the
+ * work uses, and replayed by qc_sweep_run.  The plan keeps a histogram of its
+ * own (the graph's cached one is neither read nor changed).
+ * sigmas: host double[n_sigma], each finite and > 0 (copied).  V_out: device
+ * double[n_sigma * n] or NULL (the potentials then stay in plan memory);
+ * labels_out: device int32[n_sigma * n], root node ids, V_out[s * n + v] and
+ * labels_out[s * n + v] as qc_potential / qc_ggd_labels write them; both must
+ * stay valid while the plan exists.  The graph must outlive the plan.  Runs of
+ * one plan must not overlap on the GPU.  Creation synchronises `stream`.
+ * Errors: QC_ERR_INVALID_ARG, QC_ERR_BUDGET, QC_ERR_OOM, QC_ERR_CUDA. */
+qc_status qc_sweep_create(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out, int32_t *labels_out,
+                          void *stream, qc_sweep **out);
+/* One run.  reuse_histogram = 0: everything from the resident CSR (the BFS,
+ * then potentials, descent and roots for every sigma); the call waits for the
+ * run to read the BFS's outcome (a BFS deeper than the plan's histogram rows is
+ * run again with more rows).  reuse_histogram != 0: potentials, descent and
+ * roots from the histogram of the plan's last full run (QC_ERR_INVALID_ARG if
+ * there was none); asynchronous on `stream` unless n_clusters_out is given.
+ * n_clusters_out: host int32[n_sigma] (roots per sigma) or NULL.
+ * Errors: QC_ERR_INVALID_ARG, QC_ERR_TIMEOUT (a device-side wait gave up),
+ * QC_ERR_CUDA. */
+qc_status qc_sweep_run(qc_sweep *p, int32_t reuse_histogram, int32_t *n_clusters_out, void *stream);
+/* D of the last full run (-1 before one); whether runs replay captured CUDA
+ * graphs (1) or queue the same kernels directly (0, where a capture is
+ * refused); the kernels one full run executes.  Any pointer may be NULL. */
+qc_status qc_sweep_info(const qc_sweep *p, int32_t *D, int32_t *captured, int64_t *kernels_per_run);
+void qc_sweep_destroy(qc_sweep *p);
+
 /* ---- many graphs ------------------------------------------------------------ */
 
 /* A batch plan: Algorithm 4 for n_graphs graphs, graph k clustered with
@@ -330,16 +373,17 @@ void qc_server_destroy(qc_server *s);
 /* ---- self-test of the bounded device wait ----------------------------------------- */
 
 /* The paper has no counterpart to this call.  Every persistent kernel of the
- * library synchronises its blocks with a grid barrier whose spin gives up after
- * a bounded number of polls (about a second at the library's limit), records a
- * timeout and returns, so that a block that never arrives surfaces as
- * QC_ERR_TIMEOUT instead of a hung GPU.  This call launches that barrier with
- * two blocks, one of which leaves without arriving, and a spin limit of
- * spin_limit polls (1 .. 2^24, about 100 ns each).
+ * library synchronises its blocks with a grid barrier whose wait gives up once
+ * 2 s have passed on the GPU's global timer, records a timeout and returns, so
+ * that a block that never arrives surfaces as QC_ERR_TIMEOUT instead of a hung
+ * GPU.  This call launches that barrier with two blocks, one of which leaves
+ * without arriving, and a limit of timeout_us microseconds (1 .. 10^7).
+ * waited_ns: host, receives how long the waiting block waited (GPU global
+ * timer), or NULL.
  * Returns QC_ERR_TIMEOUT (with qc_last_error describing it) when the wait gave
  * up as designed; the context stays usable.  QC_ERR_CUDA if the barrier failed
  * to notice the missing block, QC_ERR_INVALID_ARG for a bad limit. */
-qc_status qc_selftest_barrier_timeout(qc_ctx *ctx, int64_t spin_limit, void *stream);
+qc_status qc_selftest_barrier_timeout(qc_ctx *ctx, int64_t timeout_us, int64_t *waited_ns, void *stream);
 
 /* ---- self-test of the weighted path's exponential --------------------------------- */
 
@@ -356,6 +400,19 @@ qc_status qc_selftest_barrier_timeout(qc_ctx *ctx, int64_t spin_limit, void *str
 enum { QC_ARITH_EXP_NEG = 0 };
 qc_status qc_selftest_arith(qc_ctx *ctx, int32_t op, const double *x, const double *y, double *out, int64_t n,
                             void *stream);
+
+/* ---- L2 read bandwidth probe ---------------------------------------------------------- */
+
+/* The paper has no counterpart to this call.  It measures the read throughput of
+ * a device buffer of `bytes` bytes (1 MiB .. 4 GiB; below the L2 size it stays
+ * resident there) read through L2 only: mode 0 streams it (16 bytes per thread,
+ * consecutive across the grid), mode 1 reads 512-byte segments at pseudo-random
+ * positions, one warp per segment and four in flight, the pattern of the BFS's
+ * neighbour gathers.  The buffer is read about 64 times in one timed launch
+ * after a warming one; *gbs receives the bytes read per second / 1e9.  It serves
+ * as the roofline of kernels whose working set lives in L2.
+ * Errors: QC_ERR_INVALID_ARG, QC_ERR_BUDGET, QC_ERR_OOM, QC_ERR_CUDA. */
+qc_status qc_selftest_l2_read(qc_ctx *ctx, int64_t bytes, int32_t mode, double *gbs, void *stream);
 
 /* ---- histogram without device allocation ---------------------------------------- */
 

@@ -19,7 +19,7 @@ import numpy as np
 from . import native
 from .native import QCError
 
-__all__ = ["Context", "Graph", "BatchPlan", "Server", "QCError", "solve_batch"]
+__all__ = ["Context", "Graph", "SweepPlan", "BatchPlan", "Server", "QCError", "solve_batch"]
 
 
 def _torch():
@@ -81,16 +81,19 @@ class Context:
         self.check(self._lib.qc_context_kernel_stats(self.handle, kernel.encode(), ctypes.byref(st),
                                                      int(reset)))
         return {"launches": int(st.launches), "total_ms": float(st.total_ms),
-                "model_bytes": float(st.model_bytes)}
+                "model_bytes": float(st.model_bytes), "min_bytes": float(st.min_bytes)}
 
     def launch_count(self) -> int:
         return int(self._lib.qc_context_launch_count(self.handle))
 
-    def selftest_barrier_timeout(self, spin_limit: int = 1 << 14, stream=None) -> str:
-        """Run the library's grid barrier with a block that never arrives; returns the
-        status name (QC_ERR_TIMEOUT when the bounded wait gave up as designed)."""
-        st = self._lib.qc_selftest_barrier_timeout(self.handle, int(spin_limit), _stream_handle(stream))
-        return native.STATUS.get(st, str(st))
+    def selftest_barrier_timeout(self, timeout_us: int = 2000, stream=None) -> tuple[str, int]:
+        """Run the library's grid barrier with a block that never arrives and a time
+        limit of timeout_us; returns (status name, nanoseconds the waiting block
+        waited).  QC_ERR_TIMEOUT is the status when the bounded wait gave up as designed."""
+        waited = ctypes.c_int64(-1)
+        st = self._lib.qc_selftest_barrier_timeout(self.handle, int(timeout_us), ctypes.byref(waited),
+                                                   _stream_handle(stream))
+        return native.STATUS.get(st, str(st)), int(waited.value)
 
     def _selftest_arith(self, op: int, x, y, stream):
         torch = _torch()
@@ -106,6 +109,14 @@ class Context:
         """exp(-t) by the weighted potential's own routine (t: float64, >= 0); returns a
         float64 device tensor."""
         return self._selftest_arith(0, t, None, stream)
+
+    def l2_read_gbs(self, nbytes: int = 48 << 20, random_segments: bool = False, stream=None) -> float:
+        """Read throughput (GB/s) of an nbytes buffer read through L2 only, streamed or
+        as random 512-byte segments (the BFS gather pattern)."""
+        out = ctypes.c_double()
+        self.check(self._lib.qc_selftest_l2_read(self.handle, int(nbytes), int(bool(random_segments)),
+                                                 ctypes.byref(out), _stream_handle(stream)))
+        return float(out.value)
 
     def bytes_in_use(self) -> int:
         return int(self._lib.qc_context_bytes_in_use(self.handle))
@@ -271,6 +282,60 @@ class Graph:
     def close(self) -> None:
         if getattr(self, "handle", None):
             self.ctx._lib.qc_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SweepPlan:
+    """Algorithm 4 for one graph and a fixed list of sigma values, captured once
+    into CUDA graphs and replayed: run() recomputes everything from the resident
+    CSR (BFS, potentials, descent, roots); run(reuse_histogram=True) reuses the
+    histogram of the plan's last full run.
+
+    V: float64 tensor [S, n] (or None to keep the potentials inside the plan);
+    labels: int32 tensor [S, n] of root node ids.  Both are allocated here when not
+    given and stay owned by the plan object.
+    """
+
+    def __init__(self, graph: Graph, sigmas: Sequence[float], V=None, labels=None, stream=None,
+                 keep_potentials: bool = True):
+        torch = _torch()
+        ctx = graph.ctx
+        self.ctx, self.graph = ctx, graph
+        S, n = len(sigmas), graph.n
+        dev = f"cuda:{ctx.device}"
+        self.labels = labels if labels is not None else torch.empty((S, n), dtype=torch.int32, device=dev)
+        if V is None and keep_potentials:
+            V = torch.empty((S, n), dtype=torch.float64, device=dev)
+        self.V = V
+        self.S = S
+        sig = (ctypes.c_double * S)(*[float(x) for x in sigmas])
+        h = ctypes.c_void_p()
+        ctx.check(ctx._lib.qc_sweep_create(graph.handle, sig, S, V.data_ptr() if V is not None else None,
+                                           self.labels.data_ptr(), _stream_handle(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, reuse_histogram: bool = False, counts: bool = False, stream=None):
+        """One run; returns the clusters per sigma (host ints) when counts, else None."""
+        nc = (ctypes.c_int32 * self.S)() if counts else None
+        self.ctx.check(self.ctx._lib.qc_sweep_run(self.handle, int(bool(reuse_histogram)), nc,
+                                                  _stream_handle(stream)))
+        return list(nc) if counts else None
+
+    def info(self) -> dict:
+        """D of the last full run, whether runs replay captured CUDA graphs, kernels per full run."""
+        D, cap, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        self.ctx.check(self.ctx._lib.qc_sweep_info(self.handle, ctypes.byref(D), ctypes.byref(cap), ctypes.byref(k)))
+        return {"D": D.value, "captured": bool(cap.value), "kernels_per_run": k.value}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            self.ctx._lib.qc_sweep_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -72,6 +72,7 @@ constexpr int LIST_AFTER = 2;          // pull levels of a launch that scan ever
 using qcdev::ST_DONE;
 using qcdev::ST_NEED_ROWS;
 using qcdev::ST_TIMEOUT;
+using qcdev::global_ns;
 using qcdev::grid_barrier;
 
 struct BfsParams {
@@ -104,16 +105,12 @@ struct BfsParams {
     int32_t *heavy_ctr;         // [rows] block items taken so far at each level
     int32_t *wl[2];             // worklists of light items: level l reads wl[l & 1]
     int32_t *wl_count;          // [rows] length of each level's worklist
-    int32_t *status;            // [0] state, [1] level reached
+    int32_t *status;            // [0] state, [1] highest level reached (the pass that found nothing);
+                                // the graph's outcome words, kept across the chunks of one BFS
     unsigned *bar;              // [0] arrivals, [1] generation
     unsigned long long *stamp;  // [rows] globaltimer when each level's barrier opened (timing only)
+    int32_t *pulled;            // [rows] (node, tile) items pulled at each level (timing only, else null)
 };
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 __device__ __forceinline__ bool seg_full(const ulonglong2 a) { return (a.x & a.y) == ONES; }
 
@@ -201,6 +198,8 @@ __device__ void init_bits(const BfsParams &p) {
 
 // New bits found by the block at the current level.
 __shared__ unsigned int block_found;
+// Items the block pulled at the current level (reported in timing mode).
+__shared__ unsigned int block_pulled;
 // Per warp: ids and change masks of the neighbours a G = 32 gather reads.
 __shared__ int2 pack[WARPS][32];
 
@@ -352,6 +351,7 @@ __device__ void heavy_items(const BfsParams &p, const int level, const bool mask
             if (wib == 0 && qok) orow[q] = make_ulonglong2(ONES, ONES);
             continue;
         }
+        if (threadIdx.x == 0) block_pulled += 1u;
         const ulonglong2 own = qok ? vin[(size_t)v * p.R + q] : make_ulonglong2(ONES, ONES);
         const int beg = inf.y, end = inf.z;
         red[wib][lane] = gather_or<32, MASKS>(p, level, beg + 32 * wib, end, 32 * WARPS, q, qok, own, masked, t);
@@ -414,6 +414,10 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
             if (slot == 0 && q < p.R) vout[(size_t)v * p.R + q] = make_ulonglong2(ONES, ONES);
         }
         const unsigned pulls = __ballot_sync(FULL, pull);
+        // (rows of fewer than 17 segments always fit L2, so only the tiled variant counts)
+        if constexpr (G == 32) {
+            if (lane == 0 && pulls) atomicAdd(&block_pulled, (unsigned)__popc(pulls));
+        }
         mask = pulls;
         if constexpr (MASKS) {
             // item state: the next item's own segment and first neighbour ids are
@@ -495,10 +499,11 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
 template <int G, bool MASKS>
 __global__ void __launch_bounds__(256, G == 32 ? 3 : 4) bfs_persistent(const BfsParams p) {
     __shared__ ulonglong2 red[WARPS][32];
-    if constexpr (MASKS) {
-        if (threadIdx.x == 0) block_found = 0u;
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        block_found = 0u;
+        block_pulled = 0u;
     }
+    __syncthreads();
     int level = p.start_level;
     const bool stamp = p.stamp && blockIdx.x == 0 && threadIdx.x == 0;
     if (stamp) p.stamp[level - 1] = global_ns();
@@ -517,7 +522,7 @@ __global__ void __launch_bounds__(256, G == 32 ? 3 : 4) bfs_persistent(const Bfs
     for (;; ++level) {
         if (level >= p.rows) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
-                p.status[1] = level;
+                atomicMax(p.status + 1, level);
                 atomicCAS(p.status, ST_DONE, ST_NEED_ROWS);
             }
             return;
@@ -538,6 +543,10 @@ __global__ void __launch_bounds__(256, G == 32 ? 3 : 4) bfs_persistent(const Bfs
         light_items<G, MASKS>(p, level, level >= p.start_level + LIST_AFTER + 1,
                               level >= p.start_level + LIST_AFTER, masked, any_new);
         if (__syncthreads_or(any_new) && threadIdx.x == 0) p.level_new[level] = 1;
+        if (threadIdx.x == 0) {
+            if (p.pulled && block_pulled) atomicAdd(p.pulled + level, (int)block_pulled);
+            block_pulled = 0u;
+        }
         if constexpr (MASKS) {
             // a count past 2^32 in one block only misjudges the density estimate
             if (threadIdx.x == 0) {
@@ -549,7 +558,7 @@ __global__ void __launch_bounds__(256, G == 32 ? 3 : 4) bfs_persistent(const Bfs
         if (stamp) p.stamp[level + 1] = global_ns();
         if (*(volatile int32_t *)(p.level_new + level) == 0) break;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) p.status[1] = level;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(p.status + 1, level);
 }
 
 typedef void (*bfs_fn)(const BfsParams);
@@ -594,15 +603,135 @@ double qc_bfs_level_model_bytes(int64_t n, int64_t nnz, int64_t wn) {
            4.0 * (double)n;
 }
 
-qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
+// Scratch of one all-source BFS: chunk width, variant, bitset buffers, item state,
+// worklists and the control block.  Sized once per graph and reused by every
+// chunk (and, in a captured plan, by every replay).
+qc_status qc_bfs_scratch_init(qc_graph *g, qc_bfs_scratch &bs, cudaStream_t stream) {
+    qc_ctx *ctx = g->ctx;
+    const int32_t n = g->n;
+    bs.wc = qc_bfs_chunk_words(ctx, n);
+    bs.R_max = (bs.wc + 1) / 2;
+    bs.T_max = bs.R_max >= 32 ? (bs.R_max + 31) / 32 : 1;
+    const size_t vis_bytes = sizeof(ulonglong2) * (size_t)bs.R_max * (size_t)n;
+    QC_TRY(bs.visA.allocate(ctx, vis_bytes, stream));
+    QC_TRY(bs.visB.allocate(ctx, vis_bytes, stream));
+    // Change masks (rows of more than 16 segments) pay off when the frontiers of the
+    // first pull levels are sparse: a tree-like graph of mean degree d reaches about
+    // d^2 of its n nodes in two hops, so the variant with masks is taken when
+    // d^2 * mask_ratio < n (a level then reads masked segments while the previous
+    // level found fewer than 64 wn n / mask_ratio new bits).  Measured on GB300:
+    // SBM of mean degree 20 with n = 2^16 and 2^18, 7 % and 11 % faster; a
+    // DC-SBM of n = 2^14 and mean degree 16, 5 % slower (only its level 2 is sparse).
+    // QCGRAPH_MASK_RATIO overrides the ratio (0: never).
+    bs.mask_ratio = 128;
+    if (const char *env = getenv("QCGRAPH_MASK_RATIO")) bs.mask_ratio = std::max(0, atoi(env));
+    const double mean_deg = (double)g->nnz / (double)n;
+    bs.masks = bs.mask_ratio > 0 && bs.R_max > 16 && mean_deg * mean_deg * bs.mask_ratio < (double)n;
+    if (bs.masks) QC_TRY(bs.fmask.allocate(ctx, 2 * sizeof(uint32_t) * (size_t)n * bs.T_max, stream));
+    QC_TRY(bs.sat.allocate(ctx, sizeof(int32_t) * (size_t)n * bs.T_max, stream));
+    QC_TRY(bs.wl.allocate(ctx, 2 * sizeof(int32_t) * (size_t)n * bs.T_max, stream));
+    // control block: 8 ints (barrier at [2..3]), then level_new, the per-level work
+    // counters (light, heavy) and worklist lengths, each with room for any depth
+    // (<= n + 1), then the per-level bit counts (64-bit, at an even offset), then
+    // the per-level pulled-item counts of timing mode
+    const size_t ctl_ints = 8 + 7 * ((size_t)n + 2);
+    QC_TRY(bs.ctl.allocate(ctx, sizeof(int32_t) * ctl_ints, stream));
+    return QC_OK;
+}
+
+// Queue one launch: the chunk of source words starting at w0, from level `start`
+// (2: a fresh chunk), adding into hist (rows rows) and recording its outcome in
+// out[0..1] (reset first when reset_out).  stamps: per-level timestamps or null
+// (timing mode: the pulled-item counts are then kept in the control block too).
+qc_status qc_bfs_launch(qc_graph *g, qc_bfs_scratch &bs, int32_t w0, int32_t start, int32_t *hist, int32_t rows,
+                        int32_t *out, bool reset_out, unsigned long long *stamps, cudaStream_t stream) {
+    qc_ctx *ctx = g->ctx;
+    const int32_t n = g->n;
+    const int32_t W = (n + 63) / 64;
+    const int32_t wn = (W - w0) < bs.wc ? (W - w0) : bs.wc;
+    const int32_t R = (wn + 1) / 2;
+    const int32_t T = R >= 32 ? (R + 31) / 32 : 1;
+    int G = 32;
+    bfs_fn fn = pick(R, bs.masks, &G);
+    int per_sm = 0;
+    QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, 256, 0));
+    if (per_sm < 1) {
+        qc_set_error(ctx, "BFS kernel cannot be resident on an SM");
+        return QC_ERR_CUDA;
+    }
+    const int items = n * T;
+    int blocks = per_sm * qc_coop_sms(ctx);
+    if (blocks > qc_ceil_div(items, 8)) blocks = qc_ceil_div(items, 8);
+    if (blocks < 1) blocks = 1;
+    BfsParams p;
+    p.n = n;
+    p.row_ptr = g->row_ptr.as<int32_t>();
+    p.col_idx = g->col_idx.as<int32_t>();
+    p.order = g->order.as<int32_t>();
+    p.info = g->oinfo.as<int4>();
+    p.comp = g->comp.as<int32_t>();
+    p.wcomp = g->wcomp.as<int32_t>();
+    p.wmajor = g->wmajor.as<int32_t>();
+    p.wmask = g->wmask.as<unsigned long long>();
+    p.buf[0] = bs.visB.as<ulonglong2>();
+    p.buf[1] = bs.visA.as<ulonglong2>();
+    const bool with_masks = bs.masks && G == 32;
+    p.fmask[0] = with_masks ? bs.fmask.as<uint32_t>() : nullptr;
+    p.fmask[1] = with_masks ? bs.fmask.as<uint32_t>() + (size_t)n * bs.T_max : nullptr;
+    p.mask_ratio = bs.mask_ratio;
+    p.R = R;
+    p.T = T;
+    p.w0 = w0;
+    p.wn = wn;
+    p.W = W;
+    p.last_mask = (n % 64) ? (ONES << (n % 64)) : 0ull;
+    p.sat = bs.sat.as<int32_t>();
+    p.hist = hist;
+    p.rows = rows;
+    p.first_chunk = (w0 == 0);
+    p.start_level = start;
+    p.status = out;
+    int32_t *c = bs.ctl.as<int32_t>();
+    p.bar = reinterpret_cast<unsigned *>(c + 2);
+    p.level_new = c + 8;
+    p.light_ctr = p.level_new + (n + 2);
+    p.heavy_ctr = p.light_ctr + (n + 2);
+    p.wl_count = p.heavy_ctr + (n + 2);
+    p.level_bits = reinterpret_cast<unsigned long long *>(p.wl_count + (n + 2));
+    p.wl[0] = bs.wl.as<int32_t>();
+    p.wl[1] = bs.wl.as<int32_t>() + (size_t)n * bs.T_max;
+    p.stamp = stamps;
+    p.pulled = stamps ? reinterpret_cast<int32_t *>(p.level_bits + (n + 2)) : nullptr;
+    QC_CUDA_TRY(ctx, cudaMemsetAsync(bs.ctl.ptr, 0, bs.ctl.bytes, stream));
+    if (reset_out) QC_CUDA_TRY(ctx, cudaMemsetAsync(out, 0, 2 * sizeof(int32_t), stream));
+    void *args[] = {(void *)&p};
+    QC_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(256), args, 0, stream));
+    QC_LAUNCHED(ctx);
+    return QC_OK;
+}
+
+// Pulled-item counts of the last timing-mode launch (in the control block).
+static const int32_t *pulled_counts(const qc_graph *g, const qc_bfs_scratch &bs) {
+    const int32_t n = g->n;
+    return bs.ctl.as<int32_t>() + 8 + 4 * (n + 2) + 2 * (n + 2);
+}
+
+// The BFS of every source chunk.  sync: each launch is waited for and its outcome
+// read (a launch that runs out of histogram rows is relaunched from where it
+// stopped; timing mode also records per-launch figures).  Otherwise every launch
+// is queued without waiting; the outcome words (g->bfs_out) are read later by
+// qc_bfs_settle.
+static qc_status bfs_run(qc_graph *g, cudaStream_t stream, bool sync) {
     qc_range range("qc.bfs");
     qc_ctx *ctx = g->ctx;
     const int32_t n = g->n;
     const int32_t W = (n + 63) / 64;
     g->hist_valid = false;
+    g->bfs_queued = false;
     g->D = g->nnz > 0 ? 1 : 0;
     QC_TRY(qc_graph_prepare(g, stream));
     QC_TRY(ensure_hist_rows(g, g->nnz > 0 ? 32 : 2, stream));
+    if (!g->bfs_out.ptr) QC_TRY(g->bfs_out.allocate(ctx, sizeof(int32_t) * 8, stream));
     if (g->nnz == 0) {
         // no edges: h(0) = 1 for every node, nothing else
         QC_TRY(qc_fill_first_rows(g, stream));
@@ -615,37 +744,19 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
         g->hist_valid = true;
         return QC_OK;
     }
-    const int32_t wc = qc_bfs_chunk_words(ctx, n);
-    const int32_t R_max = (wc + 1) / 2;
-    const int32_t T_max = R_max >= 32 ? (R_max + 31) / 32 : 1;
-    qc_buffer visA, visB, sat, ctl, wl, fmask;
-    const size_t vis_bytes = sizeof(ulonglong2) * (size_t)R_max * (size_t)n;
-    QC_TRY(visA.allocate(ctx, vis_bytes, stream));
-    QC_TRY(visB.allocate(ctx, vis_bytes, stream));
-    // Change masks (rows of more than 16 segments) pay off when the frontiers of the
-    // first pull levels are sparse: a tree-like graph of mean degree d reaches about
-    // d^2 of its n nodes in two hops, so the variant with masks is taken when
-    // d^2 * mask_ratio < n (a level then reads masked segments while the previous
-    // level found fewer than 64 wn n / mask_ratio new bits).  Measured on GB300:
-    // SBM of mean degree 20 with n = 2^16 and 2^18, 7 % and 11 % faster; a
-    // DC-SBM of n = 2^14 and mean degree 16, 5 % slower (only its level 2 is sparse).
-    // QCGRAPH_MASK_RATIO overrides the ratio (0: never).
-    int32_t mask_ratio = 128;
-    if (const char *env = getenv("QCGRAPH_MASK_RATIO")) mask_ratio = std::max(0, atoi(env));
-    const double mean_deg = (double)g->nnz / (double)n;
-    const bool masks = mask_ratio > 0 && R_max > 16 && mean_deg * mean_deg * mask_ratio < (double)n;
-    if (masks) QC_TRY(fmask.allocate(ctx, 2 * sizeof(uint32_t) * (size_t)n * T_max, stream));
-    QC_TRY(sat.allocate(ctx, sizeof(int32_t) * (size_t)n * T_max, stream));
-    QC_TRY(wl.allocate(ctx, 2 * sizeof(int32_t) * (size_t)n * T_max, stream));
-    // control block: status (2 ints), barrier (2 uints), pad, then level_new, the
-    // per-level work counters (light, heavy) and worklist lengths, each with room for
-    // any depth (<= n + 1), then the per-level bit counts (64-bit, at an even offset)
-    const size_t ctl_ints = 8 + 6 * ((size_t)n + 2);
-    QC_TRY(ctl.allocate(ctx, sizeof(int32_t) * ctl_ints, stream));
+    qc_bfs_scratch bs;
+    QC_TRY(qc_bfs_scratch_init(g, bs, stream));
+    int32_t *out = g->bfs_out.as<int32_t>();
+    if (!sync) {
+        for (int32_t w0 = 0; w0 < W; w0 += bs.wc)
+            QC_TRY(qc_bfs_launch(g, bs, w0, 2, g->hist.as<int32_t>(), g->hist_rows, out, w0 == 0, nullptr, stream));
+        g->hist_valid = true;
+        g->bfs_queued = true;
+        return QC_OK;
+    }
     qc_pinned pin(ctx);
     QC_TRY(pin.acquire());
     int32_t *h_status = static_cast<int32_t *>(pin.ptr);
-
     const bool timing = ctx->timing.load();
     qc_event_pair ev;
     qc_buffer stamps;
@@ -653,83 +764,34 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
         QC_TRY(ev.create(ctx));
         QC_TRY(stamps.allocate(ctx, sizeof(unsigned long long) * ((size_t)n + 3), stream));
     }
-
-    const uint64_t last_mask = (n % 64) ? (ONES << (n % 64)) : 0ull;
-    for (int32_t w0 = 0; w0 < W; w0 += wc) {
-        const int32_t wn = (W - w0) < wc ? (W - w0) : wc;
+    for (int32_t w0 = 0; w0 < W; w0 += bs.wc) {
+        const int32_t wn = (W - w0) < bs.wc ? (W - w0) : bs.wc;
         const int32_t R = (wn + 1) / 2;
         const int32_t T = R >= 32 ? (R + 31) / 32 : 1;
-        int G = 32;
-        bfs_fn fn = pick(R, masks, &G);
-        int per_sm = 0;
-        QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, 256, 0));
-        if (per_sm < 1) {
-            qc_set_error(ctx, "BFS kernel cannot be resident on an SM");
-            return QC_ERR_CUDA;
-        }
-        const int items = n * T;
-        int blocks = per_sm * qc_coop_sms(ctx);
-        if (blocks > qc_ceil_div(items, 8)) blocks = qc_ceil_div(items, 8);
-        if (blocks < 1) blocks = 1;
         int32_t start = 2;
         while (true) {
-            BfsParams p;
-            p.n = n;
-            p.row_ptr = g->row_ptr.as<int32_t>();
-            p.col_idx = g->col_idx.as<int32_t>();
-            p.order = g->order.as<int32_t>();
-            p.info = g->oinfo.as<int4>();
-            p.comp = g->comp.as<int32_t>();
-            p.wcomp = g->wcomp.as<int32_t>();
-            p.wmajor = g->wmajor.as<int32_t>();
-            p.wmask = g->wmask.as<unsigned long long>();
-            p.buf[0] = visB.as<ulonglong2>();
-            p.buf[1] = visA.as<ulonglong2>();
-            const bool with_masks = masks && G == 32;
-            p.fmask[0] = with_masks ? fmask.as<uint32_t>() : nullptr;
-            p.fmask[1] = with_masks ? fmask.as<uint32_t>() + (size_t)n * T_max : nullptr;
-            p.mask_ratio = mask_ratio;
-            p.R = R;
-            p.T = T;
-            p.w0 = w0;
-            p.wn = wn;
-            p.W = W;
-            p.last_mask = last_mask;
-            p.sat = sat.as<int32_t>();
-            p.hist = g->hist.as<int32_t>();
-            p.rows = g->hist_rows;
-            p.first_chunk = (w0 == 0);
-            p.start_level = start;
-            p.status = ctl.as<int32_t>();
-            p.bar = reinterpret_cast<unsigned *>(ctl.as<int32_t>() + 2);
-            p.level_new = ctl.as<int32_t>() + 8;
-            p.light_ctr = p.level_new + (n + 2);
-            p.heavy_ctr = p.light_ctr + (n + 2);
-            p.wl_count = p.heavy_ctr + (n + 2);
-            p.level_bits = reinterpret_cast<unsigned long long *>(p.wl_count + (n + 2));
-            p.wl[0] = wl.as<int32_t>();
-            p.wl[1] = wl.as<int32_t>() + (size_t)n * T_max;
-            p.stamp = timing ? stamps.as<unsigned long long>() : nullptr;
-            QC_CUDA_TRY(ctx, cudaMemsetAsync(ctl.ptr, 0, ctl.bytes, stream));
-            void *args[] = {(void *)&p};
             if (timing) QC_CUDA_TRY(ctx, cudaEventRecord(ev.a, stream));
-            QC_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(256), args,
-                                                         0, stream));
-            QC_LAUNCHED(ctx);
+            QC_TRY(qc_bfs_launch(g, bs, w0, start, g->hist.as<int32_t>(), g->hist_rows, out, true,
+                                 timing ? stamps.as<unsigned long long>() : nullptr, stream));
             if (timing) QC_CUDA_TRY(ctx, cudaEventRecord(ev.b, stream));
-            QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_status, ctl.ptr, 2 * sizeof(int32_t),
-                                             cudaMemcpyDeviceToHost, stream));
+            QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_status, out, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
             // the preparation's status rides in the same wait (slot 2 of the pinned block)
             if (!g->prep_checked)
                 QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_status + 2, g->prep_ctl.ptr, sizeof(int32_t),
                                                  cudaMemcpyDeviceToHost, stream));
-            // level stamps ride in the same pinned block, after the status words
+            // level stamps and pulled-item counts ride in the same pinned block, after
+            // the status words: stamps in its first half, counts in its second
             unsigned long long *h_stamp = reinterpret_cast<unsigned long long *>(
                 static_cast<char *>(pin.ptr) + 64);
-            const size_t stamp_cap = std::min<size_t>((size_t)n + 3, (QC_PINNED_BYTES - 64) / 8);
-            if (timing)
+            const size_t stamp_cap = std::min<size_t>((size_t)n + 3, (QC_PINNED_BYTES / 2 - 64) / 8);
+            int32_t *h_pulled = reinterpret_cast<int32_t *>(static_cast<char *>(pin.ptr) + QC_PINNED_BYTES / 2);
+            const size_t pulled_cap = std::min<size_t>((size_t)n + 2, (QC_PINNED_BYTES / 2) / 4);
+            if (timing) {
                 QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_stamp, stamps.ptr, sizeof(unsigned long long) * stamp_cap,
                                                  cudaMemcpyDeviceToHost, stream));
+                QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_pulled, pulled_counts(g, bs), sizeof(int32_t) * pulled_cap,
+                                                 cudaMemcpyDeviceToHost, stream));
+            }
             QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
             const int32_t st = h_status[0], reached = h_status[1];
             QC_TRY(qc_graph_prepare_status(g, h_status[2]));
@@ -738,7 +800,18 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
                 QC_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ev.a, ev.b));
                 const int passes = reached - start + 1 + (start == 2 ? 1 : 0);
                 const double per_pass = qc_bfs_level_model_bytes(n, g->nnz, wn);
-                qc_record_kernel(ctx, "bfs_level", ms, passes * per_pass);
+                // compulsory HBM bytes: inputs once, histogram rows once, and per level the
+                // open rows' segments (read and written) beyond what L2 holds
+                double min_bytes = 4.0 * (n + 1) + 4.0 * (double)g->nnz   // CSR
+                                   + 4.0 * (n + 1) + 16.0 * n + 4.0 * n    // order, row bounds, components
+                                   + 16.0 * W                              // per-word component masks
+                                   + 4.0 * n * (reached - start + 1 + (start == 2 && w0 == 0 ? 2 : 0));
+                const double tile_segs = T > 1 ? (double)(R - 32 * (T - 1)) : (double)R;   // smallest tile
+                for (int l = start; l <= reached && (size_t)l < pulled_cap; ++l) {
+                    const double state = 32.0 * tile_segs * (double)h_pulled[l];
+                    if (state > (double)ctx->l2_bytes) min_bytes += state - (double)ctx->l2_bytes;
+                }
+                qc_record_kernel(ctx, "bfs_level", ms, passes * per_pass, min_bytes);
                 // stamp[l] opens level l (stamp[1] = launch start; the set-up covers levels 1-2);
                 // levels past the pinned block's room are left out of the per-level figures
                 const unsigned long long *h = h_stamp;
@@ -766,3 +839,46 @@ qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) {
     g->hist_valid = true;
     return QC_OK;
 }
+
+qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream) { return bfs_run(g, stream, true); }
+
+qc_status qc_bfs_enqueue(qc_graph *g, cudaStream_t stream) {
+    // timing mode reads each launch's figures, so it waits for every launch
+    return bfs_run(g, stream, g->ctx->timing.load() || g->nnz == 0);
+}
+
+qc_status qc_bfs_settle(qc_graph *g, cudaStream_t stream, bool *redone) {
+    *redone = false;
+    if (!g->bfs_queued) return QC_OK;
+    qc_ctx *ctx = g->ctx;
+    qc_pinned pin(ctx);
+    QC_TRY(pin.acquire());
+    int32_t *h = static_cast<int32_t *>(pin.ptr);
+    QC_CUDA_TRY(ctx, cudaMemcpyAsync(h, g->bfs_out.ptr, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    h[2] = 0;
+    if (!g->prep_checked)
+        QC_CUDA_TRY(ctx, cudaMemcpyAsync(h + 2, g->prep_ctl.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    g->bfs_queued = false;
+    const qc_status pst = qc_graph_prepare_status(g, h[2]);
+    if (pst != QC_OK) {
+        g->hist_valid = false;
+        return pst;
+    }
+    if (h[0] == ST_TIMEOUT) {
+        g->hist_valid = false;
+        qc_set_error(ctx, "BFS grid barrier timed out");
+        return QC_ERR_TIMEOUT;
+    }
+    if (h[0] == ST_NEED_ROWS) {
+        // a chunk ran out of histogram rows: run the BFS again from fresh rows,
+        // waiting for each launch (it grows the rows as it goes)
+        *redone = true;
+        g->hist.release();
+        g->hist_rows = 0;
+        return qc_bfs_histogram(g, stream);
+    }
+    g->D = h[1] - 1;
+    return QC_OK;
+}
+

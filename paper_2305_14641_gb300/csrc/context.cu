@@ -83,12 +83,13 @@ qc_status qc_event_pair::create(qc_ctx *ctx) {
     return QC_OK;
 }
 
-void qc_record_kernel(qc_ctx *ctx, const char *kernel, double ms, double model_bytes) {
+void qc_record_kernel(qc_ctx *ctx, const char *kernel, double ms, double model_bytes, double min_bytes) {
     std::lock_guard<std::mutex> lk(ctx->stats_mu);
     qc_kernel_stats &st = ctx->stats[kernel];
     st.launches += 1;
     st.total_ms += ms;
     st.model_bytes += model_bytes;
+    st.min_bytes += min_bytes;
 }
 
 // Words of sources per BFS chunk.  Every level of a chunk ends at a grid barrier
@@ -132,7 +133,7 @@ qc_status qc_context_kernel_stats(qc_ctx *ctx, const char *kernel, qc_kernel_sta
     if (!ctx || !kernel || !out) return QC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->stats_mu);
     auto it = ctx->stats.find(kernel);
-    *out = it == ctx->stats.end() ? qc_kernel_stats{0, 0.0, 0.0} : it->second;
+    *out = it == ctx->stats.end() ? qc_kernel_stats{0, 0.0, 0.0, 0.0} : it->second;
     if (reset && it != ctx->stats.end()) ctx->stats.erase(it);
     return QC_OK;
 }
@@ -326,8 +327,29 @@ qc_status qc_potential(qc_graph *g, const double *sigmas, int32_t n_sigma, doubl
         }
     cudaStream_t stream = qc_stream(stream_);
     QC_CUDA_TRY(g->ctx, cudaSetDevice(g->ctx->device));
-    if (!g->hist_valid) QC_TRY(qc_bfs_histogram(g, stream));
-    return qc_potential_from_hist(g, sigmas, n_sigma, V_out, stream);
+    if (!g->hist_valid) QC_TRY(qc_bfs_enqueue(g, stream));
+    const qc_status st = qc_potential_from_hist(g, sigmas, n_sigma, V_out, stream);
+    bool redone = false;
+    const qc_status settled = qc_bfs_settle(g, stream, &redone);
+    if (st != QC_OK) return st;
+    if (settled != QC_OK) return settled;
+    return redone ? qc_potential_from_hist(g, sigmas, n_sigma, V_out, stream) : QC_OK;
+}
+
+// Descent and roots queued on `stream`; roots per sigma counted into roots_dev.
+static qc_status ggd_enqueue(qc_graph *g, const double *V, int32_t n_sigma, int32_t *labels_out,
+                             int32_t *roots_dev, cudaStream_t stream) {
+    qc_ctx *ctx = g->ctx;
+    QC_CUDA_TRY(ctx, cudaMemsetAsync(roots_dev, 0, sizeof(int32_t) * (size_t)n_sigma, stream));
+    return qc_descend(ctx, g->n, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(),
+                      g->prepared ? g->order.as<int32_t>() : nullptr, V, n_sigma, labels_out, roots_dev, stream);
+}
+
+static qc_status read_roots(qc_ctx *ctx, const qc_buffer &roots, int32_t *n_clusters_out, cudaStream_t stream) {
+    if (!n_clusters_out) return QC_OK;
+    QC_CUDA_TRY(ctx, cudaMemcpyAsync(n_clusters_out, roots.ptr, roots.bytes, cudaMemcpyDeviceToHost, stream));
+    QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    return QC_OK;
 }
 
 qc_status qc_ggd_labels(qc_graph *g, const double *V, int32_t n_sigma, int32_t *labels_out,
@@ -342,31 +364,50 @@ qc_status qc_ggd_labels(qc_graph *g, const double *V, int32_t n_sigma, int32_t *
     QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     qc_buffer roots;
     QC_TRY(roots.allocate(ctx, sizeof(int32_t) * (size_t)n_sigma, stream));
-    QC_CUDA_TRY(ctx, cudaMemsetAsync(roots.ptr, 0, roots.bytes, stream));
-    QC_TRY(qc_descend(ctx, g->n, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(),
-                      g->prepared ? g->order.as<int32_t>() : nullptr, V, n_sigma,
-                      labels_out, roots.as<int32_t>(), stream));
-    if (n_clusters_out) {
-        QC_CUDA_TRY(ctx, cudaMemcpyAsync(n_clusters_out, roots.ptr, roots.bytes,
-                                         cudaMemcpyDeviceToHost, stream));
-        QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
-    }
-    return QC_OK;
+    QC_TRY(ggd_enqueue(g, V, n_sigma, labels_out, roots.as<int32_t>(), stream));
+    return read_roots(ctx, roots, n_clusters_out, stream);
 }
 
+// Algorithm 4: the BFS (when the histogram is not cached), potentials, descent
+// and roots are queued back to back; the BFS's outcome is read once at the end.
 qc_status qc_solve(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
                    int32_t *labels_out, int32_t *n_clusters_out, void *stream_) {
     qc_range range("qc.solve");
-    if (!g || !sigmas || n_sigma < 1 || !labels_out) return QC_ERR_INVALID_ARG;
+    if (!g || !sigmas || n_sigma < 1 || !labels_out) {
+        if (g) qc_set_error(g->ctx, "qc_solve: null pointer or n_sigma < 1");
+        return QC_ERR_INVALID_ARG;
+    }
+    for (int32_t s = 0; s < n_sigma; ++s)
+        if (!qc_sigma_ok(sigmas[s])) {
+            qc_set_error(g->ctx, "qc_solve: sigma[%d] = %g is not finite and > 0", s, sigmas[s]);
+            return QC_ERR_INVALID_ARG;
+        }
     cudaStream_t stream = qc_stream(stream_);
-    qc_buffer Vtmp;
+    qc_ctx *ctx = g->ctx;
+    QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    qc_buffer Vtmp, roots;
     double *V = V_out;
     if (!V) {
-        QC_TRY(Vtmp.allocate(g->ctx, sizeof(double) * (size_t)n_sigma * (size_t)g->n, stream));
+        QC_TRY(Vtmp.allocate(ctx, sizeof(double) * (size_t)n_sigma * (size_t)g->n, stream));
         V = Vtmp.as<double>();
     }
-    QC_TRY(qc_potential(g, sigmas, n_sigma, V, stream_));
-    return qc_ggd_labels(g, V, n_sigma, labels_out, n_clusters_out, stream_);
+    QC_TRY(roots.allocate(ctx, sizeof(int32_t) * (size_t)n_sigma, stream));
+    qc_status st = QC_OK;
+    if (!g->hist_valid) st = qc_bfs_enqueue(g, stream);
+    if (st == QC_OK) st = qc_potential_from_hist(g, sigmas, n_sigma, V, stream);
+    if (st == QC_OK) {
+        qc_range r2("qc.ggd");
+        st = ggd_enqueue(g, V, n_sigma, labels_out, roots.as<int32_t>(), stream);
+    }
+    bool redone = false;
+    const qc_status settled = qc_bfs_settle(g, stream, &redone);
+    if (st != QC_OK) return st;
+    if (settled != QC_OK) return settled;
+    if (redone) {
+        QC_TRY(qc_potential_from_hist(g, sigmas, n_sigma, V, stream));
+        QC_TRY(ggd_enqueue(g, V, n_sigma, labels_out, roots.as<int32_t>(), stream));
+    }
+    return read_roots(ctx, roots, n_clusters_out, stream);
 }
 
 }  // extern "C"

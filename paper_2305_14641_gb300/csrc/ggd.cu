@@ -153,25 +153,30 @@ parent_fn pick_parent(int sn) {
 
 }  // namespace
 
+qc_status qc_descend_into(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                          const int32_t *order, const double *V, int32_t n_sigma, int32_t *labels,
+                          int32_t *n_roots_dev, int32_t *parent, long long *keys, cudaStream_t stream) {
+    key_transpose<<<dim3(qc_ceil_div(n, 32), qc_ceil_div(n_sigma, 32)), dim3(32, 8), 0, stream>>>(
+        n, n_sigma, V, keys);
+    QC_LAUNCHED(ctx);
+    const int wblocks = qc_ceil_div(n, 8) < 16 * ctx->num_sms ? qc_ceil_div(n, 8) : 16 * ctx->num_sms;
+    for (int32_t s0 = 0; s0 < n_sigma; s0 += 16) {
+        const int32_t sn = (n_sigma - s0) < 16 ? (n_sigma - s0) : 16;
+        pick_parent(sn)<<<wblocks, 256, 0, stream>>>(n, row_ptr, col_idx, keys, n_sigma, s0, sn, order, parent);
+        QC_LAUNCHED(ctx);
+    }
+    const int blocks = qc_ceil_div(n, 256) < 2 * ctx->num_sms ? qc_ceil_div(n, 256) : 2 * ctx->num_sms;
+    find_roots_kernel<<<dim3(blocks, n_sigma), 256, 0, stream>>>(n, parent, labels, n_roots_dev);
+    QC_LAUNCHED(ctx);
+    return QC_OK;
+}
+
 qc_status qc_descend(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                      const int32_t *order, const double *V, int32_t n_sigma, int32_t *labels,
                      int32_t *n_roots_dev, cudaStream_t stream) {
     qc_buffer parent, keys;
     QC_TRY(parent.allocate(ctx, sizeof(int32_t) * (size_t)n * (size_t)n_sigma, stream));
     QC_TRY(keys.allocate(ctx, sizeof(long long) * (size_t)n * (size_t)n_sigma, stream));
-    key_transpose<<<dim3(qc_ceil_div(n, 32), qc_ceil_div(n_sigma, 32)), dim3(32, 8), 0, stream>>>(
-        n, n_sigma, V, keys.as<long long>());
-    QC_LAUNCHED(ctx);
-    const int wblocks = qc_ceil_div(n, 8) < 16 * ctx->num_sms ? qc_ceil_div(n, 8) : 16 * ctx->num_sms;
-    for (int32_t s0 = 0; s0 < n_sigma; s0 += 16) {
-        const int32_t sn = (n_sigma - s0) < 16 ? (n_sigma - s0) : 16;
-        pick_parent(sn)<<<wblocks, 256, 0, stream>>>(n, row_ptr, col_idx, keys.as<long long>(), n_sigma,
-                                                     s0, sn, order, parent.as<int32_t>());
-        QC_LAUNCHED(ctx);
-    }
-    const int blocks = qc_ceil_div(n, 256) < 2 * ctx->num_sms ? qc_ceil_div(n, 256) : 2 * ctx->num_sms;
-    find_roots_kernel<<<dim3(blocks, n_sigma), 256, 0, stream>>>(n, parent.as<int32_t>(), labels,
-                                                                 n_roots_dev);
-    QC_LAUNCHED(ctx);
-    return QC_OK;
+    return qc_descend_into(ctx, n, row_ptr, col_idx, order, V, n_sigma, labels, n_roots_dev,
+                           parent.as<int32_t>(), keys.as<long long>(), stream);
 }

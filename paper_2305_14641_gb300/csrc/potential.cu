@@ -26,12 +26,19 @@ namespace {
 
 // One thread per (sigma, node); hist is level-major so a warp reads 32
 // consecutive counts per level.  tables: w[s][d], u[s][d] for d = 0..D, den[s] = 2 sigma^2.
-__global__ void potential_kernel(int32_t n, int32_t D, const int32_t *__restrict__ hist,
+// The largest distance: D, or (when the BFS that fills hist is still queued ahead
+// on the stream) the one the BFS recorded, D_dev[0] - 1, at most D.
+__device__ __forceinline__ int32_t distance_bound(int32_t D, const int32_t *D_dev) {
+    return D_dev ? max(0, min(D, *D_dev - 1)) : D;
+}
+
+__global__ void potential_kernel(int32_t n, int32_t Dmax, const int32_t *D_dev, const int32_t *__restrict__ hist,
                                  const double *__restrict__ w, const double *__restrict__ u,
                                  const double *__restrict__ den, double *__restrict__ V) {
     const int s = blockIdx.y;
-    const double *ws = w + (size_t)s * (D + 1);
-    const double *us = u + (size_t)s * (D + 1);
+    const double *ws = w + (size_t)s * (Dmax + 1);
+    const double *us = u + (size_t)s * (Dmax + 1);
+    const int32_t D = distance_bound(Dmax, D_dev);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         double sum1 = 0.0, sum2 = 0.0;
         for (int d = 0; d <= D; ++d) {
@@ -45,19 +52,22 @@ __global__ void potential_kernel(int32_t n, int32_t D, const int32_t *__restrict
     }
 }
 
-// Small tables travel as a kernel parameter (no copy, no synchronisation).
-constexpr int INLINE_DOUBLES = 448;
+// Small tables travel as a kernel parameter (no copy, no synchronisation): 16
+// sigma values over 32 distances fit.
+constexpr int INLINE_DOUBLES = 1040;
 struct InlineTables {
     double t[INLINE_DOUBLES];      // w[s][d], then u[s][d], then den[s]
 };
 
-__global__ void potential_kernel_inline(int32_t n, int32_t D, int32_t S, const int32_t *__restrict__ hist,
+__global__ void potential_kernel_inline(int32_t n, int32_t Dmax, const int32_t *D_dev, int32_t S,
+                                        const int32_t *__restrict__ hist,
                                         const __grid_constant__ InlineTables tab, double *__restrict__ V) {
     const int s = blockIdx.y;
-    const int L = D + 1;
+    const int L = Dmax + 1;
     const double *ws = tab.t + s * L;
     const double *us = tab.t + S * L + s * L;
     const double den = tab.t[2 * S * L + s];
+    const int32_t D = distance_bound(Dmax, D_dev);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         double sum1 = 0.0, sum2 = 0.0;
         for (int d = 0; d <= D; ++d) {
@@ -131,34 +141,54 @@ extern "C" qc_status qc_potential_adjacency(qc_graph *g, const double *sigmas, i
     return QC_OK;
 }
 
-qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V,
-                                 cudaStream_t stream) {
-    qc_range range("qc.potential");
-    qc_ctx *ctx = g->ctx;
-    const int32_t L = g->D + 1;
-    std::vector<double> tab((size_t)n_sigma * (2 * L + 1));
+void qc_potential_tables(const double *sigmas, int32_t n_sigma, int32_t L, std::vector<double> &tab) {
+    tab.assign((size_t)n_sigma * (2 * L + 1), 0.0);
     double *w = tab.data(), *u = w + (size_t)n_sigma * L, *den = u + (size_t)n_sigma * L;
     for (int32_t s = 0; s < n_sigma; ++s) {
         qc_weight_table(sigmas[s], L, w + (size_t)s * L, u + (size_t)s * L);
         den[s] = 2.0 * (sigmas[s] * sigmas[s]);
     }
-    dim3 grid(qc_ceil_div(g->n, 256) < 2 * ctx->num_sms ? qc_ceil_div(g->n, 256) : 2 * ctx->num_sms,
-              n_sigma);
-    if (tab.size() <= (size_t)INLINE_DOUBLES) {
+}
+
+bool qc_potential_tables_inline(int32_t n_sigma, int32_t L) {
+    return (size_t)n_sigma * (2 * L + 1) <= (size_t)INLINE_DOUBLES;
+}
+
+qc_status qc_potential_launch(qc_ctx *ctx, int32_t n, const int32_t *hist, int32_t Dmax, const int32_t *D_dev,
+                              int32_t n_sigma, const std::vector<double> &tab, const double *dtab, double *V,
+                              cudaStream_t stream) {
+    const int32_t L = Dmax + 1;
+    dim3 grid(qc_ceil_div(n, 256) < 2 * ctx->num_sms ? qc_ceil_div(n, 256) : 2 * ctx->num_sms, n_sigma);
+    if (qc_potential_tables_inline(n_sigma, L)) {
         InlineTables it;
         std::copy(tab.begin(), tab.end(), it.t);
-        potential_kernel_inline<<<grid, 256, 0, stream>>>(g->n, g->D, n_sigma, g->hist.as<int32_t>(), it, V);
-        QC_LAUNCHED(ctx);
-        return QC_OK;
+        potential_kernel_inline<<<grid, 256, 0, stream>>>(n, Dmax, D_dev, n_sigma, hist, it, V);
+    } else {
+        potential_kernel<<<grid, 256, 0, stream>>>(n, Dmax, D_dev, hist, dtab, dtab + (size_t)n_sigma * L,
+                                                   dtab + 2 * (size_t)n_sigma * L, V);
     }
+    QC_LAUNCHED(ctx);
+    return QC_OK;
+}
+
+qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V,
+                                 cudaStream_t stream) {
+    qc_range range("qc.potential");
+    qc_ctx *ctx = g->ctx;
+    // while the BFS is still queued ahead, D is known on the device only: the
+    // tables cover every histogram row and the kernel stops at the recorded D
+    const int32_t Dmax = g->bfs_queued ? g->hist_rows - 1 : g->D;
+    const int32_t *D_dev = g->bfs_queued ? g->bfs_out.as<int32_t>() + 1 : nullptr;
+    const int32_t L = Dmax + 1;
+    std::vector<double> tab;
+    qc_potential_tables(sigmas, n_sigma, L, tab);
+    if (qc_potential_tables_inline(n_sigma, L))
+        return qc_potential_launch(ctx, g->n, g->hist.as<int32_t>(), Dmax, D_dev, n_sigma, tab, nullptr, V, stream);
     qc_buffer dtab;
     QC_TRY(dtab.allocate(ctx, sizeof(double) * tab.size(), stream));
     QC_CUDA_TRY(ctx, cudaMemcpyAsync(dtab.ptr, tab.data(), dtab.bytes, cudaMemcpyHostToDevice, stream));
     // the host table must outlive the asynchronous copy
     QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
-    const double *dw = dtab.as<double>();
-    potential_kernel<<<grid, 256, 0, stream>>>(g->n, g->D, g->hist.as<int32_t>(), dw,
-                                               dw + (size_t)n_sigma * L, dw + 2 * (size_t)n_sigma * L, V);
-    QC_LAUNCHED(ctx);
-    return QC_OK;
+    return qc_potential_launch(ctx, g->n, g->hist.as<int32_t>(), Dmax, D_dev, n_sigma, tab, dtab.as<double>(), V,
+                               stream);
 }

@@ -11,15 +11,26 @@ namespace qcdev {
 
 enum : int32_t { ST_DONE = 0, ST_NEED_ROWS = 1, ST_TIMEOUT = 2 };
 
-// ~100 ns per spin: more than a second before a wait gives up.
-constexpr unsigned long long BARRIER_SPINS = 1ull << 24;
+// A grid-barrier wait gives up once this much time has passed on the GPU's
+// global timer (the longest level of any launch here takes milliseconds).
+constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;
+// Backstop in case the global timer does not advance: polls of >= 100 ns each.
+constexpr unsigned long long BARRIER_MAX_POLLS = 1ull << 27;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).
-// bar[0] counts arrivals, bar[1] is the generation.  The spin is bounded: on
-// expiry the block records ST_TIMEOUT in *status and returns false; every
-// block then leaves at its next barrier.
+// bar[0] counts arrivals, bar[1] is the generation.  The wait is bounded: once
+// timeout_ns has passed (global timer) the block records ST_TIMEOUT in *status
+// and returns false; every block then leaves at its next barrier.  When
+// waited_ns is given, thread 0 of a block that waited stores how long it did.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *status,
-                                             unsigned long long spin_limit = BARRIER_SPINS) {
+                                             unsigned long long timeout_ns = BARRIER_TIMEOUT_NS,
+                                             unsigned long long *waited_ns = nullptr) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -33,15 +44,18 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *status,
             __threadfence();
             atomicAdd(bar + 1, 1u);
         } else {
-            unsigned long long spins = 0;
+            const unsigned long long t0 = global_ns();
+            unsigned long long polls = 0, now = t0;
             while (*vgen == gen) {
-                if (++spins > spin_limit) {
+                now = global_ns();
+                if (now - t0 > timeout_ns || ++polls > BARRIER_MAX_POLLS) {
                     atomicExch(status, ST_TIMEOUT);
                     ok = 0;
                     break;
                 }
                 __nanosleep(100);
             }
+            if (waited_ns) *waited_ns = now - t0;
         }
         __threadfence();
         ok_s = ok && (*(volatile int32_t *)status != ST_TIMEOUT);

@@ -91,7 +91,7 @@ struct qc_range {
         QC_CUDA_TRY((ctx), cudaGetLastError());                                         \
     } while (0)
 
-void qc_record_kernel(qc_ctx *ctx, const char *kernel, double ms, double model_bytes);
+void qc_record_kernel(qc_ctx *ctx, const char *kernel, double ms, double model_bytes, double min_bytes = 0.0);
 
 void qc_set_error(qc_ctx *ctx, const char *fmt, ...);
 
@@ -163,6 +163,8 @@ struct qc_graph {
     int32_t D = 0;           // largest finite hop distance
     int32_t hist_rows = 0;   // allocated rows of hist
     qc_buffer hist;          // int32[hist_rows][n], level-major
+    bool bfs_queued = false; // a BFS was queued and its outcome not yet read (qc_bfs_settle)
+    qc_buffer bfs_out;       // int32[8]: BFS outcome, [0] state, [1] highest level reached
     // preparation (see prep.cu), computed once
     bool prepared = false;
     bool prep_checked = false;   // the components launch's status has been read
@@ -192,8 +194,32 @@ int32_t qc_bfs_chunk_words(const qc_ctx *ctx, int32_t n);
 
 // ---- entry points implemented per translation unit ---------------------------------
 
-// bfs.cu: all-source bitset BFS + histogram into g->hist (sets D, hist_valid).
+// bfs.cu: scratch of one all-source BFS (every chunk reuses it).
+struct qc_bfs_scratch {
+    int32_t wc = 0, R_max = 0, T_max = 0;   // source words per chunk, row segments, tiles
+    bool masks = false;                     // variant: change masks
+    int32_t mask_ratio = 0;
+    qc_buffer visA, visB, sat, ctl, wl, fmask;
+};
+qc_status qc_bfs_scratch_init(qc_graph *g, qc_bfs_scratch &bs, cudaStream_t stream);
+// Queue one launch of the BFS kernel: the chunk of source words from w0, from
+// level `start` (2 = fresh), adding into hist[rows][n], outcome in out[0..1]
+// (reset first when reset_out).  The graph must be prepared.
+qc_status qc_bfs_launch(qc_graph *g, qc_bfs_scratch &bs, int32_t w0, int32_t start, int32_t *hist, int32_t rows,
+                        int32_t *out, bool reset_out, unsigned long long *stamps, cudaStream_t stream);
+// bfs.cu: all-source bitset BFS + histogram into g->hist (sets D, hist_valid),
+// waiting for every launch.
 qc_status qc_bfs_histogram(qc_graph *g, cudaStream_t stream);
+// The same BFS with every launch queued and nothing waited for (timing mode and
+// graphs without edges still wait): g->hist is valid for work queued behind it on
+// `stream`, but D is known on the device only (g->bfs_out[1] - 1) until
+// qc_bfs_settle reads the outcome.  Every call that queues it settles before it
+// returns.
+qc_status qc_bfs_enqueue(qc_graph *g, cudaStream_t stream);
+// Wait for `stream` and read a queued BFS's outcome: sets D, or returns its
+// error; when a launch ran out of histogram rows the BFS is run again (waiting)
+// and *redone is set, so that work queued on the old rows must be queued again.
+qc_status qc_bfs_settle(qc_graph *g, cudaStream_t stream, bool *redone);
 
 // potential.cu: V[s][v] from the cached histogram.
 qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V,
@@ -203,12 +229,27 @@ qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_si
 void qc_weight_table(double sigma, int32_t len, double *w, double *u);
 // Check sigma: finite and > 0.
 bool qc_sigma_ok(double sigma);
+// Tables of the potential kernel for sigmas over distances 0..L-1: w[s][d], then
+// u[s][d], then den[s] = 2 sigma^2.
+void qc_potential_tables(const double *sigmas, int32_t n_sigma, int32_t L, std::vector<double> &tab);
+// Whether such tables travel as a kernel parameter (else they are read from a device copy).
+bool qc_potential_tables_inline(int32_t n_sigma, int32_t L);
+// Queue the potential kernel over hist[Dmax+1][n] (D_dev: the BFS's outcome words
+// + 1 when D is known on the device only, else null); dtab: device copy of tab
+// when the tables do not travel inline.
+qc_status qc_potential_launch(qc_ctx *ctx, int32_t n, const int32_t *hist, int32_t Dmax, const int32_t *D_dev,
+                              int32_t n_sigma, const std::vector<double> &tab, const double *dtab, double *V,
+                              cudaStream_t stream);
 
 // ggd.cu: parents and roots.
 // order: nodes heaviest first (the graph's preparation) or NULL for 0..n-1.
 qc_status qc_descend(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                      const int32_t *order, const double *V, int32_t n_sigma, int32_t *labels,
                      int32_t *n_roots_dev, cudaStream_t stream);
+// The same with caller-provided scratch: parent int32[n_sigma][n], keys int64[n][n_sigma].
+qc_status qc_descend_into(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                          const int32_t *order, const double *V, int32_t n_sigma, int32_t *labels,
+                          int32_t *n_roots_dev, int32_t *parent, long long *keys, cudaStream_t stream);
 
 // batch.cu: the graph-per-CTA kernel without a plan (used by the serving loop)
 struct qc_cta_launch;

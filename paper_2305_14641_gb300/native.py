@@ -49,7 +49,7 @@ class qc_request_info(ctypes.Structure):
 
 class qc_kernel_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
-                ("model_bytes", ctypes.c_double)]
+                ("model_bytes", ctypes.c_double), ("min_bytes", ctypes.c_double)]
 
 
 STATUS = {0: "QC_OK", 1: "QC_ERR_INVALID_ARG", 2: "QC_ERR_INVALID_GRAPH", 3: "QC_ERR_OOM",
@@ -107,9 +107,16 @@ SIGNATURES = [
     ("qc_server_cancel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     ("qc_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qc_server_stats)]),
     ("qc_server_destroy", None, [ctypes.c_void_p]),
-    ("qc_selftest_barrier_timeout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    ("qc_sweep_create", ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, c_void_pp]),
+    ("qc_sweep_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, c_int32_p, ctypes.c_void_p]),
+    ("qc_sweep_info", ctypes.c_int, [ctypes.c_void_p, c_int32_p, c_int32_p, c_int64_p]),
+    ("qc_sweep_destroy", None, [ctypes.c_void_p]),
+    ("qc_selftest_barrier_timeout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, c_int64_p, ctypes.c_void_p]),
     ("qc_selftest_arith", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    ("qc_selftest_l2_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, c_double_p,
+                                            ctypes.c_void_p]),
     ("qc_histogram_static_scratch", ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                                    c_int32_p, ctypes.c_void_p]),

