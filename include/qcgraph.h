@@ -353,6 +353,16 @@ qc_status qc_server_create(qc_ctx *ctx, const qc_server_config *cfg, qc_server *
  * as the request's own status (QC_ERR_INVALID_GRAPH from poll / wait). */
 qc_status qc_server_submit(qc_server *s, int32_t n, int64_t nnz, const int32_t *row_ptr,
                            const int32_t *col_idx, double sigma, uint64_t *req_id);
+/* Queue one request on a graph already resident on the GPU (qc_graph_create on
+ * the server's context) and its sigma: the form of Algorithm 4's input that
+ * keeps the CSR, and after the first request the graph's histogram, on the
+ * device across requests, so a later sigma on the same graph needs no BFS.  The
+ * graph is only read (several requests on one graph run one after another on
+ * the single-graph path); it must outlive its requests, and the caller must not
+ * use it while they are pending.
+ * Errors: QC_ERR_INVALID_ARG (null, bad sigma, a graph of another context),
+ * QC_ERR_BUDGET. */
+qc_status qc_server_submit_graph(qc_server *s, qc_graph *g, double sigma, uint64_t *req_id);
 /* Non-blocking: *done = 1 and labels_out (host int32[n], root node ids),
  * *n_clusters and *info filled when the request has completed, else *done = 0.
  * labels_out, n_clusters and info may each be NULL.  A completed request's
@@ -400,6 +410,22 @@ qc_status qc_selftest_barrier_timeout(qc_ctx *ctx, int64_t timeout_us, int64_t *
 enum { QC_ARITH_EXP_NEG = 0 };
 qc_status qc_selftest_arith(qc_ctx *ctx, int32_t op, const double *x, const double *y, double *out, int64_t n,
                             void *stream);
+
+/* ---- self-test of the debug build ------------------------------------------------------ */
+
+/* The paper has no counterpart to this call.  The library has a debug build
+ * (libqcgraph_debug.so, the same sources compiled with QC_DEBUG) in which every
+ * neighbour id a kernel reads from the CSR is checked against [0, n) before it
+ * is used: a failed check is recorded in a device word, the id is replaced by
+ * 0, and the next call that waits for the GPU returns QC_ERR_INVALID_GRAPH
+ * naming the kernel, instead of the GPU reading out of bounds.  Release builds
+ * leave the checks out.  This call passes `id` through that check (it is never
+ * used as an address) and returns what came out in *checked_out (id itself, or
+ * 0 in the debug build when id is outside [0, n)); *debug_build says which
+ * build answered.  Returns QC_ERR_INVALID_GRAPH when the check failed (debug
+ * build only), QC_OK otherwise.  Errors: QC_ERR_INVALID_ARG, QC_ERR_CUDA. */
+qc_status qc_selftest_debug_check(qc_ctx *ctx, int32_t id, int32_t n, int32_t *checked_out, int32_t *debug_build,
+                                  void *stream);
 
 /* ---- L2 read bandwidth probe ---------------------------------------------------------- */
 

@@ -110,6 +110,14 @@ class Context:
         float64 device tensor."""
         return self._selftest_arith(0, t, None, stream)
 
+    def selftest_debug_check(self, node_id: int, n: int, stream=None) -> tuple[str, int, bool]:
+        """Pass node_id through the debug build's bounds check against [0, n) (never as an
+        address); returns (status name, the id that came out, whether this is the debug build)."""
+        out, dbg = ctypes.c_int32(-1), ctypes.c_int32(-1)
+        st = self._lib.qc_selftest_debug_check(self.handle, int(node_id), int(n), ctypes.byref(out), ctypes.byref(dbg),
+                                               _stream_handle(stream))
+        return native.STATUS.get(st, str(st)), int(out.value), bool(dbg.value)
+
     def l2_read_gbs(self, nbytes: int = 48 << 20, random_segments: bool = False, stream=None) -> float:
         """Read throughput (GB/s) of an nbytes buffer read through L2 only, streamed or
         as random 512-byte segments (the BFS gather pattern)."""
@@ -432,6 +440,15 @@ class Server:
                                                       ci.ctypes.data if len(ci) else None, float(sigma),
                                                       ctypes.byref(rid)))
         self._n[rid.value] = len(rp) - 1
+        return rid.value
+
+    def submit_graph(self, graph: "Graph", sigma: float) -> int:
+        """Queue a request on a graph resident on the GPU (made with Graph(server.ctx, ...));
+        later sigmas on the same graph reuse its cached histogram."""
+        rid = ctypes.c_uint64()
+        self.ctx.check(self.ctx._lib.qc_server_submit_graph(self.handle, graph.handle, float(sigma),
+                                                            ctypes.byref(rid)))
+        self._n[rid.value] = graph.n
         return rid.value
 
     def _result(self, rid, labels, nc, info):

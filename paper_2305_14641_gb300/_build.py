@@ -16,6 +16,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqcgraph.so")
+# debug build: every neighbour id a kernel reads is bounds-checked (QC_DEBUG); one
+# device error word shared by all translation units, hence relocatable device code
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libqcgraph_debug.so")
+DEBUG_FLAGS = ["-DQC_DEBUG", "-rdc=true"]
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,22 +44,25 @@ def _deps() -> list[str]:
     return sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          debug: bool = False) -> str:
+    """Compile libqcgraph.so (debug: libqcgraph_debug.so, bounds-checked)."""
+    lib, build_dir = (LIB_DEBUG, BUILD_DEBUG) if debug else (LIB, BUILD)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    flags = NVCC_FLAGS + (DEBUG_FLAGS if debug else []) + list(extra_flags or [])
     jobs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         jobs.append((src, obj, [cc] + flags + ["-c", src, "-o", obj]))
 
     def run(job):
@@ -70,15 +78,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
         for (src, _, _), log in zip(jobs, logs):
             if log.strip():
                 print(f"--- {os.path.basename(src)}\n{log}")
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for _, o, _ in jobs] + ["-lcudart_static", "-lpthread", "-ldl", "-lrt"]
+    tmp = lib + f".{os.getpid()}.tmp"
+    cmd = ([cc] + ARCH + (["-rdc=true"] if debug else []) + ["-shared", "-o", tmp] + [o for _, o, _ in jobs] +
+           ["-lcudart_static", "-lpthread", "-ldl", "-lrt"])
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
-        raise RuntimeError(f"link of libqcgraph.so failed:\n{res.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+        raise RuntimeError(f"link of {os.path.basename(lib)} failed:\n{res.stderr}")
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -113,7 +113,7 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
     // 1. components: L[v] names a node of v's component with id <= v
     for (int v = tid; v < n; v += nthr) {
         int m = v;
-        for (int e = rp[v]; e < rp[v + 1]; ++e) m = min(m, ci[e]);
+        for (int e = rp[v]; e < rp[v + 1]; ++e) m = min(m, qcdev::checked_id(ci[e], n, qcdev::DBG_BATCH));
         L[v] = m;
     }
     __syncthreads();
@@ -132,7 +132,7 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
         for (int v = wid; v < n; v += nw) {
             const int a = VL[v];
             for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
-                const int b = VL[ci[e]];
+                const int b = VL[qcdev::checked_id(ci[e], n, qcdev::DBG_BATCH)];
                 if (b < a) {
                     if (atomicMin(L + a, b) > b) changed = true;
                 } else if (G.directed && a < b) {
@@ -170,7 +170,7 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
         for (int v = wid; v < n; v += nw) {
             const int beg = rp[v], end = rp[v + 1];
             for (int e = beg + lane; e <= end; e += 32) {
-                const int u = (e == end) ? v : ci[e];
+                const int u = (e == end) ? v : qcdev::checked_id(ci[e], n, qcdev::DBG_BATCH);
                 const int k = (u >> 6) - c0;
                 if (k >= 0 && k < cw)
                     atomicOr((unsigned long long *)&colA[(size_t)v * P.c + k], 1ull << (u & 63));
@@ -203,7 +203,7 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
                     }
                     if (!full) {
                         for (int e = rp[v]; e < rp[v + 1]; ++e) {
-                            const uint64_t *nrow = in + (size_t)ci[e] * P.c;
+                            const uint64_t *nrow = in + (size_t)qcdev::checked_id(ci[e], n, qcdev::DBG_BATCH) * P.c;
 #pragma unroll
                             for (int k = 0; k < MAXC; ++k)
                                 if (k < cw) acc[k] |= nrow[k];
@@ -236,7 +236,7 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
                 if (!full) {
                     const int beg = rp[v], end = rp[v + 1];
                     for (int e = beg + lane; e < end; e += 32) {
-                        const uint64_t *nrow = in + (size_t)ci[e] * P.c;
+                        const uint64_t *nrow = in + (size_t)qcdev::checked_id(ci[e], n, qcdev::DBG_BATCH) * P.c;
 #pragma unroll
                         for (int k = 0; k < MAXC; ++k)
                             if (k < cw) acc[k] |= nrow[k];
@@ -296,7 +296,7 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
             long long bk = 0;
             int best = -1;
             for (int e = rp[v]; e < rp[v + 1]; ++e) {
-                const int x = ci[e];
+                const int x = qcdev::checked_id(ci[e], n, qcdev::DBG_BATCH);
                 const long long k = key[x];
                 if (best < 0 || k < bk || (k == bk && x < best)) {
                     bk = k;
@@ -310,7 +310,7 @@ __device__ void solve_graph(const CtaParams &P, const int g, unsigned char *smem
         long long bk = 0;
         int best = -1;
         for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) {
-            const int x = ci[e];
+            const int x = qcdev::checked_id(ci[e], n, qcdev::DBG_BATCH);
             const long long k = key[x];
             if (best < 0 || k < bk || (k == bk && x < best)) {
                 bk = k;
@@ -709,6 +709,7 @@ qc_status qc_batch_run(qc_batch *b, int32_t *n_clusters_out, void *stream_) {
         QC_CUDA_TRY(ctx, cudaMemcpyAsync(h, b->flags.as<int32_t>() + b->n_cta, sizeof(int32_t),
                                          cudaMemcpyDeviceToHost, stream));
         QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        QC_TRY(qc_debug_take(ctx));
         if (h[0]) {
             std::vector<int32_t> f(b->n_cta);
             QC_CUDA_TRY(ctx, cudaMemcpy(f.data(), b->flags.ptr, sizeof(int32_t) * b->n_cta,

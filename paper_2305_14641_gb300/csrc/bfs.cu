@@ -180,7 +180,7 @@ __device__ void init_bits(const BfsParams &p) {
         unsigned long long *row = words + (size_t)v * stride;
         const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
         for (int e = beg + lane; e <= end; e += 32) {
-            const int u = (e == end) ? v : p.col_idx[e];
+            const int u = (e == end) ? v : qcdev::checked_id(p.col_idx[e], p.n, qcdev::DBG_BFS);
             const int k = (u >> 6) - p.w0;
             if (k >= 0 && k < p.wn) {
                 atomicOr(row + k, 1ull << (u & 63));
@@ -228,7 +228,7 @@ __device__ __forceinline__ ulonglong2 gather_or(const BfsParams &p, const int le
     for (int j0 = j_first; j0 < end; j0 += stride) {
         if (!__any_sync(FULL, act)) break;
         const int cnt = min(32, end - j0);
-        const int myu = (have0 && j0 == j_first) ? myu0 : ((lane < cnt) ? p.col_idx[j0 + lane] : 0);
+        const int myu = (have0 && j0 == j_first) ? myu0 : ((lane < cnt) ? qcdev::checked_id(p.col_idx[j0 + lane], p.n, qcdev::DBG_BFS) : 0);
         if (G == 32 && MASKS && masked) {
             const uint32_t fm = (lane < cnt) ? p.fmask[(level - 1) & 1][(size_t)myu * p.T + t] : 0u;
             const unsigned nz = __ballot_sync(FULL, fm != 0u);
@@ -434,7 +434,7 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
                 const int beg = __shfl_sync(FULL, beg_l, b);
                 const int len = __shfl_sync(FULL, end_l, b) - beg;
                 x.own = (q < p.R) ? vin[(size_t)v * p.R + q] : make_ulonglong2(ONES, ONES);
-                x.myu = (lane < len) ? p.col_idx[beg + lane] : 0;
+                x.myu = (lane < len) ? qcdev::checked_id(p.col_idx[beg + lane], p.n, qcdev::DBG_BFS) : 0;
             };
             Item cur, nxt;
             if (mask) fetch(__ffs(mask) - 1, cur);
@@ -467,7 +467,7 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
                 x.end = __shfl_sync(FULL, end_l, b);
                 const int q = x.t * 32 + ql;
                 x.own = (q < p.R) ? vin[(size_t)x.v * p.R + q] : make_ulonglong2(ONES, ONES);
-                x.myu = (lane < x.end - x.beg) ? p.col_idx[x.beg + lane] : 0;
+                x.myu = (lane < x.end - x.beg) ? qcdev::checked_id(p.col_idx[x.beg + lane], p.n, qcdev::DBG_BFS) : 0;
             };
             Item cur, nxt;
             if (mask) fetch(__ffs(mask) - 1, cur);
@@ -793,6 +793,7 @@ static qc_status bfs_run(qc_graph *g, cudaStream_t stream, bool sync) {
                                                  cudaMemcpyDeviceToHost, stream));
             }
             QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+            QC_TRY(qc_debug_take(ctx));
             const int32_t st = h_status[0], reached = h_status[1];
             QC_TRY(qc_graph_prepare_status(g, h_status[2]));
             if (timing) {
@@ -860,6 +861,11 @@ qc_status qc_bfs_settle(qc_graph *g, cudaStream_t stream, bool *redone) {
         QC_CUDA_TRY(ctx, cudaMemcpyAsync(h + 2, g->prep_ctl.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
     QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
     g->bfs_queued = false;
+    const qc_status dst = qc_debug_take(ctx);
+    if (dst != QC_OK) {
+        g->hist_valid = false;
+        return dst;
+    }
     const qc_status pst = qc_graph_prepare_status(g, h[2]);
     if (pst != QC_OK) {
         g->hist_valid = false;

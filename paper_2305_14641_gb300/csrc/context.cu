@@ -349,7 +349,7 @@ static qc_status read_roots(qc_ctx *ctx, const qc_buffer &roots, int32_t *n_clus
     if (!n_clusters_out) return QC_OK;
     QC_CUDA_TRY(ctx, cudaMemcpyAsync(n_clusters_out, roots.ptr, roots.bytes, cudaMemcpyDeviceToHost, stream));
     QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
-    return QC_OK;
+    return qc_debug_take(ctx);
 }
 
 qc_status qc_ggd_labels(qc_graph *g, const double *V, int32_t n_sigma, int32_t *labels_out,

@@ -22,6 +22,7 @@
 // interleaving still ends at the same root.  The root goes to a separate label
 // array: a halving write by another walker may still replace parent[v] after v
 // found its root, so the parent array itself is not the answer.
+#include "qc_device.cuh"
 #include "qc_internal.h"
 
 namespace {
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(256) ggd_parent_kernel(int32_t n, const int32_
         int best = -1;
         for (int j0 = beg; j0 < end; j0 += 32) {
             const int cnt = min(32, end - j0);
-            const int myu = (lane < cnt) ? col_idx[j0 + lane] : 0;
+            const int myu = (lane < cnt) ? qcdev::checked_id(col_idx[j0 + lane], n, qcdev::DBG_GGD) : 0;
             for (int m = 0; m < cnt; m += SLOTS * U) {
                 long long x[U];
                 int uu[U];

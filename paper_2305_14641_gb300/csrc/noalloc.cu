@@ -25,6 +25,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "qc_device.cuh"
 #include "qc_internal.h"
 
 #define QC_STATIC_SCRATCH_BYTES (16u << 20)
@@ -56,7 +57,7 @@ __global__ void sa_init(int32_t n, const int32_t *row_ptr, const int32_t *col_id
         int k = (v >> 6) - w0;
         if (k >= 0 && k < wn) row[k] |= 1ull << (v & 63);
         for (int e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
-            const int u = col_idx[e];
+            const int u = qcdev::checked_id(col_idx[e], n, qcdev::DBG_NOALLOC);
             k = (u >> 6) - w0;
             if (k >= 0 && k < wn) row[k] |= 1ull << (u & 63);
         }
@@ -82,7 +83,7 @@ __global__ void sa_level(int32_t n, const int32_t *row_ptr, const int32_t *col_i
             const ulonglong2 own = mine ? vin[(size_t)v * R + q] : make_ulonglong2(ONES, ONES);
             ulonglong2 acc = make_ulonglong2(0, 0);
             for (int e = beg; e < end; ++e) {
-                const int u = col_idx[e];
+                const int u = qcdev::checked_id(col_idx[e], n, qcdev::DBG_NOALLOC);
                 if (mine) {
                     const ulonglong2 x = vin[(size_t)u * R + q];
                     acc.x |= x.x;
@@ -194,6 +195,7 @@ extern "C" qc_status qc_histogram_static_scratch(int32_t n, int64_t nnz, const i
         }
     }
     if (cudaStreamSynchronize(stream) != cudaSuccess) return QC_ERR_CUDA;
+    QC_TRY(qc_debug_take(nullptr));
     *D_out = D;
     return QC_OK;
 }

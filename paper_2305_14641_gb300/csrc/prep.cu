@@ -15,6 +15,8 @@
 // as soon as v's own component has reached it.  For a directed graph the
 // components are the weakly connected ones: still a bound on reachability, but
 // a row may then never complete.
+#include <algorithm>
+
 #include "qc_device.cuh"
 #include "qc_internal.h"
 
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(256) cc_afforest(int32_t n, const int32_t *row
     for (int r = 0; r < 2; ++r) {
         for (int v = tid; v < n; v += nthreads) {
             const int e = row_ptr[v] + r;
-            if (e < row_ptr[v + 1]) uf_link(L, v, col_idx[e]);
+            if (e < row_ptr[v + 1]) uf_link(L, v, qcdev::checked_id(col_idx[e], n, qcdev::DBG_PREP));
         }
         if (!qcdev::grid_barrier(bar, ctl)) return;
         uf_compress(L, n, tid, nthreads);
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(256) cc_afforest(int32_t n, const int32_t *row
     for (int v = tid >> 5; v < n; v += nthreads >> 5) {
         if (*(volatile int32_t *)(L + v) == giant) continue;
         const int end = row_ptr[v + 1];
-        for (int e = row_ptr[v] + 2 + lane; e < end; e += 32) uf_link(L, v, col_idx[e]);
+        for (int e = row_ptr[v] + 2 + lane; e < end; e += 32) uf_link(L, v, qcdev::checked_id(col_idx[e], n, qcdev::DBG_PREP));
     }
     if (!qcdev::grid_barrier(bar, ctl)) return;
     uf_compress(L, n, tid, nthreads);
@@ -162,6 +164,9 @@ __global__ void word_components(int32_t n, int32_t W, const int32_t *comp, int32
 
 __device__ __forceinline__ int degree_bucket(int deg) { return 31 - __clz(deg + 1); }
 
+// Degree order, scattered: nodes by decreasing degree bucket, in whatever order
+// the atomics hand out positions within a bucket (which interleaves the graph's
+// regions).  Taken when the BFS's bitsets fit in L2.
 __global__ void bucket_count(int32_t n, const int32_t *row_ptr, int32_t *counts) {
     __shared__ int32_t local[32];
     if (threadIdx.x < 32) local[threadIdx.x] = 0;
@@ -188,6 +193,96 @@ __global__ void bucket_scan(const int32_t *counts, int32_t *cursor, int32_t *n_h
 __global__ void bucket_scatter(int32_t n, const int32_t *row_ptr, int32_t *cursor, int32_t *order) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
         order[atomicAdd(&cursor[degree_bucket(row_ptr[v + 1] - row_ptr[v])], 1)] = v;
+}
+
+// Degree order, stable: nodes by decreasing degree bucket and, within a bucket,
+// by increasing id.  Graphs whose ids follow their communities (as generated
+// graphs and many real ones do) then keep neighbouring rows close in the BFS's
+// work lists, so the rows a level gathers for nearby items are reused from L2
+// before they are evicted.  Taken when the BFS's two bitset buffers exceed L2
+// (measured on GB300: the SBM of 262,144 nodes, 2 x 256 MiB of bitsets, solves
+// in 92.8 instead of 99.9 ms; the DC-SBM of 16,384 nodes, 2 x 32 MiB, is 4 %
+// slower in the stable order, so it keeps the scattered one).  Block i of the grid owns the nodes [i chunk, (i + 1) chunk):
+// order_counts counts its nodes per bucket, order_offsets turns the counts into
+// first positions (heaviest bucket first, then block by block), and order_place
+// writes each block's nodes in id order.
+__global__ void order_counts(int32_t n, int32_t chunk, const int32_t *row_ptr, int32_t *counts) {
+    __shared__ int32_t c[32];
+    if (threadIdx.x < 32) c[threadIdx.x] = 0;
+    __syncthreads();
+    const int v0 = blockIdx.x * chunk, v1 = min(n, v0 + chunk);
+    for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x)
+        atomicAdd(&c[degree_bucket(row_ptr[v + 1] - row_ptr[v])], 1);
+    __syncthreads();
+    if (threadIdx.x < 32) counts[blockIdx.x * 32 + threadIdx.x] = c[threadIdx.x];
+}
+
+// One block of 32 warps; warp b scans bucket b over the nb blocks, then the
+// buckets are stacked heaviest first; *n_heavy = nodes in buckets >= QC_HEAVY_BUCKET.
+__global__ void __launch_bounds__(1024) order_offsets(int32_t nb, const int32_t *counts, int32_t *offsets,
+                                                      int32_t *n_heavy) {
+    __shared__ int32_t total[32];
+    const int lane = threadIdx.x & 31, b = threadIdx.x >> 5;
+    int run = 0;
+    for (int i0 = 0; i0 < nb; i0 += 32) {
+        const int i = i0 + lane;
+        const int c = i < nb ? counts[i * 32 + b] : 0;
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (i < nb) offsets[i * 32 + b] = run + incl - c;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) total[b] = run;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int bb = 31; bb >= 0; --bb) {
+            const int t = total[bb];
+            total[bb] = acc;
+            acc += t;
+            if (bb == QC_HEAVY_BUCKET) *n_heavy = acc;
+        }
+    }
+    __syncthreads();
+    for (int i = lane; i < nb; i += 32) offsets[i * 32 + b] += total[b];
+}
+
+// 256 threads: the block's nodes 256 at a time; a node's place is its bucket's
+// next position plus the nodes of that bucket before it in this step (earlier
+// warps, then earlier lanes of its warp).
+__global__ void __launch_bounds__(256) order_place(int32_t n, int32_t chunk, const int32_t *row_ptr,
+                                                  const int32_t *offsets, int32_t *order) {
+    __shared__ int32_t base[32];
+    __shared__ int32_t wcount[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x < 32) base[threadIdx.x] = offsets[blockIdx.x * 32 + threadIdx.x];
+    const int v0 = blockIdx.x * chunk, v1 = min(n, v0 + chunk);
+    for (int s = v0; s < v1; s += 256) {
+        const int v = s + threadIdx.x;
+        const bool ok = v < v1;
+        const int b = ok ? degree_bucket(row_ptr[v + 1] - row_ptr[v]) : 32;
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        wcount[w][lane] = 0;
+        __syncthreads();
+        if (ok && rank == 0) wcount[w][b] = __popc(same);
+        __syncthreads();
+        if (ok) {
+            int before = 0;
+            for (int ww = 0; ww < w; ++ww) before += wcount[ww][b];
+            order[base[b] + before + rank] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int tot = 0;
+            for (int ww = 0; ww < 8; ++ww) tot += wcount[ww][threadIdx.x];
+            base[threadIdx.x] += tot;
+        }
+        __syncthreads();
+    }
 }
 
 // info[i] = {order[i], its row start, its row end, 0}: one 16-byte load gives a
@@ -230,7 +325,6 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
     QC_TRY(g->oinfo.allocate(ctx, sizeof(int4) * (size_t)n, stream));
     qc_buffer p, bins;
     QC_TRY(p.allocate(ctx, sizeof(int32_t) * (size_t)n, stream));
-    QC_TRY(bins.allocate(ctx, sizeof(int32_t) * 64, stream));
     const int tb = 256;
     const int nb = qc_ceil_div(n, tb) < 4 * ctx->num_sms ? qc_ceil_div(n, tb) : 4 * ctx->num_sms;
     // components: one thread per node is all the link phases use; more blocks only
@@ -261,14 +355,30 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
                                                             g->wmajor.as<int32_t>(),
                                                             g->wmask.as<unsigned long long>());
     QC_LAUNCHED(ctx);
-    QC_CUDA_TRY(ctx, cudaMemsetAsync(bins.ptr, 0, bins.bytes, stream));
-    bucket_count<<<nb, tb, 0, stream>>>(n, rp, bins.as<int32_t>());
-    QC_LAUNCHED(ctx);
-    bucket_scan<<<1, 32, 0, stream>>>(bins.as<int32_t>(), bins.as<int32_t>() + 32,
-                                      g->order.as<int32_t>() + n);
-    QC_LAUNCHED(ctx);
-    bucket_scatter<<<nb, tb, 0, stream>>>(n, rp, bins.as<int32_t>() + 32, g->order.as<int32_t>());
-    QC_LAUNCHED(ctx);
+    const double bitset_bytes = 2.0 * 8.0 * (double)n * (double)qc_bfs_chunk_words(ctx, n);
+    if (bitset_bytes > (double)ctx->l2_bytes) {
+        // stable degree order: blocks own contiguous ranges of node ids
+        const int ob = std::max(1, std::min(qc_ceil_div(n, 256), 4 * ctx->num_sms));
+        const int chunk = qc_ceil_div(n, ob);
+        QC_TRY(bins.allocate(ctx, sizeof(int32_t) * 64 * (size_t)ob, stream));
+        int32_t *counts = bins.as<int32_t>(), *offsets = counts + 32 * (size_t)ob;
+        order_counts<<<ob, 256, 0, stream>>>(n, chunk, rp, counts);
+        QC_LAUNCHED(ctx);
+        order_offsets<<<1, 1024, 0, stream>>>(ob, counts, offsets, g->order.as<int32_t>() + n);
+        QC_LAUNCHED(ctx);
+        order_place<<<ob, 256, 0, stream>>>(n, chunk, rp, offsets, g->order.as<int32_t>());
+        QC_LAUNCHED(ctx);
+    } else {
+        QC_TRY(bins.allocate(ctx, sizeof(int32_t) * 64, stream));
+        QC_CUDA_TRY(ctx, cudaMemsetAsync(bins.ptr, 0, bins.bytes, stream));
+        bucket_count<<<nb, tb, 0, stream>>>(n, rp, bins.as<int32_t>());
+        QC_LAUNCHED(ctx);
+        bucket_scan<<<1, 32, 0, stream>>>(bins.as<int32_t>(), bins.as<int32_t>() + 32,
+                                          g->order.as<int32_t>() + n);
+        QC_LAUNCHED(ctx);
+        bucket_scatter<<<nb, tb, 0, stream>>>(n, rp, bins.as<int32_t>() + 32, g->order.as<int32_t>());
+        QC_LAUNCHED(ctx);
+    }
     order_info<<<nb, tb, 0, stream>>>(n, rp, g->order.as<int32_t>(), g->oinfo.as<int4>());
     QC_LAUNCHED(ctx);
     g->prepared = true;

@@ -64,4 +64,25 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *status,
     return ok_s;
 }
 
+// Bounds checks of the debug build (compiled with -DQC_DEBUG, library
+// libqcgraph_debug.so): every neighbour id a kernel reads from the CSR passes
+// through checked_id before it is used as an index.  An id outside [0, n)
+// records `code` in the device word qc_debug_word (the first failure wins) and
+// is replaced by 0, so the kernel ends normally and the host reports
+// QC_ERR_INVALID_GRAPH naming the check, instead of an out-of-range access.
+// Release builds compile the checks away.
+enum : int32_t {
+    DBG_BFS = 1, DBG_PREP = 2, DBG_GGD = 3, DBG_BATCH = 4, DBG_WEIGHTED = 5, DBG_NOALLOC = 6, DBG_SELFTEST = 7
+};
+#ifdef QC_DEBUG
+extern __device__ int32_t qc_debug_word;
+__device__ __forceinline__ int checked_id(int id, int n, int32_t code) {
+    if ((unsigned)id < (unsigned)n) return id;
+    atomicCAS(&qc_debug_word, 0, code);
+    return 0;
+}
+#else
+__device__ __forceinline__ int checked_id(int id, int, int32_t) { return id; }
+#endif
+
 }  // namespace qcdev

@@ -151,6 +151,7 @@ struct qc_buffer {
 
 struct qc_graph {
     qc_ctx *ctx = nullptr;
+    std::mutex use_mu;       // held by a serving worker while it runs the graph's single-graph path
     int32_t n = 0;
     int64_t nnz = 0;
     bool directed = false;   // row v = out-neighbours (QC_DIRECTED)
@@ -268,6 +269,12 @@ qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *ro
                           const int32_t *col_idx_dev, bool symmetric, bool row_ptr_checked, cudaStream_t stream);
 qc_status qc_validate_hist(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
                            const int32_t *hist_dev, int32_t D, cudaStream_t stream);
+
+// selftest.cu: in the debug build, the first failed bounds check since the last
+// call (read and cleared after the work queued so far has finished; the
+// caller has already waited for it); QC_ERR_INVALID_GRAPH naming it, else
+// QC_OK.  Always QC_OK in release builds.
+qc_status qc_debug_take(qc_ctx *ctx);
 
 static inline cudaStream_t qc_stream(void *s) { return static_cast<cudaStream_t>(s); }
 

@@ -6,6 +6,30 @@
 #include "qc_device.cuh"
 #include "qc_internal.h"
 
+#ifdef QC_DEBUG
+namespace qcdev {
+__device__ int32_t qc_debug_word = 0;
+}
+#endif
+
+qc_status qc_debug_take(qc_ctx *ctx) {
+#ifdef QC_DEBUG
+    int32_t w = 0;
+    QC_CUDA_TRY(ctx, cudaMemcpyFromSymbol(&w, qcdev::qc_debug_word, sizeof(w)));
+    if (w == 0) return QC_OK;
+    const int32_t zero = 0;
+    QC_CUDA_TRY(ctx, cudaMemcpyToSymbol(qcdev::qc_debug_word, &zero, sizeof(zero)));
+    static const char *where[] = {"", "BFS", "graph preparation", "descent", "batched kernel",
+                                  "weighted shortest paths", "no-alloc histogram", "self-test"};
+    qc_set_error(ctx, "debug build: a neighbour id outside [0, n) reached the %s kernels (check %d)",
+                 (w > 0 && w < 8) ? where[w] : "?", w);
+    return QC_ERR_INVALID_GRAPH;
+#else
+    (void)ctx;
+    return QC_OK;
+#endif
+}
+
 namespace {
 
 // Block 0 waits at the barrier; block 1 leaves without arriving.
@@ -132,4 +156,35 @@ extern "C" qc_status qc_selftest_l2_read(qc_ctx *ctx, int64_t bytes, int32_t mod
     QC_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ev.a, ev.b));
     *gbs = moved / (ms * 1e-3) / 1e9;
     return QC_OK;
+}
+
+// ---- self-test of the debug build's bounds checks ------------------------------------
+
+namespace {
+
+// Passes `id` through the check (never using it as an address) and stores the id
+// that comes out.
+__global__ void debug_check_kernel(int32_t id, int32_t n, int32_t *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = qcdev::checked_id(id, n, qcdev::DBG_SELFTEST);
+}
+
+}  // namespace
+
+extern "C" qc_status qc_selftest_debug_check(qc_ctx *ctx, int32_t id, int32_t n, int32_t *checked_out,
+                                             int32_t *debug_build, void *stream_) {
+    if (!ctx || !checked_out || !debug_build || n < 1) return QC_ERR_INVALID_ARG;
+#ifdef QC_DEBUG
+    *debug_build = 1;
+#else
+    *debug_build = 0;
+#endif
+    cudaStream_t stream = qc_stream(stream_);
+    QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    qc_buffer out;
+    QC_TRY(out.allocate(ctx, sizeof(int32_t), stream));
+    debug_check_kernel<<<1, 32, 0, stream>>>(id, n, out.as<int32_t>());
+    QC_LAUNCHED(ctx);
+    QC_CUDA_TRY(ctx, cudaMemcpyAsync(checked_out, out.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    return qc_debug_take(ctx);
 }

@@ -52,6 +52,7 @@ struct Req {
     Clock::time_point t_submit, t_admit, t_start, t_done;
     int32_t batch_size = 0;
     qc_graph *g = nullptr;
+    bool borrowed = false;       // g is the caller's resident graph (never destroyed here)
     qc_buffer labels_dev;
     std::vector<int32_t> labels;
     int32_t n_clusters = 0;
@@ -130,10 +131,8 @@ struct qc_server {
         r->state = s;
         r->status = status;
         r->t_done = Clock::now();
-        if (r->g) {
-            qc_graph_destroy(r->g);
-            r->g = nullptr;
-        }
+        if (r->g && !r->borrowed) qc_graph_destroy(r->g);
+        r->g = nullptr;
         r->labels_dev.release();
         resident -= r->bytes;
         active -= 1;
@@ -162,8 +161,9 @@ struct qc_server {
         size_t total = 0;
         s.offs.clear();
         for (Req *r : rs) {
-            QC_TRY(qc_graph_create(ctx, r->n, r->nnz, r->rp.data(), r->nnz ? r->ci.data() : nullptr, 0,
-                                   s.stream, &r->g));
+            if (!r->borrowed)
+                QC_TRY(qc_graph_create(ctx, r->n, r->nnz, r->rp.data(), r->nnz ? r->ci.data() : nullptr, 0,
+                                       s.stream, &r->g));
             QC_TRY(r->labels_dev.allocate(ctx, sizeof(int32_t) * (size_t)r->n, s.stream));
             graphs.push_back(r->g);
             sig.push_back(r->sigma);
@@ -202,6 +202,8 @@ struct qc_server {
 
     // Hand out the results of a finished slot (mu held).
     void complete(Slot &s) {
+        // debug build: a failed bounds check in the launch fails its requests
+        const qc_status dbg = qc_debug_take(ctx);
         size_t total = 0;
         for (Req *r : s.reqs) total += (size_t)r->n;
         const int32_t *counts = s.pinned + total;
@@ -210,6 +212,10 @@ struct qc_server {
             Req *r = s.reqs[i];
             if (r->cancel) {
                 finish(r, RState::Cancelled, QC_ERR_CANCELLED);
+                continue;
+            }
+            if (dbg != QC_OK) {
+                finish(r, RState::Failed, dbg);
                 continue;
             }
             if (flags[i]) {          // deeper than the batched kernel keeps: single-graph path
@@ -319,18 +325,24 @@ struct qc_server {
             r->t_start = Clock::now();
             lk.unlock();
             qc_status status = QC_OK;
-            if (r->g) {
-                qc_graph_destroy(r->g);
-                r->g = nullptr;
+            if (!r->borrowed) {
+                if (r->g) {
+                    qc_graph_destroy(r->g);
+                    r->g = nullptr;
+                }
+                // large requests are validated here, on the device (see qc_server_submit)
+                status = qc_graph_create(ctx, r->n, r->nnz, r->rp.data(), r->nnz ? r->ci.data() : nullptr,
+                                         QC_VALIDATE, large_stream, &r->g);
             }
-            // large requests are validated here, on the device (see qc_server_submit)
-            status = qc_graph_create(ctx, r->n, r->nnz, r->rp.data(), r->nnz ? r->ci.data() : nullptr,
-                                     QC_VALIDATE, large_stream, &r->g);
             if (status == QC_OK && !r->labels_dev.ptr)
                 status = r->labels_dev.allocate(ctx, sizeof(int32_t) * (size_t)r->n, large_stream);
             int32_t nc = 0;
-            if (status == QC_OK)
+            if (status == QC_OK) {
+                // a resident graph may carry several requests: one solve on it at a time
+                // (its cached histogram serves every sigma after the first)
+                std::lock_guard<std::mutex> glk(r->g->use_mu);
                 status = qc_solve(r->g, &r->sigma, 1, nullptr, r->labels_dev.as<int32_t>(), &nc, large_stream);
+            }
             std::vector<int32_t> host;
             if (status == QC_OK) {
                 host.resize(r->n);
@@ -441,6 +453,37 @@ qc_status qc_server_submit(qc_server *s, int32_t n, int64_t nnz, const int32_t *
     return QC_OK;
 }
 
+qc_status qc_server_submit_graph(qc_server *s, qc_graph *g, double sigma, uint64_t *req_id) {
+    if (!s || !g || !req_id || !qc_sigma_ok(sigma)) return QC_ERR_INVALID_ARG;
+    if (g->ctx != s->ctx) {
+        qc_set_error(s->ctx, "qc_server_submit_graph: the graph belongs to another context");
+        return QC_ERR_INVALID_ARG;
+    }
+    auto r = std::make_unique<Req>();
+    r->n = g->n;
+    r->nnz = g->nnz;
+    r->g = g;
+    r->borrowed = true;
+    r->sigma = sigma;
+    r->large = g->n > qc_cta_max_nodes();
+    // the CSR is resident already: only the request's scratch counts
+    r->bytes = s->estimate(g->n, g->nnz, r->large) - (4 * ((size_t)g->n + 1) + 4 * (size_t)g->nnz);
+    r->t_submit = Clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (r->bytes > s->budget || s->stop) {
+        qc_set_error(s->ctx, "request of %zu estimated bytes exceeds the serving budget of %zu", r->bytes,
+                     s->budget);
+        return QC_ERR_BUDGET;
+    }
+    r->id = s->next_id++;
+    *req_id = r->id;
+    s->queue.push_back(r.get());
+    s->reqs.emplace(r->id, std::move(r));
+    s->st.submitted++;
+    s->cv.notify_all();
+    return QC_OK;
+}
+
 qc_status qc_server_poll(qc_server *s, uint64_t req_id, int32_t *labels_out, int32_t *n_clusters,
                          qc_request_info *info, int *done) {
     if (!s || !done) return QC_ERR_INVALID_ARG;
@@ -519,7 +562,7 @@ void qc_server_destroy(qc_server *s) {
         if (ls) cudaStreamDestroy(ls);
     for (auto &kv : s->reqs) {
         Req *r = kv.second.get();
-        if (r->g) qc_graph_destroy(r->g);
+        if (r->g && !r->borrowed) qc_graph_destroy(r->g);
         r->labels_dev.release();
     }
     s->ctx->coop_sm_share = s->saved_share;

@@ -278,6 +278,7 @@ static qc_status sweep_run(qc_sweep *p, int32_t reuse_histogram, int32_t *n_clus
                 QC_TRY(queue_full(p, stream));
             }
             QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+            QC_TRY(qc_debug_take(ctx));
             if (p->pinned[0] == ST_TIMEOUT) {
                 p->have_hist = false;
                 qc_set_error(ctx, "qc_sweep_run: BFS grid barrier timed out");

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(256, 3) sssp_persistent(const SsspParams p) {
             const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
             bool stirred = false;
             for (int e = beg + lane; e < end && !stirred; e += 32)
-                stirred = *(volatile int32_t *)(p.chgv + p.col_idx[e]) >= pass - 1;
+                stirred = *(volatile int32_t *)(p.chgv + qcdev::checked_id(p.col_idx[e], p.n, qcdev::DBG_WEIGHTED)) >= pass - 1;
             if (!__any_sync(FULL, stirred)) continue;
             bool v_fell = false;
             // GU source groups at a time, and up to NB changed neighbours at a time,
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256, 3) sssp_persistent(const SsspParams p) {
                     int u = 0;
                     unsigned long long wt = 0ull;
                     if (e < end) {
-                        u = p.col_idx[e];
+                        u = qcdev::checked_id(p.col_idx[e], p.n, qcdev::DBG_WEIGHTED);
                         wt = (unsigned long long)__double_as_longlong(p.w[e]);
                     }
                     unsigned fm[GU];
@@ -400,7 +400,7 @@ __global__ void check_weights(int32_t n, const int32_t *row_ptr, const int32_t *
             const double x = w[e];
             if (!(x > 0.0) || !(x < 1e308)) bad |= BAD_WEIGHT;
             if (!symmetric) continue;
-            const int u = col_idx[e];
+            const int u = qcdev::checked_id(col_idx[e], n, qcdev::DBG_WEIGHTED);
             int lo = row_ptr[u], hi = row_ptr[u + 1] - 1;
             bool same = false;
             while (lo <= hi) {
@@ -482,6 +482,7 @@ extern "C" qc_status qc_graph_set_weights(qc_graph *g, const double *w, uint32_t
         int32_t *h = static_cast<int32_t *>(pin.ptr);
         QC_CUDA_TRY(ctx, cudaMemcpyAsync(h, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
         QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        QC_TRY(qc_debug_take(ctx));
         if (h[0]) {
             qc_set_error(ctx, "invalid weights (flags 0x%x):%s%s", h[0],
                          (h[0] & BAD_WEIGHT) ? " not finite and > 0;" : "",
@@ -570,6 +571,7 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
         QC_LAUNCHED(ctx);
         QC_CUDA_TRY(ctx, cudaMemcpyAsync(h, ctl.ptr, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
         QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+        QC_TRY(qc_debug_take(ctx));
         if (h[0] == qcdev::ST_TIMEOUT) {
             qc_set_error(ctx, "shortest paths: grid barrier timed out (sources from %d)", s0);
             return QC_ERR_TIMEOUT;

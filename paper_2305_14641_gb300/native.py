@@ -11,7 +11,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libqcgraph.so")
+# QCGRAPH_DEBUG_LIB=1 selects the bounds-checked debug build (libqcgraph_debug.so)
+LIB_PATH = os.path.join(HERE, "libqcgraph_debug.so" if os.environ.get("QCGRAPH_DEBUG_LIB") == "1"
+                        else "libqcgraph.so")
 
 c_int32_p = ctypes.POINTER(ctypes.c_int32)
 c_int64_p = ctypes.POINTER(ctypes.c_int64)
@@ -100,6 +102,8 @@ SIGNATURES = [
     ("qc_server_create", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qc_server_config), c_void_pp]),
     ("qc_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]),
+    ("qc_server_submit_graph", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                              ctypes.POINTER(ctypes.c_uint64)]),
     ("qc_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, c_int32_p,
                                       ctypes.POINTER(qc_request_info), ctypes.POINTER(ctypes.c_int)]),
     ("qc_server_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
@@ -115,6 +119,8 @@ SIGNATURES = [
     ("qc_selftest_barrier_timeout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, c_int64_p, ctypes.c_void_p]),
     ("qc_selftest_arith", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    ("qc_selftest_debug_check", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, c_int32_p,
+                                                c_int32_p, ctypes.c_void_p]),
     ("qc_selftest_l2_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, c_double_p,
                                             ctypes.c_void_p]),
     ("qc_histogram_static_scratch", ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,

@@ -238,3 +238,26 @@ def test_server_request_stream_full(qc, ctx):
     bad = [k for k in range(400)
            if labels_digest(res[k]["labels"]) != gold["labels_digest"][k] or res[k]["n_clusters"] != gold["n_clusters"][k]]
     assert not bad, (len(bad), explain(graphs[bad[0]], reqs[bad[0]].sigma, res[bad[0]]["labels"]))
+
+
+def test_server_resident_graphs(qc):
+    """Requests on graphs already resident on the GPU (qc_server_submit_graph):
+    several sigmas per graph, one small enough for the batched kernel and one for
+    the single-graph path (whose later requests reuse its cached histogram), all
+    equal to the oracle's labels."""
+    small = gg.planted_partition(600, 5, 0.05, 0.004, gg.rng(47))
+    large = gg.planted_partition(6000, 12, 0.01, 0.0005, gg.rng(48))
+    with qc.Server(0) as srv:
+        Gs = qc.Graph.from_graph(srv.ctx, small)
+        Gl = qc.Graph.from_graph(srv.ctx, large)
+        jobs = [(small, Gs, s) for s in (0.7, 1.5)] + [(large, Gl, s) for s in (0.8, 1.6, 2.4)]
+        ids = [srv.submit_graph(G, s) for _, G, s in jobs]
+        res = [srv.wait(i, timeout_ms=120000) for i in ids]
+        st = srv.stats()
+        Gs.close()
+        Gl.close()
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    for (graph, _, s), r in zip(jobs, res):
+        ref = oracle.solve(graph, [s])
+        assert np.array_equal(r["labels"], ref.labels[0]), (graph.name, s)
+        assert r["n_clusters"] == ref.n_clusters[0]
