@@ -46,7 +46,7 @@ def test_profile_figures_only_for_the_profiled_sources(tmp_path):
     # the committed summaries carry the figures the bench reads
     for name in ("bfs_persistent_dcsbm16384.md", "bfs_persistent_sbm262144.md"):
         committed = open(os.path.join(bench.ROOT, "profiles", name)).read()
-        for key in ("traffic_bytes_per_launch", "l2_read_bytes_per_launch", "kernel_source_sha256"):
+        for key in ("traffic_bytes_per_launch", "kernel_source_sha256"):
             assert key + ":" in committed, (name, key)
 
 
