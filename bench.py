@@ -21,8 +21,10 @@ CUDA events, inputs resident in HBM, L2 flushed (256 MiB write) before every
 timed step.  On one GPU the default line also carries the rest of the headline
 metric: `batch4096` (the batched plan against the plain one-graph-at-a-time
 form, labels compared) and `serve` (p50/p99 latency of the Poisson request
-stream, throughput against serial plain solves, labels compared); --no-extra
-leaves them out.  `e2e` is the same metric through the public API with host
+stream, throughput against serial plain solves, labels compared, four
+large-request workers at 40 % of the SMs each), with `serve_low_latency` the
+same stream where two workers split 80 % of the SMs among the large requests
+running; --no-extra leaves them out.  `e2e` is the same metric through the public API with host
 buffers: pinned host CSR -> device, solve, labels back to pinned host memory.
 `--impl reference` times the CPU oracle (test infrastructure, plain C) on the
 same workload instead.  With --gpus N > 1 each rank runs an independent replica
@@ -461,6 +463,11 @@ def bench_ours(args, graph, sigmas, spec):
             # the rest of the headline metric: batched vs plain, and the served form's latency
             line["batch4096"] = batch_summary(args)
             line["serve"] = serve_summary(args)
+            # the same stream at the latency-oriented operating point: two large-request
+            # workers whose requests split 80 % of the SMs among those running at once
+            low = argparse.Namespace(**vars(args))
+            low.large_workers, low.large_sm_share, low.divide_share = 2, 0.8, 1
+            line["serve_low_latency"] = serve_summary(low)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -549,7 +556,8 @@ def serve_summary(args) -> dict:
     graphs = [r.graph() for r in reqs]
     t_gen = time.perf_counter() - t_gen
     lat, results, served_labels = {}, {}, {}
-    with qc.Server(0, large_workers=args.large_workers, large_sm_share=args.large_sm_share) as srv:
+    with qc.Server(0, large_workers=args.large_workers, large_sm_share=args.large_sm_share,
+                   divide_share=args.divide_share) as srv:
         # warm up: a few requests of each kind
         for g, r in list(zip(graphs, reqs))[:8]:
             srv.wait(srv.submit(g.row_ptr, g.col_idx, r.sigma))
@@ -631,7 +639,7 @@ def serve_summary(args) -> dict:
     bfs_s = bfs["total_ms"] / 1000.0
     return {"metric": "clusterings/s", "workload": SERVE_WORKLOAD, "requests": len(reqs),
             "warmup_requests": warm, "large_workers": args.large_workers,
-            "large_sm_share": args.large_sm_share,
+            "large_sm_share": args.large_sm_share, "divide_share": bool(args.divide_share),
             "served_open_loop_per_s": len(reqs) / open_wall,
             "p50_ms": float(np.percentile(L[keep], 50)), "p99_ms": float(np.percentile(L[keep], 99)),
             "served_closed_loop_per_s": closed, "serial_plain_per_s": serial,
@@ -822,10 +830,10 @@ QUALITY_SHAPES = {"cora-shaped": (2708, 5278, 7), "citeseer-shaped": (3327, 4676
 def bench_quality(args):
     """Quality against the planted communities over the 16-value sigma sweep (the
     analogue of the paper's sigma-sensitivity figure on synthetic stand-ins):
-    modularity, ARI, FMI, NMI and the number of clusters per sigma."""
+    modularity, ARI, FMI, NMI (computed on the device) and the number of clusters
+    per sigma; solve_ms covers the solve and the 16 measurements."""
     import torch
     import paper_2305_14641_gb300 as qc
-    from paper_2305_14641_gb300 import metrics
     sigmas = gg.sigma_sweep16()
     ctx = qc.Context(0)
     out = {}
@@ -835,15 +843,13 @@ def bench_quality(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, labels, counts = g.solve(sigmas)
-        labels = labels.cpu().numpy()
-        secs = time.perf_counter() - t0
+        truth = torch.as_tensor(graph.block, device="cuda")
         curve = []
         for s, lab, c in zip(sigmas, labels, counts):
-            curve.append({"sigma": round(s, 4), "clusters": int(c),
-                          "modularity": metrics.modularity(graph.row_ptr, graph.col_idx, lab),
-                          "ari": metrics.adjusted_rand_index(graph.block, lab),
-                          "fmi": metrics.fowlkes_mallows(graph.block, lab),
-                          "nmi": metrics.normalized_mutual_info(graph.block, lab)})
+            m = qc.quality(ctx, lab, graph=g, truth=truth, n_truth=int(graph.block.max()) + 1)
+            curve.append({"sigma": round(s, 4), "clusters": int(c), "modularity": m["modularity"],
+                          "ari": m["ari"], "fmi": m["fmi"], "nmi": m["nmi"]})
+        secs = time.perf_counter() - t0
         best = max(curve, key=lambda r: r["nmi"])
         out[name] = {"n": n, "edges": graph.nnz // 2, "planted": k, "solve_ms": 1000.0 * secs,
                      "best_by_nmi": best, "curve": curve}
@@ -875,6 +881,8 @@ def main():
                     help="default workload only: leave out the batch4096 and serve sub-lines")
     ap.add_argument("--large-workers", type=int, default=4)
     ap.add_argument("--large-sm-share", type=float, default=0.4)
+    ap.add_argument("--divide-share", type=int, default=0,
+                    help="serve: split the large-request SM share among the large requests running")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = SINGLE[args.workload]["steps"] if args.workload in SINGLE else 200

@@ -265,6 +265,33 @@ qc_status qc_sweep_run(qc_sweep *p, int32_t reuse_histogram, int32_t *n_clusters
 qc_status qc_sweep_info(const qc_sweep *p, int32_t *D, int32_t *captured, int64_t *kernels_per_run);
 void qc_sweep_destroy(qc_sweep *p);
 
+/* ---- quality of a clustering ------------------------------------------------------ */
+
+/* The measures of the paper's evaluation (Section 4.2) for a label vector on the
+ * device.  labels: device int32[n], each a node id in [0, n) (root ids, as
+ * qc_ggd_labels writes them).  g: the clustered graph (undirected, n nodes, made
+ * on ctx), or NULL to skip modularity.  truth: device int32[n] of true
+ * classes in [0, n_truth), or NULL to skip ARI, FMI and NMI.  Results (host,
+ * NaN where skipped):
+ *   modularity  Q = inside / w - gamma sum_c (degree sum of c)^2 / w^2 (inside =
+ *               CSR entries within a cluster, w = the degree total: Newman's form);
+ *   ari         the Adjusted Rand Index (Hubert & Arabie) over pair counts of
+ *               the contingency table;
+ *   fmi         TP / sqrt((TP + FP)(TP + FN)) over pairs;
+ *   nmi         MI / sqrt(H(truth) H(labels)), natural logarithms;
+ *   clusters    distinct labels.
+ * Counts and pair sums are exact integers on the device; the entropies and
+ * the mutual information are binary64 sums.  Synchronises `stream`.
+ * Errors: QC_ERR_INVALID_ARG (nulls, a graph of another size or context, a
+ * label or class out of range, a contingency table over 2^31 cells),
+ * QC_ERR_BUDGET, QC_ERR_OOM, QC_ERR_CUDA. */
+typedef struct {
+    double modularity, ari, fmi, nmi;
+    int32_t clusters;
+} qc_quality_result;
+qc_status qc_quality(qc_ctx *ctx, const qc_graph *g, int32_t n, const int32_t *labels, const int32_t *truth,
+                     int32_t n_truth, double gamma, qc_quality_result *out, void *stream);
+
 /* ---- many graphs ------------------------------------------------------------ */
 
 /* A batch plan: Algorithm 4 for n_graphs graphs, graph k clustered with
@@ -309,6 +336,9 @@ typedef struct {
                                   (0 = 0.4); applies to the whole context until
                                   qc_server_destroy restores its previous share, so
                                   give a server a context of its own */
+    int32_t divide_share;      /* 1: a large request gets large_sm_share divided by the
+                                  number of large requests running at that moment (a lone
+                                  one gets all of it); 0: each gets large_sm_share */
 } qc_server_config;
 
 typedef struct {

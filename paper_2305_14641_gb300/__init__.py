@@ -19,7 +19,7 @@ import numpy as np
 from . import native
 from .native import QCError
 
-__all__ = ["Context", "Graph", "SweepPlan", "BatchPlan", "Server", "QCError", "solve_batch"]
+__all__ = ["Context", "Graph", "SweepPlan", "BatchPlan", "Server", "QCError", "solve_batch", "quality"]
 
 
 def _torch():
@@ -408,6 +408,28 @@ class BatchPlan:
             pass
 
 
+def quality(ctx: Context, labels, graph: "Graph" = None, truth=None, n_truth: int | None = None,
+            gamma: float = 1.0, stream=None) -> dict:
+    """Modularity (with graph), ARI, FMI and NMI (with truth) of a label vector on the
+    GPU (int32 root ids, as the solve writes them), computed on the device."""
+    torch = _torch()
+    dev = f"cuda:{ctx.device}"
+    lab = torch.as_tensor(labels, device=dev).to(torch.int32).contiguous().reshape(-1)
+    n = lab.numel()
+    tr = None
+    if truth is not None:
+        tr = torch.as_tensor(truth, device=dev).to(torch.int32).contiguous().reshape(-1)
+        if n_truth is None:
+            n_truth = int(tr.max().item()) + 1
+    if graph is not None and graph.n != n:
+        raise ValueError("labels and graph differ in size")
+    out = native.qc_quality_result()
+    ctx.check(ctx._lib.qc_quality(ctx.handle, graph.handle if graph is not None else None, n, lab.data_ptr(),
+                                  tr.data_ptr() if tr is not None else None, int(n_truth or 0), float(gamma),
+                                  ctypes.byref(out), _stream_handle(stream)))
+    return {"modularity": out.modularity, "ari": out.ari, "fmi": out.fmi, "nmi": out.nmi, "clusters": out.clusters}
+
+
 def solve_batch(ctx: Context, graphs: Sequence[Graph], sigmas: Sequence[float], stream=None):
     """One-shot batched solve: (labels tensor, offsets)."""
     plan = BatchPlan(ctx, graphs, sigmas, stream)
@@ -423,10 +445,11 @@ class Server:
     allocator so that the library's threads never call back into Python."""
 
     def __init__(self, device: int = 0, mem_budget_bytes: int = 100 << 30, max_active: int = 256,
-                 streams: int = 4, large_workers: int = 4, large_sm_share: float = 0.4):
+                 streams: int = 4, large_workers: int = 4, large_sm_share: float = 0.4,
+                 divide_share: bool = False):
         self.ctx = Context(device, allocator="cuda")
         cfg = native.qc_server_config(int(mem_budget_bytes), int(max_active), int(streams),
-                                      int(large_workers), float(large_sm_share))
+                                      int(large_workers), float(large_sm_share), int(bool(divide_share)))
         h = ctypes.c_void_p()
         self.ctx.check(self.ctx._lib.qc_server_create(self.ctx.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h

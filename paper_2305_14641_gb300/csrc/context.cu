@@ -83,6 +83,8 @@ qc_status qc_event_pair::create(qc_ctx *ctx) {
     return QC_OK;
 }
 
+thread_local float qc_thread_sm_share = 0.f;
+
 void qc_record_kernel(qc_ctx *ctx, const char *kernel, double ms, double model_bytes, double min_bytes) {
     std::lock_guard<std::mutex> lk(ctx->stats_mu);
     qc_kernel_stats &st = ctx->stats[kernel];

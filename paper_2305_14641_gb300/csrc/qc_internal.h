@@ -280,8 +280,14 @@ static inline cudaStream_t qc_stream(void *s) { return static_cast<cudaStream_t>
 
 static inline int qc_ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Share of the SMs the calling thread's cooperative launches may fill, when set
+// (> 0); else the context's share applies.  The serving loop's workers set it per
+// request.
+extern thread_local float qc_thread_sm_share;
+
 // SMs' worth of blocks a cooperative (persistent) kernel may fill.
 static inline int qc_coop_sms(const qc_ctx *ctx) {
-    const int s = (int)(ctx->coop_sm_share.load() * (float)ctx->num_sms);
+    const float share = qc_thread_sm_share > 0.f ? qc_thread_sm_share : ctx->coop_sm_share.load();
+    const int s = (int)(share * (float)ctx->num_sms);
     return s < 1 ? 1 : (s > ctx->num_sms ? ctx->num_sms : s);
 }

@@ -115,6 +115,9 @@ struct qc_server {
     std::vector<std::thread> large;
     std::vector<cudaStream_t> large_streams;
     float saved_share = 1.0f;          // the context's SM share before the server set its own
+    float large_share = 0.4f;          // SM share of the large-request path
+    bool divide_share = false;         // split large_share among the large requests running
+    int32_t large_running = 0;         // large requests on the GPU right now
 
     size_t estimate(int32_t n, int64_t nnz, bool is_large) const {
         const size_t csr = 4 * ((size_t)n + 1) + 4 * (size_t)nnz;
@@ -323,6 +326,10 @@ struct qc_server {
                 continue;
             }
             r->t_start = Clock::now();
+            large_running += 1;
+            // this request's persistent kernels fill large_share of the SMs, or that share
+            // split among the large requests running now
+            qc_thread_sm_share = divide_share ? large_share / (float)large_running : large_share;
             lk.unlock();
             qc_status status = QC_OK;
             if (!r->borrowed) {
@@ -351,6 +358,7 @@ struct qc_server {
                     status = QC_ERR_CUDA;
             }
             lk.lock();
+            large_running -= 1;
             st.large_solved++;
             if (status == QC_OK) {
                 r->labels.swap(host);
@@ -400,6 +408,8 @@ qc_status qc_server_create(qc_ctx *ctx, const qc_server_config *cfg, qc_server *
                                                                                           : 0.4f;
     s->saved_share = ctx->coop_sm_share.load();
     ctx->coop_sm_share = share;
+    s->large_share = share;
+    s->divide_share = cfg && cfg->divide_share;
     QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     // batched launches of small requests first: highest stream priority
     int prio_low = 0, prio_high = 0;

@@ -31,7 +31,7 @@ class qc_allocator(ctypes.Structure):
 class qc_server_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int32),
                 ("streams", ctypes.c_int32), ("large_workers", ctypes.c_int32),
-                ("large_sm_share", ctypes.c_float)]
+                ("large_sm_share", ctypes.c_float), ("divide_share", ctypes.c_int32)]
 
 
 class qc_server_stats(ctypes.Structure):
@@ -47,6 +47,11 @@ class qc_request_info(ctypes.Structure):
     _fields_ = [("admit_ms", ctypes.c_double), ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
                 ("n", ctypes.c_int32),
                 ("nnz", ctypes.c_int64), ("batch_size", ctypes.c_int32)]
+
+
+class qc_quality_result(ctypes.Structure):
+    _fields_ = [("modularity", ctypes.c_double), ("ari", ctypes.c_double), ("fmi", ctypes.c_double),
+                ("nmi", ctypes.c_double), ("clusters", ctypes.c_int32)]
 
 
 class qc_kernel_stats(ctypes.Structure):
@@ -92,6 +97,9 @@ SIGNATURES = [
                                      c_int32_p, ctypes.c_void_p]),
     ("qc_solve", ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_int32, ctypes.c_void_p,
                                 ctypes.c_void_p, c_int32_p, ctypes.c_void_p]),
+    ("qc_quality", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+                                  ctypes.POINTER(qc_quality_result), ctypes.c_void_p]),
     ("qc_batch_create", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, c_void_pp, c_double_p,
                                        ctypes.c_void_p, c_int64_p, ctypes.c_void_p, c_void_pp]),
     ("qc_batch_run", ctypes.c_int, [ctypes.c_void_p, c_int32_p, ctypes.c_void_p]),
