@@ -69,6 +69,8 @@ constexpr int NOT_SAT = 0x7fffffff;
 constexpr int WARPS = 8;               // warps per block
 constexpr int GRAB = 4;                // light list positions taken per counter update
 constexpr int LIST_AFTER = 2;          // pull levels of a launch that scan every item
+constexpr int TH_WORDS = 256;          // longest chunk row the two-hop set-up builds in shared memory
+constexpr int TH_U = 8;                // neighbour-of-neighbour ids each lane has in flight
 using qcdev::ST_DONE;
 using qcdev::ST_NEED_ROWS;
 using qcdev::ST_TIMEOUT;
@@ -110,6 +112,9 @@ struct BfsParams {
     unsigned *bar;              // [0] arrivals, [1] generation
     unsigned long long *stamp;  // [rows] globaltimer when each level's barrier opened (timing only)
     int32_t *pulled;            // [rows] (node, tile) items pulled at each level (timing only, else null)
+    const unsigned long long *deg2;   // sum over nodes of degree^2 (the graph's preparation)
+    int64_t nnz;
+    int32_t two_hop;            // levels 1 and 2 from the CSR (two_hop_setup): 0 never, 1 sparse graphs, 2 always
 };
 
 __device__ __forceinline__ bool seg_full(const ulonglong2 a) { return (a.x & a.y) == ONES; }
@@ -194,10 +199,244 @@ __device__ void init_bits(const BfsParams &p) {
     if (lane == 0 && set) atomicAdd(p.level_bits + 1, (unsigned long long)set);
 }
 
-// ---- levels >= 2: pull ------------------------------------------------------------
-
 // New bits found by the block at the current level.
 __shared__ unsigned int block_found;
+
+// ---- levels 1 and 2 together: the two-hop set-up ------------------------------------
+//
+// A source s is within two hops of v exactly when s is v, a neighbour of v or a
+// neighbour of a neighbour, so vis_2[v] can be written from the CSR alone: the
+// preset bits, then v and N(v) (that is vis_1[v]), then N(u) for every u in N(v).
+// The bits of vis_2[v] outside vis_1[v] are next_2[v], the sources at distance
+// exactly 2, counted into hist[2][v].  This reads sum_u deg(u)^2 neighbour ids,
+// against the E neighbour rows of wn/2 segments that the first pull level
+// gathers, so a launch takes it on sparse graphs (4 sum deg^2 <= wn E) and it
+// then replaces the level-1 set-up and the first pull level.  The row is built
+// in shared memory with atomic ORs on 32-bit words; a light node is one warp's,
+// a heavy node (degree >= 127, the first order[n] positions) the whole block's.
+// The emitting warp keeps vis_1[v] in registers, so the count and, with change
+// masks, the segments that gained bits at level 2 come from comparing the two.
+
+constexpr int TH_T = TH_WORDS / 64;     // tiles of a row the set-up builds
+
+// Preset bits of v's row in 64-bit words tid, tid + nt, ... (padding words all ones).
+__device__ __forceinline__ void th_preset(const BfsParams &p, uint32_t *row, int v, int tid, int nt) {
+    const int cv = p.comp[v];
+    unsigned long long *row64 = reinterpret_cast<unsigned long long *>(row);
+    for (int k = tid; k < 2 * p.R; k += nt) row64[k] = (k < p.wn) ? preset_word(p, p.w0 + k, cv) : ONES;
+}
+
+// Sets source u's bit in the row if u is a source of the chunk.
+__device__ __forceinline__ void th_set(const BfsParams &p, uint32_t *row, int u) {
+    const int b = u - 64 * p.w0;
+    if (b >= 0 && b < 64 * p.wn) atomicOr(row + (b >> 5), 1u << (b & 31));
+}
+
+// Bits of v and of its neighbours (ids beg + tid, beg + tid + nt, ...; end stands for v).
+__device__ __forceinline__ void th_first(const BfsParams &p, uint32_t *row, int v, int beg, int end, int tid,
+                                         int nt) {
+    for (int e = beg + tid; e <= end; e += nt)
+        th_set(p, row, (e == end) ? v : qcdev::checked_id(p.col_idx[e], p.n, qcdev::DBG_BFS));
+}
+
+// The row's segments 32 t + lane (t < T) of this warp, for the comparison at the end.
+__device__ __forceinline__ void th_capture(const BfsParams &p, const uint32_t *row, ulonglong2 (&r1)[TH_T]) {
+    const int lane = threadIdx.x & 31;
+    const ulonglong2 *seg = reinterpret_cast<const ulonglong2 *>(row);
+#pragma unroll
+    for (int t = 0; t < TH_T; ++t) {
+        const int s = 32 * t + lane;
+        r1[t] = (t < p.T && s < p.R) ? seg[s] : make_ulonglong2(ONES, ONES);
+    }
+}
+
+// Start and length of the neighbour list of batch member `lane` (ids j0 + lane).
+__device__ __forceinline__ void th_lists(const BfsParams &p, int j0, int end, int &ub, int &ul) {
+    const int lane = threadIdx.x & 31;
+    ub = 0;
+    ul = 0;
+    if (j0 + lane < end) {
+        const int u = qcdev::checked_id(p.col_idx[j0 + lane], p.n, qcdev::DBG_BFS);
+        ub = p.row_ptr[u];
+        ul = p.row_ptr[u + 1] - ub;
+    }
+}
+
+// Bits of the neighbours of v's neighbours, for the neighbour batches of 32 starting
+// at beg + 32 sub, stride 32 nsub (one warp of nsub); (ub0, ul0) are the lists of the
+// first batch, fetched by the caller.  The batch's lists are laid end to end and the
+// warp walks that concatenation 32 ids at a time, each lane finding the list its
+// position falls in by a binary search over the batch's exclusive prefix sums.
+// Under the selection rule a degree is at most sqrt(wn E / 4) < 2^19 (forced:
+// below 2^20), so a batch's total fits an int.
+__device__ __forceinline__ void th_second(const BfsParams &p, uint32_t *row, int beg, int end, int sub, int nsub,
+                                          int ub, int ul) {
+    const int lane = threadIdx.x & 31;
+    for (int j0 = beg + 32 * sub; j0 < end; j0 += 32 * nsub) {
+        if (j0 != beg + 32 * sub) th_lists(p, j0, end, ub, ul);
+        int incl = ul;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - ul;
+        for (int f0 = 0; f0 < total; f0 += 32 * TH_U) {
+            int w[TH_U];
+#pragma unroll
+            for (int k = 0; k < TH_U; ++k) {
+                const int f = f0 + 32 * k + lane;
+                // the last lane i with excl_i <= f owns position f (lists of length 0
+                // share their successor's start, so the last one wins)
+                int i = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (__shfl_sync(FULL, excl, i + step) <= f) i += step;
+                const int at = __shfl_sync(FULL, ub, i) + (f - __shfl_sync(FULL, excl, i));
+                w[k] = (f < total) ? qcdev::checked_id(p.col_idx[at], p.n, qcdev::DBG_BFS) : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < TH_U; ++k)
+                if (w[k] >= 0) th_set(p, row, w[k]);
+        }
+    }
+}
+
+// One warp writes the finished row of v (order position oi) as level 2, its tiles'
+// saturation (level 2 if all ones) and change masks, and v's histogram entries.
+template <bool MASKS>
+__device__ __forceinline__ bool th_emit(const BfsParams &p, const uint32_t *row, const ulonglong2 (&r1)[TH_T], int v,
+                                        int oi, int deg) {
+    const int lane = threadIdx.x & 31;
+    const ulonglong2 *seg = reinterpret_cast<const ulonglong2 *>(row);
+    ulonglong2 *out = p.buf[0] + (size_t)v * p.R;
+    int count = 0;
+    unsigned fulls = 0u, chgs[TH_T];
+#pragma unroll
+    for (int t = 0; t < TH_T; ++t) {
+        const int s = 32 * t + lane;
+        bool full = true, changed = false;
+        if (t < p.T && s < p.R) {
+            const ulonglong2 x = seg[s];
+            out[s] = x;
+            full = seg_full(x);
+            count += __popcll(x.x & ~r1[t].x) + __popcll(x.y & ~r1[t].y);
+            changed = x.x != r1[t].x || x.y != r1[t].y;
+        }
+        if (__all_sync(FULL, full)) fulls |= 1u << t;
+        chgs[t] = __ballot_sync(FULL, changed);
+    }
+    if (lane < p.T) {
+        const int t = lane;
+        p.sat[(size_t)oi * p.T + t] = ((fulls >> t) & 1u) ? 2 : NOT_SAT;
+        if constexpr (MASKS) {
+            unsigned c = chgs[0];
+#pragma unroll
+            for (int k = 1; k < TH_T; ++k)
+                if (t == k) c = chgs[k];
+            p.fmask[0][(size_t)v * p.T + t] = c;
+            p.fmask[1][(size_t)v * p.T + t] = 0u;
+        }
+    }
+    count = __reduce_add_sync(FULL, count);
+    if (lane == 0) {
+        if (p.first_chunk) {
+            p.hist[v] = 1;
+            p.hist[(size_t)p.n + v] = deg;
+        }
+        if (count) p.hist[2 * (size_t)p.n + v] += count;
+        if constexpr (MASKS) {
+            if (count) atomicAdd(&block_found, (unsigned)count);
+        }
+    }
+    return count != 0;
+}
+
+// Levels 1 and 2 of a chunk: heavy nodes block by block, then light nodes warp by
+// warp, both taken from counters.  rows: WARPS rows of 2 TH_WORDS 32-bit words.
+// Returns whether this thread's rows gained bits at level 2.
+template <bool MASKS>
+__device__ __forceinline__ bool two_hop_setup(const BfsParams &p, uint32_t (*rows)[2 * TH_WORDS]) {
+    bool any_new = false;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int heavy = p.order[p.n];
+    __shared__ int th_grab;
+    ulonglong2 r1[TH_T];
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) th_grab = atomicAdd(p.heavy_ctr + 1, 1);
+        __syncthreads();
+        const int oi = th_grab;
+        if (oi >= heavy) break;
+        const int4 inf = p.info[oi];
+        uint32_t *row = rows[0];
+        int ub, ul;
+        th_lists(p, inf.y + 32 * wib, inf.z, ub, ul);
+        th_preset(p, row, inf.x, threadIdx.x, blockDim.x);
+        __syncthreads();
+        th_first(p, row, inf.x, inf.y, inf.z, threadIdx.x, blockDim.x);
+        __syncthreads();
+        if (wib == 0) th_capture(p, row, r1);
+        __syncthreads();
+        th_second(p, row, inf.y, inf.z, wib, WARPS, ub, ul);
+        __syncthreads();
+        if (wib == 0 && th_emit<MASKS>(p, row, r1, inf.x, oi, inf.z - inf.y)) any_new = true;
+    }
+    uint32_t *row = rows[wib];
+    while (true) {
+        int oi = 0;
+        if (lane == 0) oi = heavy + atomicAdd(p.light_ctr + 1, 1);
+        oi = __shfl_sync(FULL, oi, 0);
+        if (oi >= p.n) break;
+        const int4 inf = p.info[oi];
+        int ub, ul;
+        th_lists(p, inf.y, inf.z, ub, ul);
+        th_preset(p, row, inf.x, lane, 32);
+        __syncwarp();
+        th_first(p, row, inf.x, inf.y, inf.z, lane, 32);
+        __syncwarp();
+        th_capture(p, row, r1);
+        th_second(p, row, inf.y, inf.z, 0, 1, ub, ul);
+        __syncwarp();
+        if (th_emit<MASKS>(p, row, r1, inf.x, oi, inf.z - inf.y)) any_new = true;
+        __syncwarp();
+    }
+    return any_new;
+}
+
+// Whether a fresh chunk's levels 1 and 2 come from the two-hop set-up (the same
+// answer in bfs_two_hop and bfs_persistent).  two_hop 1: on sparse graphs; 2: on
+// every graph whose degrees are below 2^20 (their squares sum below 2^40), which
+// keeps a batch's id count within an int.
+__device__ __forceinline__ bool two_hop_taken(const BfsParams &p) {
+    if (p.start_level != 2 || p.rows <= 2 || 2 * p.R > TH_WORDS) return false;
+    const unsigned long long d2 = *p.deg2;
+    return (p.two_hop == 1 && 4ull * d2 <= (unsigned long long)p.wn * (unsigned long long)p.nnz) ||
+           (p.two_hop == 2 && d2 < (1ull << 40));
+}
+
+// The two-hop set-up as its own launch, queued just before bfs_persistent: levels
+// 1 and 2 of the chunk, hist rows 0-2, the items' saturation, level 2's flag and
+// (with masks) its change masks and bit count.
+template <bool MASKS>
+__global__ void __launch_bounds__(256) bfs_two_hop(const BfsParams p) {
+    __shared__ __align__(16) uint32_t rows[WARPS][2 * TH_WORDS];
+    if (!two_hop_taken(p)) return;
+    if (threadIdx.x == 0) block_found = 0u;
+    if (p.stamp && blockIdx.x == 0 && threadIdx.x == 0) p.stamp[1] = global_ns();
+    __syncthreads();
+    const bool any_new = two_hop_setup<MASKS>(p, rows);
+    if (__syncthreads_or(any_new) && threadIdx.x == 0) p.level_new[2] = 1;
+    if constexpr (MASKS) {
+        // a count past 2^32 in one block only misjudges the density estimate
+        if (threadIdx.x == 0 && block_found) atomicAdd(p.level_bits + 2, (unsigned long long)block_found);
+    }
+}
+
+// ---- levels >= 2: pull ------------------------------------------------------------
+
 // Items the block pulled at the current level (reported in timing mode).
 __shared__ unsigned int block_pulled;
 // Per warp: ids and change masks of the neighbours a G = 32 gather reads.
@@ -506,13 +745,25 @@ __global__ void __launch_bounds__(256, G == 32 ? 3 : 4) bfs_persistent(const Bfs
     __syncthreads();
     int level = p.start_level;
     const bool stamp = p.stamp && blockIdx.x == 0 && threadIdx.x == 0;
-    if (stamp) p.stamp[level - 1] = global_ns();
+    const bool after_two_hop = two_hop_taken(p);
+    if (stamp && !after_two_hop) p.stamp[level - 1] = global_ns();
     if (level == 2) {
-        init_fill(p);
-        if (!grid_barrier(p.bar, p.status)) return;
-        init_bits(p);
-        if (!grid_barrier(p.bar, p.status)) return;
-        if (stamp) p.stamp[2] = global_ns();
+        if (after_two_hop) {
+            // bfs_two_hop wrote levels 1 and 2
+            if (stamp) p.stamp[2] = p.stamp[3] = global_ns();
+            if (*(volatile int32_t *)(p.level_new + 2) == 0) {
+                // nothing at distance 2: the BFS ends here
+                if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(p.status + 1, 2);
+                return;
+            }
+            level = 3;
+        } else {
+            init_fill(p);
+            if (!grid_barrier(p.bar, p.status)) return;
+            init_bits(p);
+            if (!grid_barrier(p.bar, p.status)) return;
+            if (stamp) p.stamp[2] = global_ns();
+        }
     }
     // masks of the previous level are complete: the set-up writes level 1's, and
     // a masked level writes its own; after the first level that is not masked
@@ -627,6 +878,11 @@ qc_status qc_bfs_scratch_init(qc_graph *g, qc_bfs_scratch &bs, cudaStream_t stre
     if (const char *env = getenv("QCGRAPH_MASK_RATIO")) bs.mask_ratio = std::max(0, atoi(env));
     const double mean_deg = (double)g->nnz / (double)n;
     bs.masks = bs.mask_ratio > 0 && bs.R_max > 16 && mean_deg * mean_deg * bs.mask_ratio < (double)n;
+    // QCGRAPH_TWO_HOP: 0 keeps the level-1 set-up and the first pull level on every
+    // graph, 2 takes the two-hop set-up wherever its row fits (tests), 1 (default)
+    // on sparse graphs
+    bs.two_hop = 1;
+    if (const char *env = getenv("QCGRAPH_TWO_HOP")) bs.two_hop = std::min(2, std::max(0, atoi(env)));
     if (bs.masks) QC_TRY(bs.fmask.allocate(ctx, 2 * sizeof(uint32_t) * (size_t)n * bs.T_max, stream));
     QC_TRY(bs.sat.allocate(ctx, sizeof(int32_t) * (size_t)n * bs.T_max, stream));
     QC_TRY(bs.wl.allocate(ctx, 2 * sizeof(int32_t) * (size_t)n * bs.T_max, stream));
@@ -702,8 +958,22 @@ qc_status qc_bfs_launch(qc_graph *g, qc_bfs_scratch &bs, int32_t w0, int32_t sta
     p.wl[1] = bs.wl.as<int32_t>() + (size_t)n * bs.T_max;
     p.stamp = stamps;
     p.pulled = stamps ? reinterpret_cast<int32_t *>(p.level_bits + (n + 2)) : nullptr;
+    p.deg2 = qc_graph_deg2(g);
+    p.nnz = g->nnz;
+    p.two_hop = bs.two_hop;
     QC_CUDA_TRY(ctx, cudaMemsetAsync(bs.ctl.ptr, 0, bs.ctl.bytes, stream));
     if (reset_out) QC_CUDA_TRY(ctx, cudaMemsetAsync(out, 0, 2 * sizeof(int32_t), stream));
+    if (start == 2 && bs.two_hop && 2 * R <= TH_WORDS) {
+        // levels 1-2 from the CSR when the graph is sparse enough (decided on the
+        // device, by both kernels alike)
+        const bfs_fn th = with_masks ? bfs_two_hop<true> : bfs_two_hop<false>;
+        int th_per_sm = 0;
+        QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&th_per_sm, (const void *)th, 256, 0));
+        int th_blocks = std::max(1, th_per_sm) * qc_coop_sms(ctx);
+        if (th_blocks > qc_ceil_div(n, 8)) th_blocks = qc_ceil_div(n, 8);
+        th<<<std::max(1, th_blocks), 256, 0, stream>>>(p);
+        QC_LAUNCHED(ctx);
+    }
     void *args[] = {(void *)&p};
     QC_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(256), args, 0, stream));
     QC_LAUNCHED(ctx);

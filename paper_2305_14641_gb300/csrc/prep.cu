@@ -286,12 +286,20 @@ __global__ void __launch_bounds__(256) order_place(int32_t n, int32_t chunk, con
 }
 
 // info[i] = {order[i], its row start, its row end, 0}: one 16-byte load gives a
-// BFS item everything it needs before it reads the neighbour ids.
-__global__ void order_info(int32_t n, const int32_t *row_ptr, const int32_t *order, int4 *info) {
+// BFS item everything it needs before it reads the neighbour ids.  Also adds up
+// the squared degrees into *deg2 (zeroed before): the number of neighbour-of-
+// neighbour ids a two-hop expansion of every node reads.
+__global__ void order_info(int32_t n, const int32_t *row_ptr, const int32_t *order, int4 *info,
+                           unsigned long long *deg2) {
+    unsigned long long sq = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int v = order[i];
-        info[i] = make_int4(v, row_ptr[v], row_ptr[v + 1], 0);
+        const int b = row_ptr[v], e = row_ptr[v + 1];
+        info[i] = make_int4(v, b, e, 0);
+        sq += (unsigned long long)(e - b) * (unsigned long long)(e - b);
     }
+    for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+    if ((threadIdx.x & 31) == 0 && sq) atomicAdd(deg2, sq);
 }
 
 __global__ void first_rows(int32_t n, const int32_t *row_ptr, int32_t *hist) {
@@ -379,10 +387,15 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
         bucket_scatter<<<nb, tb, 0, stream>>>(n, rp, bins.as<int32_t>() + 32, g->order.as<int32_t>());
         QC_LAUNCHED(ctx);
     }
-    order_info<<<nb, tb, 0, stream>>>(n, rp, g->order.as<int32_t>(), g->oinfo.as<int4>());
+    order_info<<<nb, tb, 0, stream>>>(n, rp, g->order.as<int32_t>(), g->oinfo.as<int4>(),
+                                      const_cast<unsigned long long *>(qc_graph_deg2(g)));
     QC_LAUNCHED(ctx);
     g->prepared = true;
     return QC_OK;
+}
+
+const unsigned long long *qc_graph_deg2(const qc_graph *g) {
+    return reinterpret_cast<const unsigned long long *>(g->prep_ctl.as<int32_t>() + 6);
 }
 
 qc_status qc_graph_prepare_status(qc_graph *g, int32_t host_status) {

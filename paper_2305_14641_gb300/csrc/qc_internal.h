@@ -169,7 +169,7 @@ struct qc_graph {
     // preparation (see prep.cu), computed once
     bool prepared = false;
     bool prep_checked = false;   // the components launch's status has been read
-    qc_buffer prep_ctl;      // int32[8]: status and grid barrier of that launch
+    qc_buffer prep_ctl;      // int32[8]: status and grid barrier of that launch; [6..7] sum of degree^2
     qc_buffer comp;          // int32[n] component = smallest node id in it
     qc_buffer wcomp;         // int32[W] component of a whole 64-source word, or -1
     qc_buffer wmajor;        // int32[W] the component holding most of a mixed word's sources
@@ -200,9 +200,12 @@ struct qc_bfs_scratch {
     int32_t wc = 0, R_max = 0, T_max = 0;   // source words per chunk, row segments, tiles
     bool masks = false;                     // variant: change masks
     int32_t mask_ratio = 0;
+    int32_t two_hop = 1;                    // levels 1-2 from the CSR: 0 never, 1 sparse graphs, 2 always
     qc_buffer visA, visB, sat, ctl, wl, fmask;
 };
 qc_status qc_bfs_scratch_init(qc_graph *g, qc_bfs_scratch &bs, cudaStream_t stream);
+// prep.cu: device address of the sum over nodes of degree^2 (written by the preparation)
+const unsigned long long *qc_graph_deg2(const qc_graph *g);
 // Queue one launch of the BFS kernel: the chunk of source words from w0, from
 // level `start` (2 = fresh), adding into hist[rows][n], outcome in out[0..1]
 // (reset first when reset_out).  The graph must be prepared.

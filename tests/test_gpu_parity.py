@@ -127,6 +127,28 @@ def test_change_masks(qc, ctx, ratio, chunk, monkeypatch):
     assert_solution_matches(qc, ctx, gg.directed_erdos_renyi(6000, 3.0 / 6000, gg.rng(26, int(chunk))), [1.2])
 
 
+@pytest.mark.parametrize("mode", ["0", "2"])
+def test_two_hop_setup(qc, ctx, mode, monkeypatch):
+    """Levels 1 and 2 written straight from the CSR (mode 2: on every graph it
+    fits) and the level-1 set-up followed by a pull level (mode 0), each against
+    the oracle: ragged sizes, isolated nodes and several components, a complete
+    graph (every row full at level 1), hubs taken block-wide (a star of 20,000
+    leaves), chunked sources, change masks, and directed arcs."""
+    monkeypatch.setenv("QCGRAPH_TWO_HOP", mode)
+    rng = gg.rng(61)
+    graphs = [gg.erdos_renyi(n, p, rng) for n, p in ((65, 0.05), (1000, 0.004), (3001, 0.003), (2047, 0.3))]
+    graphs += [gg.complete(40), gg.path(300), gg.star(70, 5), gg.two_cliques_bridge(9), gg.path(2)]
+    graphs += [gg.dcsbm(3000, 8, 2.5, 10.0, 200.0, 0.1, gg.rng(24)),
+               gg.directed_erdos_renyi(2000, 3.0 / 2000, gg.rng(62)), gg.star(20001, 0)]
+    for graph in graphs:
+        assert_solution_matches(qc, ctx, graph, [0.6, 1.5])
+    monkeypatch.setenv("QCGRAPH_CHUNK_WORDS", "5")
+    assert_solution_matches(qc, ctx, gg.planted_partition(700, 5, 0.05, 0.004, gg.rng(63)), [0.9])
+    monkeypatch.setenv("QCGRAPH_CHUNK_WORDS", "96")
+    monkeypatch.setenv("QCGRAPH_MASK_RATIO", "1")
+    assert_solution_matches(qc, ctx, gg.planted_partition(9000, 30, 0.012, 0.0002, gg.rng(64)), [0.7])
+
+
 def test_planted_and_dcsbm_mid(qc, ctx):
     g1 = gg.planted_partition(4000, 16, 0.02, 0.0005, gg.rng(23))
     g2 = gg.dcsbm(3000, 8, 2.5, 10.0, 200.0, 0.1, gg.rng(24))
