@@ -27,6 +27,10 @@
  *     every array it passes; the library never frees them.
  *   - Outputs go into caller-provided buffers.  The library allocates its own
  *     scratch through the context's allocator (see qc_allocator).
+ *   - An object made on a stream (a graph, a batch plan) allocates its memory
+ *     stream-ordered on that stream and gives it back on the same stream when it
+ *     is destroyed, so the stream must outlive the object.  Objects that own a
+ *     stream (sweep plans, servers) give their memory back before destroying it.
  *   - There is no CPU fallback: without a usable GPU every call that needs one
  *     returns QC_ERR_CUDA.
  */
@@ -231,6 +235,20 @@ qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, int32_t n_sig
  * those two calls. */
 qc_status qc_solve(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V_out,
                    int32_t *labels_out, int32_t *n_clusters_out, void *stream);
+
+/* Algorithm 4 from a CSR to labels in one call, for a graph that is not kept:
+ * qc_graph_create (arguments and flags as there: host arrays unless
+ * QC_PTR_DEVICE, QC_VALIDATE, QC_DIRECTED), then the BFS and histogram, the
+ * potential for every sigma, the descent and the roots, with the labels copied
+ * to labels_out: int32[n_sigma][n], host or device memory (any address the CUDA
+ * copy engines can write).  n_clusters_out: host int32[n_sigma] or NULL.  The
+ * work after the upload is queued back to back and the call waits once at the
+ * end (and, with QC_VALIDATE, once for the validation's verdict), so on return
+ * labels_out holds the result and the library holds nothing of the graph.
+ * Errors: those of qc_graph_create and qc_solve. */
+qc_status qc_cluster(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                     uint32_t flags, const double *sigmas, int32_t n_sigma, int32_t *labels_out,
+                     int32_t *n_clusters_out, void *stream);
 
 /* ---- one graph, a fixed sigma sweep, replayed ---------------------------------- */
 

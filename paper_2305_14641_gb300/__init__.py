@@ -19,7 +19,7 @@ import numpy as np
 from . import native
 from .native import QCError
 
-__all__ = ["Context", "Graph", "SweepPlan", "BatchPlan", "Server", "QCError", "solve_batch", "quality"]
+__all__ = ["Context", "Graph", "SweepPlan", "BatchPlan", "Server", "QCError", "cluster", "solve_batch", "quality"]
 
 
 def _torch():
@@ -428,6 +428,42 @@ def quality(ctx: Context, labels, graph: "Graph" = None, truth=None, n_truth: in
                                   tr.data_ptr() if tr is not None else None, int(n_truth or 0), float(gamma),
                                   ctypes.byref(out), _stream_handle(stream)))
     return {"modularity": out.modularity, "ari": out.ari, "fmi": out.fmi, "nmi": out.nmi, "clusters": out.clusters}
+
+
+def cluster(ctx: Context, row_ptr, col_idx, sigmas: Sequence[float], labels_out=None, counts: bool = True,
+            validate: bool = True, directed: bool = False, stream=None):
+    """Algorithm 4 from a CSR to labels in one library call (the graph is not kept).
+
+    row_ptr / col_idx: numpy arrays (host) or CUDA int32 tensors.  labels_out: an
+    int32 [S, n] torch tensor (pinned host or CUDA) or numpy array to write into;
+    by default a new numpy array.  Returns (labels, clusters per sigma or None)."""
+    torch = _torch()
+    flags = (native.QC_VALIDATE if validate else 0) | (native.QC_DIRECTED if directed else 0)
+    if isinstance(row_ptr, torch.Tensor):
+        rp = row_ptr.to(device=f"cuda:{ctx.device}", dtype=torch.int32).contiguous()
+        ci = col_idx.to(device=f"cuda:{ctx.device}", dtype=torch.int32).contiguous()
+        flags |= native.QC_PTR_DEVICE
+        n, nnz = rp.numel() - 1, ci.numel()
+        p_rp, p_ci = rp.data_ptr(), (ci.data_ptr() if nnz else None)
+    else:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        n, nnz = len(rp) - 1, len(ci)
+        p_rp, p_ci = rp.ctypes.data, (ci.ctypes.data if nnz else None)
+    S = len(sigmas)
+    if labels_out is None:
+        labels_out = np.empty((S, n), dtype=np.int32)
+    if isinstance(labels_out, torch.Tensor):
+        assert labels_out.dtype == torch.int32 and labels_out.is_contiguous() and labels_out.numel() == S * n
+        p_lab = labels_out.data_ptr()
+    else:
+        assert labels_out.dtype == np.int32 and labels_out.flags.c_contiguous and labels_out.size == S * n
+        p_lab = labels_out.ctypes.data
+    sig = (ctypes.c_double * S)(*[float(x) for x in sigmas])
+    nc = (ctypes.c_int32 * S)() if counts else None
+    ctx.check(ctx._lib.qc_cluster(ctx.handle, n, nnz, p_rp, p_ci, flags, sig, S, p_lab, nc,
+                                  _stream_handle(stream)))
+    return labels_out, (list(nc) if counts else None)
 
 
 def solve_batch(ctx: Context, graphs: Sequence[Graph], sigmas: Sequence[float], stream=None):

@@ -71,6 +71,7 @@ constexpr int GRAB = 4;                // light list positions taken per counter
 constexpr int LIST_AFTER = 2;          // pull levels of a launch that scan every item
 constexpr int TH_WORDS = 256;          // longest chunk row the two-hop set-up builds in shared memory
 constexpr int TH_U = 8;                // neighbour-of-neighbour ids each lane has in flight
+constexpr int TH_PIPELINE = 16;        // light nodes per warp from which the set-up takes them ahead
 using qcdev::ST_DONE;
 using qcdev::ST_NEED_ROWS;
 using qcdev::ST_TIMEOUT;
@@ -109,10 +110,11 @@ struct BfsParams {
     int32_t *wl_count;          // [rows] length of each level's worklist
     int32_t *status;            // [0] state, [1] highest level reached (the pass that found nothing);
                                 // the graph's outcome words, kept across the chunks of one BFS
-    unsigned *bar;              // [0] arrivals, [1] generation
+    unsigned *bar;              // [0] barrier arrivals over the launch
     unsigned long long *stamp;  // [rows] globaltimer when each level's barrier opened (timing only)
     int32_t *pulled;            // [rows] (node, tile) items pulled at each level (timing only, else null)
     const unsigned long long *deg2;   // sum over nodes of degree^2 (the graph's preparation)
+    const int32_t *lo, *hi;     // [n]: the chunk's sources in N(u) are col_idx[lo[u] .. hi[u]) (two-hop set-up)
     int64_t nnz;
     int32_t two_hop;            // levels 1 and 2 from the CSR (two_hop_setup): 0 never, 1 sparse graphs, 2 always
 };
@@ -232,11 +234,14 @@ __device__ __forceinline__ void th_set(const BfsParams &p, uint32_t *row, int u)
     if (b >= 0 && b < 64 * p.wn) atomicOr(row + (b >> 5), 1u << (b & 31));
 }
 
-// Bits of v and of its neighbours (ids beg + tid, beg + tid + nt, ...; end stands for v).
+// Bits of v and of its neighbours (ids beg + tid, beg + tid + nt, ...; end stands for
+// v); id0, when not negative, is the id at beg + tid, already loaded.
 __device__ __forceinline__ void th_first(const BfsParams &p, uint32_t *row, int v, int beg, int end, int tid,
-                                         int nt) {
+                                         int nt, int id0 = -1) {
     for (int e = beg + tid; e <= end; e += nt)
-        th_set(p, row, (e == end) ? v : qcdev::checked_id(p.col_idx[e], p.n, qcdev::DBG_BFS));
+        th_set(p, row, (e == end) ? v
+                       : (e == beg + tid && id0 >= 0) ? id0
+                                                     : qcdev::checked_id(p.col_idx[e], p.n, qcdev::DBG_BFS));
 }
 
 // The row's segments 32 t + lane (t < T) of this warp, for the comparison at the end.
@@ -250,16 +255,25 @@ __device__ __forceinline__ void th_capture(const BfsParams &p, const uint32_t *r
     }
 }
 
-// Start and length of the neighbour list of batch member `lane` (ids j0 + lane).
-__device__ __forceinline__ void th_lists(const BfsParams &p, int j0, int end, int &ub, int &ul) {
-    const int lane = threadIdx.x & 31;
+// Start and length of the chunk's part of the neighbour list of u (none for u < 0).
+__device__ __forceinline__ void th_bounds(const BfsParams &p, int u, int &ub, int &ul) {
     ub = 0;
     ul = 0;
-    if (j0 + lane < end) {
-        const int u = qcdev::checked_id(p.col_idx[j0 + lane], p.n, qcdev::DBG_BFS);
-        ub = p.row_ptr[u];
-        ul = p.row_ptr[u + 1] - ub;
+    if (u >= 0) {
+        ub = p.lo[u];
+        ul = p.hi[u] - ub;
     }
+}
+
+// Neighbour id j0 + lane of a list ending at end, or -1 past its end.
+__device__ __forceinline__ int th_id(const BfsParams &p, int j0, int end) {
+    const int e = j0 + (threadIdx.x & 31);
+    return e < end ? qcdev::checked_id(p.col_idx[e], p.n, qcdev::DBG_BFS) : -1;
+}
+
+// th_bounds of batch member `lane` (ids j0 + lane).
+__device__ __forceinline__ void th_lists(const BfsParams &p, int j0, int end, int &ub, int &ul) {
+    th_bounds(p, th_id(p, j0, end), ub, ul);
 }
 
 // Bits of the neighbours of v's neighbours, for the neighbour batches of 32 starting
@@ -385,25 +399,76 @@ __device__ __forceinline__ bool two_hop_setup(const BfsParams &p, uint32_t (*row
         if (wib == 0 && th_emit<MASKS>(p, row, r1, inf.x, oi, inf.z - inf.y)) any_new = true;
     }
     uint32_t *row = rows[wib];
-    while (true) {
-        int oi = 0;
-        if (lane == 0) oi = heavy + atomicAdd(p.light_ctr + 1, 1);
-        oi = __shfl_sync(FULL, oi, 0);
-        if (oi >= p.n) break;
-        const int4 inf = p.info[oi];
+    if (p.n - heavy < TH_PIPELINE * ((gridDim.x * blockDim.x) >> 5)) {
+        // few nodes per warp: take one at a time, so the last ones go to idle warps
+        while (true) {
+            int oi = 0;
+            if (lane == 0) oi = heavy + atomicAdd(p.light_ctr + 1, 1);
+            oi = __shfl_sync(FULL, oi, 0);
+            if (oi >= p.n) break;
+            const int4 inf = p.info[oi];
+            const int id = th_id(p, inf.y, inf.z);
+            int ub, ul;
+            th_bounds(p, id, ub, ul);
+            th_preset(p, row, inf.x, lane, 32);
+            __syncwarp();
+            th_first(p, row, inf.x, inf.y, inf.z, lane, 32, id);
+            __syncwarp();
+            th_capture(p, row, r1);
+            th_second(p, row, inf.y, inf.z, 0, 1, ub, ul);
+            __syncwarp();
+            if (th_emit<MASKS>(p, row, r1, inf.x, oi, inf.z - inf.y)) any_new = true;
+            __syncwarp();
+        }
+        return any_new;
+    }
+    // many nodes per warp: pipelined, so while node k is built the warp already holds
+    // node k+1's position, row bounds and first neighbour ids, and node k+2's position
+    // is on its way
+    const int4 none = make_int4(0, 0, 0, 0);
+    int ahead = 0;
+    if (lane == 0) ahead = heavy + atomicAdd(p.light_ctr + 1, 1);
+    int oi = __shfl_sync(FULL, ahead, 0);
+    int4 inf = oi < p.n ? p.info[oi] : none;
+    int id = oi < p.n ? th_id(p, inf.y, inf.z) : -1;
+    if (lane == 0) ahead = heavy + atomicAdd(p.light_ctr + 1, 1);
+    while (oi < p.n) {
+        const int oi1 = __shfl_sync(FULL, ahead, 0);
+        const int4 inf1 = oi1 < p.n ? p.info[oi1] : none;
+        if (lane == 0) ahead = heavy + atomicAdd(p.light_ctr + 1, 1);
         int ub, ul;
-        th_lists(p, inf.y, inf.z, ub, ul);
+        th_bounds(p, id, ub, ul);
         th_preset(p, row, inf.x, lane, 32);
         __syncwarp();
-        th_first(p, row, inf.x, inf.y, inf.z, lane, 32);
+        th_first(p, row, inf.x, inf.y, inf.z, lane, 32, id);
         __syncwarp();
         th_capture(p, row, r1);
         th_second(p, row, inf.y, inf.z, 0, 1, ub, ul);
+        const int id1 = oi1 < p.n ? th_id(p, inf1.y, inf1.z) : -1;
         __syncwarp();
         if (th_emit<MASKS>(p, row, r1, inf.x, oi, inf.z - inf.y)) any_new = true;
         __syncwarp();
+        oi = oi1;
+        inf = inf1;
+        id = id1;
     }
     return any_new;
+}
+
+// hi[u] = the first position of N(u) at or after lo[u] whose id is >= bound (rows
+// are sorted): with lo at the chunk's first source, [lo[u], hi[u]) is N(u)
+// restricted to the chunk, and hi is the next chunk's lo.
+__global__ void chunk_cursor(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const int32_t *lo,
+                             int32_t bound, int32_t *hi) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        int a = lo[u], b = row_ptr[u + 1];
+        while (a < b) {
+            const int m = a + ((b - a) >> 1);
+            if (col_idx[m] < bound) a = m + 1;
+            else b = m;
+        }
+        hi[u] = a;
+    }
 }
 
 // Whether a fresh chunk's levels 1 and 2 come from the two-hop set-up (the same
@@ -883,6 +948,8 @@ qc_status qc_bfs_scratch_init(qc_graph *g, qc_bfs_scratch &bs, cudaStream_t stre
     // on sparse graphs
     bs.two_hop = 1;
     if (const char *env = getenv("QCGRAPH_TWO_HOP")) bs.two_hop = std::min(2, std::max(0, atoi(env)));
+    if (bs.two_hop && bs.wc < (n + 63) / 64 && bs.R_max * 2 <= TH_WORDS)
+        QC_TRY(bs.cursor.allocate(ctx, 2 * sizeof(int32_t) * (size_t)n, stream));
     if (bs.masks) QC_TRY(bs.fmask.allocate(ctx, 2 * sizeof(uint32_t) * (size_t)n * bs.T_max, stream));
     QC_TRY(bs.sat.allocate(ctx, sizeof(int32_t) * (size_t)n * bs.T_max, stream));
     QC_TRY(bs.wl.allocate(ctx, 2 * sizeof(int32_t) * (size_t)n * bs.T_max, stream));
@@ -963,9 +1030,26 @@ qc_status qc_bfs_launch(qc_graph *g, qc_bfs_scratch &bs, int32_t w0, int32_t sta
     p.two_hop = bs.two_hop;
     QC_CUDA_TRY(ctx, cudaMemsetAsync(bs.ctl.ptr, 0, bs.ctl.bytes, stream));
     if (reset_out) QC_CUDA_TRY(ctx, cudaMemsetAsync(out, 0, 2 * sizeof(int32_t), stream));
+    p.lo = p.row_ptr;
+    p.hi = p.row_ptr + 1;
     if (start == 2 && bs.two_hop && 2 * R <= TH_WORDS) {
         // levels 1-2 from the CSR when the graph is sparse enough (decided on the
-        // device, by both kernels alike)
+        // device, by both kernels alike).  With several chunks the set-up reads only
+        // the chunk's part of each neighbour list: chunk k's part of N(u) runs from
+        // cursor k to cursor k + 1 (cursor 0 = row_ptr), found by binary search from
+        // the previous chunk's end; the cursors alternate between two arrays
+        if (wn < W && bs.cursor.ptr) {
+            const int32_t k = w0 / bs.wc;
+            int32_t *cur = bs.cursor.as<int32_t>();
+            const int32_t *lo = k == 0 ? p.row_ptr : cur + (size_t)(k & 1) * n;
+            int32_t *hi = cur + (size_t)((k + 1) & 1) * n;
+            const int64_t bound = std::min<int64_t>(64 * (int64_t)(w0 + wn), n);
+            const int cb = std::min(qc_ceil_div(n, 256), 8 * ctx->num_sms);
+            chunk_cursor<<<cb, 256, 0, stream>>>(n, p.row_ptr, p.col_idx, lo, (int32_t)bound, hi);
+            QC_LAUNCHED(ctx);
+            p.lo = lo;
+            p.hi = hi;
+        }
         const bfs_fn th = with_masks ? bfs_two_hop<true> : bfs_two_hop<false>;
         int th_per_sm = 0;
         QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&th_per_sm, (const void *)th, 256, 0));

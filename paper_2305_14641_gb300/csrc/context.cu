@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 
 #include "qc_internal.h"
 
@@ -219,19 +220,6 @@ qc_status qc_graph_create(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *ro
     cudaStream_t stream = qc_stream(stream_);
     QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     const bool on_device = flags & QC_PTR_DEVICE;
-    if (!on_device && (flags & QC_VALIDATE)) {
-        // row_ptr is checked on the host first: the device checks index through it
-        if (row_ptr[0] != 0 || row_ptr[n] != nnz) {
-            qc_set_error(ctx, "invalid CSR: row_ptr[0]=%d row_ptr[n]=%d nnz=%lld", row_ptr[0],
-                         row_ptr[n], (long long)nnz);
-            return QC_ERR_INVALID_GRAPH;
-        }
-        for (int32_t v = 0; v < n; ++v)
-            if (row_ptr[v + 1] < row_ptr[v]) {
-                qc_set_error(ctx, "invalid CSR: row_ptr decreases at row %d", v);
-                return QC_ERR_INVALID_GRAPH;
-            }
-    }
     qc_graph *g = new qc_graph();
     g->ctx = ctx;
     g->n = n;
@@ -254,7 +242,7 @@ qc_status qc_graph_create(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *ro
     }
     if (flags & QC_VALIDATE) {
         st = qc_validate_csr(ctx, n, nnz, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(), !g->directed,
-                             !on_device, stream);
+                             stream);
         if (st != QC_OK) {
             delete g;
             return st;
@@ -410,6 +398,60 @@ qc_status qc_solve(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V
         QC_TRY(ggd_enqueue(g, V, n_sigma, labels_out, roots.as<int32_t>(), stream));
     }
     return read_roots(ctx, roots, n_clusters_out, stream);
+}
+
+
+qc_status qc_cluster(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                     uint32_t flags, const double *sigmas, int32_t n_sigma, int32_t *labels_out,
+                     int32_t *n_clusters_out, void *stream_) {
+    qc_range range("qc.cluster");
+    if (!ctx) return QC_ERR_INVALID_ARG;
+    if (!sigmas || n_sigma < 1 || !labels_out) {
+        qc_set_error(ctx, "qc_cluster: null pointer or n_sigma < 1");
+        return QC_ERR_INVALID_ARG;
+    }
+    for (int32_t s = 0; s < n_sigma; ++s)
+        if (!qc_sigma_ok(sigmas[s])) {
+            qc_set_error(ctx, "qc_cluster: sigma[%d] = %g is not finite and > 0", s, sigmas[s]);
+            return QC_ERR_INVALID_ARG;
+        }
+    cudaStream_t stream = qc_stream(stream_);
+    qc_graph *g = nullptr;
+    QC_TRY(qc_graph_create(ctx, n, nnz, row_ptr, col_idx, flags, stream_, &g));
+    std::unique_ptr<qc_graph, void (*)(qc_graph *)> hold(g, qc_graph_destroy);
+    const size_t cells = (size_t)n_sigma * (size_t)n;
+    qc_buffer V, labels, roots;
+    QC_TRY(V.allocate(ctx, sizeof(double) * cells, stream));
+    QC_TRY(labels.allocate(ctx, sizeof(int32_t) * cells, stream));
+    QC_TRY(roots.allocate(ctx, sizeof(int32_t) * (size_t)n_sigma, stream));
+    qc_pinned pin(ctx);
+    const bool counts_pinned = n_clusters_out && sizeof(int32_t) * (size_t)n_sigma <= QC_PINNED_BYTES;
+    if (counts_pinned) QC_TRY(pin.acquire());
+    // potentials, descent and both copies out, queued behind the BFS
+    auto queue = [&]() -> qc_status {
+        QC_TRY(qc_potential_from_hist(g, sigmas, n_sigma, V.as<double>(), stream));
+        {
+            qc_range r2("qc.ggd");
+            QC_TRY(ggd_enqueue(g, V.as<double>(), n_sigma, labels.as<int32_t>(), roots.as<int32_t>(), stream));
+        }
+        QC_CUDA_TRY(ctx, cudaMemcpyAsync(labels_out, labels.ptr, labels.bytes, cudaMemcpyDefault, stream));
+        if (counts_pinned)
+            QC_CUDA_TRY(ctx, cudaMemcpyAsync(pin.ptr, roots.ptr, roots.bytes, cudaMemcpyDeviceToHost, stream));
+        return QC_OK;
+    };
+    qc_status st = qc_bfs_enqueue(g, stream);
+    if (st == QC_OK) st = queue();
+    bool redone = false;
+    const qc_status settled = qc_bfs_settle(g, stream, &redone);
+    if (st != QC_OK) return st;
+    if (settled != QC_OK) return settled;
+    if (redone) QC_TRY(queue());
+    if (n_clusters_out && !counts_pinned)
+        QC_CUDA_TRY(ctx, cudaMemcpyAsync(n_clusters_out, roots.ptr, roots.bytes, cudaMemcpyDeviceToHost, stream));
+    QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
+    QC_TRY(qc_debug_take(ctx));
+    if (counts_pinned) memcpy(n_clusters_out, pin.ptr, roots.bytes);
+    return QC_OK;
 }
 
 }  // extern "C"

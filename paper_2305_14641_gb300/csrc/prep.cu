@@ -22,20 +22,9 @@
 
 namespace {
 
-// Connected components by sampled union-find (after Sutton et al., "Optimizing
-// Parallel Graph Connectivity Computation via Subgraph Sampling", 2018), in
-// one cooperative launch:
-//   1. every node links to its first and then its second neighbour (lock-free
-//      union: a root is attached below a smaller root by compare-and-swap, so
-//      every root is the smallest id of its tree), compressing after each round;
-//   2. the label shared by most of 64 evenly spaced nodes names the largest
-//      component found so far;
-//   3. nodes outside that component link to their remaining neighbours; nodes
-//      inside it skip theirs (in an undirected graph the other end of each such
-//      edge, if outside, links it), and a final compression leaves every node
-//      pointing at its root, the smallest id of its component.
-// A directed graph lists an arc in one row only, so there every node links all
-// its arcs (the result: weakly connected components).
+// Union-find over the labels L (a node's label chain ends at its tree's root).
+// uf_link is a lock-free union: a root is attached below a smaller root by
+// compare-and-swap, so every root is the smallest id of its tree.
 __device__ __forceinline__ void uf_link(int32_t *L, int u, int v) {
     volatile int32_t *VL = L;
     int p1 = VL[u], p2 = VL[v];
@@ -58,61 +47,7 @@ __device__ __forceinline__ void uf_compress(int32_t *L, int n, int tid, int nthr
     }
 }
 
-__global__ void __launch_bounds__(256) cc_afforest(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
-                                                   int32_t *L, int32_t *ctl, int32_t directed) {
-    unsigned *bar = reinterpret_cast<unsigned *>(ctl + 2);
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nthreads = gridDim.x * blockDim.x;
-    for (int v = tid; v < n; v += nthreads) L[v] = v;
-    if (!qcdev::grid_barrier(bar, ctl)) return;
-    for (int r = 0; r < 2; ++r) {
-        for (int v = tid; v < n; v += nthreads) {
-            const int e = row_ptr[v] + r;
-            if (e < row_ptr[v + 1]) uf_link(L, v, qcdev::checked_id(col_idx[e], n, qcdev::DBG_PREP));
-        }
-        if (!qcdev::grid_barrier(bar, ctl)) return;
-        uf_compress(L, n, tid, nthreads);
-        if (!qcdev::grid_barrier(bar, ctl)) return;
-    }
-    // the most common label among 64 evenly spaced nodes
-    __shared__ int s_lab[64], s_cnt[64];
-    if (blockIdx.x == 0) {
-        if (threadIdx.x < 64) s_lab[threadIdx.x] = L[(int)(((long long)threadIdx.x * (n - 1)) / 63)];
-        __syncthreads();
-        if (threadIdx.x < 64) {
-            int c = 0;
-            for (int i = 0; i < 64; ++i) c += (s_lab[i] == s_lab[threadIdx.x]);
-            s_cnt[threadIdx.x] = c;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int best = 0;
-            for (int i = 1; i < 64; ++i)
-                if (s_cnt[i] > s_cnt[best]) best = i;
-            ctl[4] = directed ? -1 : s_lab[best];
-        }
-    }
-    if (!qcdev::grid_barrier(bar, ctl)) return;
-    const int giant = *(volatile int32_t *)(ctl + 4);
-    const int lane = threadIdx.x & 31;
-    for (int v = tid >> 5; v < n; v += nthreads >> 5) {
-        if (*(volatile int32_t *)(L + v) == giant) continue;
-        const int end = row_ptr[v + 1];
-        for (int e = row_ptr[v] + 2 + lane; e < end; e += 32) uf_link(L, v, qcdev::checked_id(col_idx[e], n, qcdev::DBG_PREP));
-    }
-    if (!qcdev::grid_barrier(bar, ctl)) return;
-    uf_compress(L, n, tid, nthreads);
-    if (tid == 0) ctl[1] = 1;
-}
-
-// Final labels: the root of each node's label chain.
-__global__ void cc_flatten(int32_t n, const int32_t *L, int32_t *comp) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        int x = L[v];
-        while (L[x] != x) x = L[x];
-        comp[v] = x;
-    }
-}
+__device__ __forceinline__ int degree_bucket(int deg) { return 31 - __clz(deg + 1); }
 
 // Per 64-source word: wcomp = the one component of all its sources, or -1; the
 // component holding most of them (wmajor) and their bits (wmask), so that the
@@ -120,7 +55,7 @@ __global__ void cc_flatten(int32_t n, const int32_t *L, int32_t *comp) {
 // word bit by bit only for nodes of the word's minor components.
 // One warp per word: a vote settles the common case of a word inside one
 // component; lane 0 counts the components of a mixed word.
-__global__ void word_components(int32_t n, int32_t W, const int32_t *comp, int32_t *wcomp, int32_t *wmajor,
+__device__ void word_components(int32_t n, int32_t W, const int32_t *comp, int32_t *wcomp, int32_t *wmajor,
                                 unsigned long long *wmask) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -162,37 +97,121 @@ __global__ void word_components(int32_t n, int32_t W, const int32_t *comp, int32
     }
 }
 
-__device__ __forceinline__ int degree_bucket(int deg) { return 31 - __clz(deg + 1); }
+struct PrepParams {
+    int32_t n, W;
+    const int32_t *row_ptr, *col_idx;
+    int32_t *L;                     // [n] union-find labels (scratch)
+    int32_t *ctl;                   // [0] status, [2..3] barrier, [4] largest component, [6..7] sum deg^2
+    int32_t directed;
+    int32_t *comp, *wcomp, *wmajor;
+    unsigned long long *wmask;
+    // scattered degree order (null order: another kernel writes it)
+    int32_t *bins;                  // [64] zeroed: counts per bucket, then each bucket's next position
+    int32_t *order;                 // [n + 1]
+    int4 *info;                     // [n]
+};
 
-// Degree order, scattered: nodes by decreasing degree bucket, in whatever order
-// the atomics hand out positions within a bucket (which interleaves the graph's
-// regions).  Taken when the BFS's bitsets fit in L2.
-__global__ void bucket_count(int32_t n, const int32_t *row_ptr, int32_t *counts) {
+// The whole preparation in one cooperative launch, phases separated by grid
+// barriers:
+//   A. labels L[v] = v; per-bucket degree counts; the sum of squared degrees;
+//   B. every node links to its first two neighbours; the bucket counts become
+//      each bucket's first position (heaviest bucket first);
+//   C. compression; every node takes a position in its bucket (the scattered order);
+//   D. the label shared by most of 64 evenly spaced nodes names the largest
+//      component found so far; info[i] for every order position;
+//   E. nodes outside that component link to their remaining neighbours (in a
+//      directed graph every node links all its arcs);
+//   F. comp[v] = the root of v's tree, the smallest id of its component;
+//   G. the words' components.
+// Components by sampled union-find after Sutton et al., "Optimizing Parallel
+// Graph Connectivity Computation via Subgraph Sampling" (2018).
+__global__ void __launch_bounds__(256) prep_fused(const PrepParams p) {
+    unsigned *bar = reinterpret_cast<unsigned *>(p.ctl + 2);
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    const int n = p.n;
     __shared__ int32_t local[32];
+    __shared__ int s_lab[64], s_cnt[64];
+    // A
     if (threadIdx.x < 32) local[threadIdx.x] = 0;
     __syncthreads();
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        atomicAdd(&local[degree_bucket(row_ptr[v + 1] - row_ptr[v])], 1);
+    unsigned long long sq = 0;
+    for (int v = tid; v < n; v += nthreads) {
+        p.L[v] = v;
+        const int d = p.row_ptr[v + 1] - p.row_ptr[v];
+        if (p.order) atomicAdd(&local[degree_bucket(d)], 1);
+        sq += (unsigned long long)d * (unsigned long long)d;
+    }
+    for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+    if ((threadIdx.x & 31) == 0 && sq) atomicAdd(reinterpret_cast<unsigned long long *>(p.ctl + 6), sq);
     __syncthreads();
-    if (threadIdx.x < 32 && local[threadIdx.x]) atomicAdd(&counts[threadIdx.x], local[threadIdx.x]);
-}
-
-// cursor[b] = number of nodes in buckets above b (heaviest bucket first);
-// *n_heavy = nodes in buckets >= QC_HEAVY_BUCKET (a prefix of the order).
-__global__ void bucket_scan(const int32_t *counts, int32_t *cursor, int32_t *n_heavy) {
-    if (threadIdx.x == 0) {
+    if (p.order && threadIdx.x < 32 && local[threadIdx.x]) atomicAdd(&p.bins[threadIdx.x], local[threadIdx.x]);
+    if (!qcdev::grid_barrier(bar, p.ctl)) return;
+    // B
+    for (int v = tid; v < n; v += nthreads) {
+        const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
+        for (int e = beg; e < end && e < beg + 2; ++e)
+            uf_link(p.L, v, qcdev::checked_id(p.col_idx[e], n, qcdev::DBG_PREP));
+    }
+    if (p.order && tid == 0) {
         int acc = 0;
         for (int b = 31; b >= 0; --b) {
-            cursor[b] = acc;
-            acc += counts[b];
-            if (b == QC_HEAVY_BUCKET) *n_heavy = acc;
+            p.bins[32 + b] = acc;
+            acc += p.bins[b];
+            if (b == QC_HEAVY_BUCKET) p.order[n] = acc;
         }
     }
-}
-
-__global__ void bucket_scatter(int32_t n, const int32_t *row_ptr, int32_t *cursor, int32_t *order) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        order[atomicAdd(&cursor[degree_bucket(row_ptr[v + 1] - row_ptr[v])], 1)] = v;
+    if (!qcdev::grid_barrier(bar, p.ctl)) return;
+    // C
+    uf_compress(p.L, n, tid, nthreads);
+    if (p.order)
+        for (int v = tid; v < n; v += nthreads)
+            p.order[atomicAdd(&p.bins[32 + degree_bucket(p.row_ptr[v + 1] - p.row_ptr[v])], 1)] = v;
+    if (!qcdev::grid_barrier(bar, p.ctl)) return;
+    // D
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < 64) s_lab[threadIdx.x] = p.L[(int)(((long long)threadIdx.x * (n - 1)) / 63)];
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            int c = 0;
+            for (int i = 0; i < 64; ++i) c += (s_lab[i] == s_lab[threadIdx.x]);
+            s_cnt[threadIdx.x] = c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int best = 0;
+            for (int i = 1; i < 64; ++i)
+                if (s_cnt[i] > s_cnt[best]) best = i;
+            p.ctl[4] = p.directed ? -1 : s_lab[best];
+        }
+    }
+    if (p.order)
+        for (int i = tid; i < n; i += nthreads) {
+            const int v = p.order[i];
+            p.info[i] = make_int4(v, p.row_ptr[v], p.row_ptr[v + 1], 0);
+        }
+    if (!qcdev::grid_barrier(bar, p.ctl)) return;
+    // E
+    const int giant = *(volatile int32_t *)(p.ctl + 4);
+    const int lane = threadIdx.x & 31;
+    for (int v = tid >> 5; v < n; v += nthreads >> 5) {
+        if (*(volatile int32_t *)(p.L + v) == giant) continue;
+        const int end = p.row_ptr[v + 1];
+        for (int e = p.row_ptr[v] + 2 + lane; e < end; e += 32)
+            uf_link(p.L, v, qcdev::checked_id(p.col_idx[e], n, qcdev::DBG_PREP));
+    }
+    if (!qcdev::grid_barrier(bar, p.ctl)) return;
+    // F
+    for (int v = tid; v < n; v += nthreads) {
+        const volatile int32_t *VL = p.L;
+        int x = VL[v];
+        while (VL[x] != x) x = VL[x];
+        p.comp[v] = x;
+    }
+    if (!qcdev::grid_barrier(bar, p.ctl)) return;
+    // G
+    word_components(n, p.W, p.comp, p.wcomp, p.wmajor, p.wmask);
+    if (tid == 0) p.ctl[1] = 1;
 }
 
 // Degree order, stable: nodes by decreasing degree bucket and, within a bucket,
@@ -286,20 +305,12 @@ __global__ void __launch_bounds__(256) order_place(int32_t n, int32_t chunk, con
 }
 
 // info[i] = {order[i], its row start, its row end, 0}: one 16-byte load gives a
-// BFS item everything it needs before it reads the neighbour ids.  Also adds up
-// the squared degrees into *deg2 (zeroed before): the number of neighbour-of-
-// neighbour ids a two-hop expansion of every node reads.
-__global__ void order_info(int32_t n, const int32_t *row_ptr, const int32_t *order, int4 *info,
-                           unsigned long long *deg2) {
-    unsigned long long sq = 0;
+// BFS item everything it needs before it reads the neighbour ids.
+__global__ void order_info(int32_t n, const int32_t *row_ptr, const int32_t *order, int4 *info) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int v = order[i];
-        const int b = row_ptr[v], e = row_ptr[v + 1];
-        info[i] = make_int4(v, b, e, 0);
-        sq += (unsigned long long)(e - b) * (unsigned long long)(e - b);
+        info[i] = make_int4(v, row_ptr[v], row_ptr[v + 1], 0);
     }
-    for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
-    if ((threadIdx.x & 31) == 0 && sq) atomicAdd(deg2, sq);
 }
 
 __global__ void first_rows(int32_t n, const int32_t *row_ptr, int32_t *hist) {
@@ -331,44 +342,52 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
     QC_TRY(g->wmask.allocate(ctx, sizeof(unsigned long long) * (size_t)W, stream));
     QC_TRY(g->order.allocate(ctx, sizeof(int32_t) * (size_t)(n + 1), stream));
     QC_TRY(g->oinfo.allocate(ctx, sizeof(int4) * (size_t)n, stream));
-    qc_buffer p, bins;
-    QC_TRY(p.allocate(ctx, sizeof(int32_t) * (size_t)n, stream));
-    const int tb = 256;
-    const int nb = qc_ceil_div(n, tb) < 4 * ctx->num_sms ? qc_ceil_div(n, tb) : 4 * ctx->num_sms;
-    // components: one thread per node is all the link phases use; more blocks only
-    // make each of the kernel's grid barriers dearer
-    const int wb = qc_ceil_div(n, 256) < 8 * ctx->num_sms ? qc_ceil_div(n, 256) : 8 * ctx->num_sms;
+    qc_buffer L, bins;
+    QC_TRY(L.allocate(ctx, sizeof(int32_t) * (size_t)n, stream));
     const int32_t *rp = g->row_ptr.as<int32_t>();
     const int32_t *ci = g->col_idx.as<int32_t>();
+    // the scattered degree order is written inside the fused launch; the stable one
+    // (bitsets beyond L2) by its own kernels afterwards
+    const double bitset_bytes = 2.0 * 8.0 * (double)n * (double)qc_bfs_chunk_words(ctx, n);
+    const bool stable = bitset_bytes > (double)ctx->l2_bytes;
+    const int ob = std::max(1, std::min(qc_ceil_div(n, 256), 4 * ctx->num_sms));
+    QC_TRY(bins.allocate(ctx, sizeof(int32_t) * (stable ? 64 * (size_t)ob : 64), stream));
+    QC_TRY(g->prep_ctl.allocate(ctx, sizeof(int32_t) * 8, stream));
+    QC_CUDA_TRY(ctx, cudaMemsetAsync(g->prep_ctl.ptr, 0, g->prep_ctl.bytes, stream));
+    if (!stable) QC_CUDA_TRY(ctx, cudaMemsetAsync(bins.ptr, 0, bins.bytes, stream));
     {
+        // one thread per node is all the link phases use; more blocks only make each
+        // grid barrier dearer
         int per_sm = 0;
-        QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)cc_afforest,
-                                                                       256, 0));
+        QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)prep_fused, 256, 0));
+        const int wb = qc_ceil_div(n, 256) < 8 * ctx->num_sms ? qc_ceil_div(n, 256) : 8 * ctx->num_sms;
         int blocks = per_sm * qc_coop_sms(ctx);
         if (blocks > wb) blocks = wb;
         if (blocks < 1) blocks = 1;
-        QC_TRY(g->prep_ctl.allocate(ctx, sizeof(int32_t) * 8, stream));
-        QC_CUDA_TRY(ctx, cudaMemsetAsync(g->prep_ctl.ptr, 0, g->prep_ctl.bytes, stream));
-        int32_t n_ = n, directed = g->directed ? 1 : 0;
-        int32_t *L = p.as<int32_t>(), *c = g->prep_ctl.as<int32_t>();
-        void *args[] = {&n_, (void *)&rp, (void *)&ci, &L, &c, &directed};
-        QC_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)cc_afforest, dim3(blocks), dim3(256), args, 0,
+        PrepParams pp;
+        pp.n = n;
+        pp.W = W;
+        pp.row_ptr = rp;
+        pp.col_idx = ci;
+        pp.L = L.as<int32_t>();
+        pp.ctl = g->prep_ctl.as<int32_t>();
+        pp.directed = g->directed ? 1 : 0;
+        pp.comp = g->comp.as<int32_t>();
+        pp.wcomp = g->wcomp.as<int32_t>();
+        pp.wmajor = g->wmajor.as<int32_t>();
+        pp.wmask = g->wmask.as<unsigned long long>();
+        pp.bins = stable ? nullptr : bins.as<int32_t>();
+        pp.order = stable ? nullptr : g->order.as<int32_t>();
+        pp.info = stable ? nullptr : g->oinfo.as<int4>();
+        void *args[] = {(void *)&pp};
+        QC_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void *)prep_fused, dim3(blocks), dim3(256), args, 0,
                                                      stream));
         QC_LAUNCHED(ctx);
         g->prep_checked = false;
     }
-    cc_flatten<<<nb, tb, 0, stream>>>(n, p.as<int32_t>(), g->comp.as<int32_t>());
-    QC_LAUNCHED(ctx);
-    word_components<<<qc_ceil_div(W, 8), 256, 0, stream>>>(n, W, g->comp.as<int32_t>(), g->wcomp.as<int32_t>(),
-                                                            g->wmajor.as<int32_t>(),
-                                                            g->wmask.as<unsigned long long>());
-    QC_LAUNCHED(ctx);
-    const double bitset_bytes = 2.0 * 8.0 * (double)n * (double)qc_bfs_chunk_words(ctx, n);
-    if (bitset_bytes > (double)ctx->l2_bytes) {
+    if (stable) {
         // stable degree order: blocks own contiguous ranges of node ids
-        const int ob = std::max(1, std::min(qc_ceil_div(n, 256), 4 * ctx->num_sms));
         const int chunk = qc_ceil_div(n, ob);
-        QC_TRY(bins.allocate(ctx, sizeof(int32_t) * 64 * (size_t)ob, stream));
         int32_t *counts = bins.as<int32_t>(), *offsets = counts + 32 * (size_t)ob;
         order_counts<<<ob, 256, 0, stream>>>(n, chunk, rp, counts);
         QC_LAUNCHED(ctx);
@@ -376,20 +395,10 @@ qc_status qc_graph_prepare(qc_graph *g, cudaStream_t stream) {
         QC_LAUNCHED(ctx);
         order_place<<<ob, 256, 0, stream>>>(n, chunk, rp, offsets, g->order.as<int32_t>());
         QC_LAUNCHED(ctx);
-    } else {
-        QC_TRY(bins.allocate(ctx, sizeof(int32_t) * 64, stream));
-        QC_CUDA_TRY(ctx, cudaMemsetAsync(bins.ptr, 0, bins.bytes, stream));
-        bucket_count<<<nb, tb, 0, stream>>>(n, rp, bins.as<int32_t>());
-        QC_LAUNCHED(ctx);
-        bucket_scan<<<1, 32, 0, stream>>>(bins.as<int32_t>(), bins.as<int32_t>() + 32,
-                                          g->order.as<int32_t>() + n);
-        QC_LAUNCHED(ctx);
-        bucket_scatter<<<nb, tb, 0, stream>>>(n, rp, bins.as<int32_t>() + 32, g->order.as<int32_t>());
+        const int nb = qc_ceil_div(n, 256) < 4 * ctx->num_sms ? qc_ceil_div(n, 256) : 4 * ctx->num_sms;
+        order_info<<<nb, 256, 0, stream>>>(n, rp, g->order.as<int32_t>(), g->oinfo.as<int4>());
         QC_LAUNCHED(ctx);
     }
-    order_info<<<nb, tb, 0, stream>>>(n, rp, g->order.as<int32_t>(), g->oinfo.as<int4>(),
-                                      const_cast<unsigned long long *>(qc_graph_deg2(g)));
-    QC_LAUNCHED(ctx);
     g->prepared = true;
     return QC_OK;
 }

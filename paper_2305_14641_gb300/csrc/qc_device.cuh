@@ -24,7 +24,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).
-// bar[0] counts arrivals, bar[1] is the generation.  The wait is bounded: once
+// bar[0] counts arrivals over the whole launch and is never reset: the k-th
+// barrier (k = 1, 2, ...) opens once the count reaches k x gridDim.x, so a block
+// only adds one and waits for that multiple (the launch starts with bar[0] = 0,
+// and passes fewer than 2^32 / gridDim.x barriers).  The wait is bounded: once
 // timeout_ns has passed (global timer) the block records ST_TIMEOUT in *status
 // and returns false; every block then leaves at its next barrier.  When
 // waited_ns is given, thread 0 of a block that waited stores how long it did.
@@ -34,19 +37,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *status,
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = bar + 1;
-        const unsigned gen = *vgen;
         __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        const unsigned ticket = atomicAdd(bar, 1u);
+        const unsigned target = ticket - ticket % gridDim.x + gridDim.x;
         int ok = 1;
-        if (arrived == gridDim.x) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        if (ticket + 1u != target) {
+            volatile unsigned *count = bar;
             const unsigned long long t0 = global_ns();
             unsigned long long polls = 0, now = t0;
-            while (*vgen == gen) {
+            while ((int)(*count - target) < 0) {
                 now = global_ns();
                 if (now - t0 > timeout_ns || ++polls > BARRIER_MAX_POLLS) {
                     atomicExch(status, ST_TIMEOUT);

@@ -202,6 +202,18 @@ struct qc_bfs_scratch {
     int32_t mask_ratio = 0;
     int32_t two_hop = 1;                    // levels 1-2 from the CSR: 0 never, 1 sparse graphs, 2 always
     qc_buffer visA, visB, sat, ctl, wl, fmask;
+    qc_buffer cursor;                       // two-hop set-up over several chunks: 2 x int32[n]
+    // Gives every buffer back (stream-ordered on the stream each was allocated on,
+    // so call it while those streams exist).
+    void release() {
+        visA.release();
+        visB.release();
+        sat.release();
+        ctl.release();
+        wl.release();
+        fmask.release();
+        cursor.release();
+    }
 };
 qc_status qc_bfs_scratch_init(qc_graph *g, qc_bfs_scratch &bs, cudaStream_t stream);
 // prep.cu: device address of the sum over nodes of degree^2 (written by the preparation)
@@ -267,9 +279,9 @@ int32_t *qc_cta_flags(qc_cta_launch *L);
 void qc_cta_launch_free(qc_cta_launch *L);
 
 // validate.cu
-// row_ptr_checked: the caller already checked row_ptr on the host (skip that pass).
+// One launch checks the whole CSR (row_ptr included) and waits for the verdict.
 qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
-                          const int32_t *col_idx_dev, bool symmetric, bool row_ptr_checked, cudaStream_t stream);
+                          const int32_t *col_idx_dev, bool symmetric, cudaStream_t stream);
 qc_status qc_validate_hist(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
                            const int32_t *hist_dev, int32_t D, cudaStream_t stream);
 

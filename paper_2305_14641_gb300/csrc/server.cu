@@ -560,21 +560,31 @@ void qc_server_destroy(qc_server *s) {
     if (s->sched.joinable()) s->sched.join();
     for (std::thread &t : s->large)
         if (t.joinable()) t.join();
+    // requests' memory is given back on the streams it was allocated on, so those
+    // streams go only after it
+    for (Slot &sl : s->slots)
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+    for (cudaStream_t ls : s->large_streams)
+        if (ls) cudaStreamSynchronize(ls);
+    for (auto &kv : s->reqs) {
+        Req *r = kv.second.get();
+        if (r->g && !r->borrowed) qc_graph_destroy(r->g);
+        r->g = nullptr;
+        r->labels_dev.release();
+    }
     for (Slot &sl : s->slots) {
+        if (sl.launch) qc_cta_launch_free(sl.launch);
         if (sl.stream) {
             cudaStreamSynchronize(sl.stream);
             cudaStreamDestroy(sl.stream);
         }
-        if (sl.launch) qc_cta_launch_free(sl.launch);
         if (sl.pinned) cudaFreeHost(sl.pinned);
     }
     for (cudaStream_t ls : s->large_streams)
-        if (ls) cudaStreamDestroy(ls);
-    for (auto &kv : s->reqs) {
-        Req *r = kv.second.get();
-        if (r->g && !r->borrowed) qc_graph_destroy(r->g);
-        r->labels_dev.release();
-    }
+        if (ls) {
+            cudaStreamSynchronize(ls);
+            cudaStreamDestroy(ls);
+        }
     s->ctx->coop_sm_share = s->saved_share;
     delete s;
 }

@@ -149,12 +149,7 @@ qc_sweep::~qc_sweep() {
     parent.release();
     keys.release();
     dtab.release();
-    bs.visA.release();
-    bs.visB.release();
-    bs.sat.release();
-    bs.ctl.release();
-    bs.wl.release();
-    bs.fmask.release();
+    bs.release();
     if (cap) {
         cudaStreamSynchronize(cap);
         cudaStreamDestroy(cap);

@@ -13,22 +13,23 @@ enum : int32_t {
     BAD_ASYMMETRIC = 16,
 };
 
-__global__ void check_row_ptr(int32_t n, int64_t nnz, const int32_t *row_ptr, int32_t *err) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        if (row_ptr[v + 1] < row_ptr[v]) atomicOr(err, BAD_ROW_PTR);
-        if (v == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz)) atomicOr(err, BAD_ROW_PTR);
-    }
-}
-
-// One warp per row.  Safe to run only after check_row_ptr passed.
-__global__ void check_rows(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, bool symmetric,
-                           int32_t *err) {
+// One warp per row.  Every row bound is checked before it is used, so the scan
+// stays inside row_ptr[0..n] and col_idx[0..nnz) whatever the arrays hold:
+// row v's warp checks 0 <= row_ptr[v] <= row_ptr[v+1] <= nnz (which, over all v,
+// makes row_ptr non-decreasing within [0, nnz]); thread 0 checks the two ends.
+__global__ void check_csr(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx, bool symmetric,
+                          int32_t *err) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     int bad = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz)) bad |= BAD_ROW_PTR;
     for (int v = warp; v < n; v += nwarps) {
         const int beg = row_ptr[v], end = row_ptr[v + 1];
+        if (beg < 0 || beg > end || (int64_t)end > nnz) {
+            bad |= BAD_ROW_PTR;
+            continue;
+        }
         for (int e = beg + lane; e < end; e += 32) {
             const int u = col_idx[e];
             if (u < 0 || u >= n) { bad |= BAD_COLUMN; continue; }
@@ -37,10 +38,12 @@ __global__ void check_rows(int32_t n, const int32_t *row_ptr, const int32_t *col
             if (!symmetric) continue;
             // symmetric: v must appear in row u (binary search; rows may be unsorted
             // only if BAD_ORDER is also reported)
-            int lo = row_ptr[u], hi = row_ptr[u + 1] - 1;
+            const int64_t ulo = row_ptr[u], uend = row_ptr[u + 1];
+            if (ulo < 0 || uend < ulo || uend > nnz) { bad |= BAD_ROW_PTR; continue; }
+            int lo = (int)ulo, hi = (int)uend - 1;
             bool found = false;
             while (lo <= hi) {
-                const int mid = (lo + hi) >> 1;
+                const int mid = lo + ((hi - lo) >> 1);
                 const int x = col_idx[mid];
                 if (x == v) { found = true; break; }
                 if (x < v) lo = mid + 1; else hi = mid - 1;
@@ -110,31 +113,21 @@ qc_status qc_validate_hist(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
 }
 
 qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
-                          const int32_t *col_idx, bool symmetric, bool row_ptr_checked, cudaStream_t stream) {
+                          const int32_t *col_idx, bool symmetric, cudaStream_t stream) {
     qc_buffer err;
     QC_TRY(err.allocate(ctx, sizeof(int32_t), stream));
     QC_CUDA_TRY(ctx, cudaMemsetAsync(err.ptr, 0, sizeof(int32_t), stream));
-    int32_t h_err = 0;
-    if (!row_ptr_checked) {
-        // the row scan indexes through row_ptr, so row_ptr is checked (and waited for) first
-        const int blocks = qc_ceil_div(n, 256) < 4 * ctx->num_sms ? qc_ceil_div(n, 256) : 4 * ctx->num_sms;
-        check_row_ptr<<<blocks, 256, 0, stream>>>(n, nnz, row_ptr, err.as<int32_t>());
-        QC_LAUNCHED(ctx);
-        QC_CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
-        QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
-        if (h_err) {
-            qc_set_error(ctx, "invalid CSR: row_ptr is not 0-based, non-decreasing and ending at nnz");
-            return QC_ERR_INVALID_GRAPH;
-        }
-    }
-    if (nnz == 0) return QC_OK;
+    qc_pinned pin(ctx);
+    QC_TRY(pin.acquire());
+    int32_t &h_err = *static_cast<int32_t *>(pin.ptr);
     const int wblocks = qc_ceil_div(n, 8) < 8 * ctx->num_sms ? qc_ceil_div(n, 8) : 8 * ctx->num_sms;
-    check_rows<<<wblocks, 256, 0, stream>>>(n, row_ptr, col_idx, symmetric, err.as<int32_t>());
+    check_csr<<<wblocks, 256, 0, stream>>>(n, nnz, row_ptr, col_idx, symmetric, err.as<int32_t>());
     QC_LAUNCHED(ctx);
     QC_CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
     QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
     if (h_err) {
-        qc_set_error(ctx, "invalid CSR (flags 0x%x):%s%s%s%s", h_err,
+        qc_set_error(ctx, "invalid CSR (flags 0x%x):%s%s%s%s%s", h_err,
+                     (h_err & BAD_ROW_PTR) ? " row_ptr not 0-based, non-decreasing and ending at nnz;" : "",
                      (h_err & BAD_COLUMN) ? " column id out of range;" : "",
                      (h_err & BAD_ORDER) ? " row not strictly ascending;" : "",
                      (h_err & BAD_SELF_LOOP) ? " self-loop;" : "",

@@ -97,6 +97,9 @@ SIGNATURES = [
                                      c_int32_p, ctypes.c_void_p]),
     ("qc_solve", ctypes.c_int, [ctypes.c_void_p, c_double_p, ctypes.c_int32, ctypes.c_void_p,
                                 ctypes.c_void_p, c_int32_p, ctypes.c_void_p]),
+    ("qc_cluster", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_uint32, c_double_p, ctypes.c_int32, ctypes.c_void_p,
+                                  c_int32_p, ctypes.c_void_p]),
     ("qc_quality", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                   ctypes.POINTER(qc_quality_result), ctypes.c_void_p]),

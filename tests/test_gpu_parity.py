@@ -237,14 +237,59 @@ def test_invalid_inputs(qc, ctx):
         with pytest.raises(qc.QCError) as e:
             qc.Graph(ctx, r, c)
         assert e.value.status_name == "QC_ERR_INVALID_GRAPH", name
-    bad_rp = rp.copy(); bad_rp[2] = bad_rp[3] + 1
+    # row_ptr itself: decreasing, not starting at 0, ending past or before nnz,
+    # negative and huge entries; the device check reads every row bound before it
+    # indexes through it, so none of these reads outside the arrays
+    bad_rps = []
+    for pos, val in ((2, int(rp[3]) + 1), (0, 1), (-1, len(ci) + 5), (-1, len(ci) - 1), (1, -3),
+                     (2, 2**31 - 1), (3, -2**31)):
+        b = rp.copy()
+        b[pos] = val
+        bad_rps.append(b)
+    for bad_rp in bad_rps:
+        with pytest.raises(qc.QCError) as e:
+            qc.Graph(ctx, bad_rp, ci)
+        assert e.value.status_name == "QC_ERR_INVALID_GRAPH", bad_rp
+        assert "row_ptr" in str(e.value), str(e.value)
+        dev_bad = torch.tensor(bad_rp, device="cuda"), torch.tensor(ci, device="cuda")
+        with pytest.raises(qc.QCError) as e:
+            qc.Graph(ctx, *dev_bad)
+        assert e.value.status_name == "QC_ERR_INVALID_GRAPH", bad_rp
+    # the context is still usable
+    assert_solution_matches(qc, ctx, graph, [1.0])
+
+
+def test_cluster_one_call(qc, ctx):
+    """qc_cluster: a CSR (host or device) to labels (numpy, pinned host tensor,
+    CUDA tensor) in one call, against the oracle; graphs with several
+    components, directed arcs, no edges, and a path whose histogram outgrows the
+    first launch's rows (the BFS is rerun and the rest queued again); invalid
+    input is still reported by the call."""
+    sig = [0.7, 1.9]
+    graphs = [gg.planted_partition(3000, 12, 0.02, 0.001, gg.rng(71)),
+              gg.dcsbm(3000, 8, 2.5, 10.0, 200.0, 0.1, gg.rng(72)),
+              gg.directed_erdos_renyi(2000, 3.0 / 2000, gg.rng(73)), gg.path(300),
+              gg.Graph(50, np.zeros(51, dtype=np.int32), np.zeros(0, dtype=np.int32), name="empty")]
+    for graph in graphs:
+        ref = oracle.solve(graph, sig)
+        directed = getattr(graph, "directed", False)
+        lab, counts = qc.cluster(ctx, graph.row_ptr, graph.col_idx, sig, directed=directed)
+        assert np.array_equal(lab, ref.labels), graph.name
+        assert counts == ref.n_clusters, graph.name
+        pinned = torch.empty((2, graph.n), dtype=torch.int32).pin_memory()
+        qc.cluster(ctx, graph.row_ptr, graph.col_idx, sig, labels_out=pinned, counts=False, directed=directed)
+        assert np.array_equal(pinned.numpy(), ref.labels), graph.name
+        dev = torch.empty((2, graph.n), dtype=torch.int32, device="cuda")
+        _, c2 = qc.cluster(ctx, torch.tensor(graph.row_ptr, device="cuda"), torch.tensor(graph.col_idx, device="cuda"),
+                           sig, labels_out=dev, directed=directed)
+        assert np.array_equal(dev.cpu().numpy(), ref.labels), graph.name
+        assert c2 == ref.n_clusters, graph.name
     with pytest.raises(qc.QCError) as e:
-        qc.Graph(ctx, bad_rp, ci)
+        qc.cluster(ctx, np.array([0, 1, 1], dtype=np.int32), np.array([1], dtype=np.int32), sig)
     assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
-    dev_bad = torch.tensor(bad_rp, device="cuda"), torch.tensor(ci, device="cuda")
     with pytest.raises(qc.QCError) as e:
-        qc.Graph(ctx, *dev_bad)
-    assert e.value.status_name == "QC_ERR_INVALID_GRAPH"
+        qc.cluster(ctx, graphs[0].row_ptr, graphs[0].col_idx, [1.0, float("nan")])
+    assert e.value.status_name == "QC_ERR_INVALID_ARG"
 
 
 def test_device_input_and_allocators(qc):

@@ -74,6 +74,15 @@ def test_deeper_than_the_rows(qc, ctx):
 def test_many_chunks_and_directed(qc, ctx, monkeypatch):
     monkeypatch.setenv("QCGRAPH_CHUNK_WORDS", "3")
     check_plan(qc, ctx, gg.planted_partition(700, 5, 0.05, 0.004, gg.rng(63)), [0.9, 2.2])
+    # chunks of 96 words on a sparse graph: the two-hop set-up with chunk cursors
+    # inside the captured plan; the plan gives all its memory back before its
+    # stream goes, so the next call on the context runs clean
+    monkeypatch.setenv("QCGRAPH_CHUNK_WORDS", "96")
+    graph = gg.planted_partition(9000, 30, 0.012, 0.0002, gg.rng(65))
+    check_plan(qc, ctx, graph, [0.7, 1.6])
+    ref = oracle.solve(graph, [1.1])
+    lab, counts = qc.cluster(ctx, graph.row_ptr, graph.col_idx, [1.1])
+    assert np.array_equal(lab, ref.labels) and counts == ref.n_clusters
     monkeypatch.delenv("QCGRAPH_CHUNK_WORDS")
     check_plan(qc, ctx, gg.directed_planted_partition(1500, 6, 0.02, 0.001, gg.rng(64)), [0.8, 2.5])
 
