@@ -56,7 +56,7 @@ WORKLOAD = ("dcsbm-16384: degree-corrected SBM, N=16384, 32 equal communities, p
             "degrees (density exponent 2.5, mean 16, max 512), mixing 0.1, seed 1; sigma sweep of 16 "
             "values log-spaced 0.5-4.0 reusing one histogram")
 METRIC = "clusterings/s"
-PROFILE = os.path.join(ROOT, "profiles", "bfs_persistent_dcsbm16384.md")
+PROFILE = os.path.join(ROOT, "profiles", "bfs_dcsbm16384.md")
 
 # single-graph workloads: generator, description, the ncu summary holding the BFS
 # kernel's DRAM traffic per launch, and how many nodes the CPU baseline samples
@@ -73,7 +73,7 @@ SINGLE = {
     "sbm262144": {"make": lambda: gg.sbm262144(),
                   "desc": ("sbm-262144: SBM, N=262144, 256 equal communities of 1024, mean degree 20, "
                            "mixing 0.15, seed 2; sigma 1.5"),
-                  "profile": os.path.join(ROOT, "profiles", "bfs_persistent_sbm262144.md"),
+                  "profile": os.path.join(ROOT, "profiles", "bfs_sbm262144.md"),
                   "cpu_sample_nodes": 512, "steps": 3},
 }
 KERNEL_SRC = [os.path.join(ROOT, "paper_2305_14641_gb300", "csrc", f) for f in ("bfs.cu", "qc_device.cuh")]
@@ -438,7 +438,8 @@ def bench_ours(args, graph, sigmas, spec):
                        "captured": plan_info["captured"] if plan_info else None},
             "gteps": edges * world * args.steps / (total_ms / 1000.0) / 1e9,
             "bfs_gteps": (edges / (bfs_ms / 1000.0) / 1e9) if bfs_ms > 0 else None,
-            "roofline": {"kernel": "bfs_persistent", "bound": "hbm", "achieved": achieved,
+            "roofline": {"kernel": "bfs_two_hop + bfs_persistent (one BFS launch of a source chunk)",
+                         "bound": "hbm", "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
                          "traffic": traffic,
@@ -446,8 +447,8 @@ def bench_ours(args, graph, sigmas, spec):
                          "bytes_model": "compulsory HBM bytes per launch (a lower bound): CSR, node order, row "
                                         "bounds, components and per-word masks read once, histogram rows written "
                                         "once, and per level the open (node, tile) rows read and written beyond "
-                                        "what L2 holds (counted on the device); the bitset buffers of this "
-                                        "workload fit in L2, so they add nothing",
+                                        "what L2 holds (counted on the device; the two-hop set-up's level-2 rows "
+                                        "written once); bitset buffers that fit in L2 add nothing",
                          "model_bytes_per_launch": (kstats["model_bytes"] / kstats["launches"]
                                                     if kstats["launches"] else None),
                          "model": "pull-all upper bound: per level 8*wn*(E+3N) bitset bytes + CSR + one "

@@ -1140,7 +1140,11 @@ static qc_status bfs_run(qc_graph *g, cudaStream_t stream, bool sync) {
             const size_t stamp_cap = std::min<size_t>((size_t)n + 3, (QC_PINNED_BYTES / 2 - 64) / 8);
             int32_t *h_pulled = reinterpret_cast<int32_t *>(static_cast<char *>(pin.ptr) + QC_PINNED_BYTES / 2);
             const size_t pulled_cap = std::min<size_t>((size_t)n + 2, (QC_PINNED_BYTES / 2) / 4);
+            // the squared-degree sum (bytes 16..23), to repeat the two-hop selection here
+            unsigned long long *h_deg2 = reinterpret_cast<unsigned long long *>(static_cast<char *>(pin.ptr) + 16);
             if (timing) {
+                QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_deg2, qc_graph_deg2(g), sizeof(unsigned long long),
+                                                 cudaMemcpyDeviceToHost, stream));
                 QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_stamp, stamps.ptr, sizeof(unsigned long long) * stamp_cap,
                                                  cudaMemcpyDeviceToHost, stream));
                 QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_pulled, pulled_counts(g, bs), sizeof(int32_t) * pulled_cap,
@@ -1165,6 +1169,17 @@ static qc_status bfs_run(qc_graph *g, cudaStream_t stream, bool sync) {
                 for (int l = start; l <= reached && (size_t)l < pulled_cap; ++l) {
                     const double state = 32.0 * tile_segs * (double)h_pulled[l];
                     if (state > (double)ctx->l2_bytes) min_bytes += state - (double)ctx->l2_bytes;
+                }
+                // a two-hop set-up (the kernels' own rule, evaluated the same way) writes every
+                // node's level-2 row once
+                const unsigned long long d2 = *h_deg2;
+                const bool two_hop =
+                    start == 2 && g->hist_rows > 2 && 2 * R <= TH_WORDS &&
+                    ((bs.two_hop == 1 && 4ull * d2 <= (unsigned long long)wn * (unsigned long long)g->nnz) ||
+                     (bs.two_hop == 2 && d2 < (1ull << 40)));
+                if (two_hop) {
+                    const double rows2 = 16.0 * (double)R * (double)n;
+                    if (rows2 > (double)ctx->l2_bytes) min_bytes += rows2 - (double)ctx->l2_bytes;
                 }
                 qc_record_kernel(ctx, "bfs_level", ms, passes * per_pass, min_bytes);
                 // stamp[l] opens level l (stamp[1] = launch start; the set-up covers levels 1-2);

@@ -44,7 +44,7 @@ def test_profile_figures_only_for_the_profiled_sources(tmp_path):
     assert bench.profile_value("l2_throughput_frac", str(stale)) is None
     assert bench.profile_traffic(str(tmp_path / "missing.md")) is None
     # the committed summaries carry the figures the bench reads
-    for name in ("bfs_persistent_dcsbm16384.md", "bfs_persistent_sbm262144.md"):
+    for name in ("bfs_dcsbm16384.md", "bfs_sbm262144.md"):
         committed = open(os.path.join(bench.ROOT, "profiles", name)).read()
         for key in ("traffic_bytes_per_launch", "kernel_source_sha256"):
             assert key + ":" in committed, (name, key)
