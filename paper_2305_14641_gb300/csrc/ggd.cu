@@ -12,9 +12,10 @@
 // is the same as comparing the doubles.  Keys are laid out node-major,
 // K[v * S + s], so one neighbour's S keys are one contiguous run.
 //
-// Parents: one warp per node; lane j scans neighbours j, j + 32, ... keeping
-// the best (key, id) for up to 16 sigma values, then a butterfly over the 32
-// lanes combines them (the result does not depend on the scan order).
+// Parents: one warp per node (a block per node of degree >= 127); lanes scan
+// the neighbours keeping the best (key, id) for up to 16 sigma values, then a
+// butterfly over the lanes (and, for a block, shared memory) combines them (the
+// result does not depend on the scan order).
 //
 // Roots: every (sigma, node) thread walks its chain with path halving
 // (parent[x] <- parent[parent[x]]) in a scratch parent array; concurrent walkers
@@ -55,64 +56,105 @@ __device__ __forceinline__ bool better(long long k, int u, long long bk, int bes
     return best < 0 || k < bk || (k == bk && u < best);
 }
 
-// Sigma values s0 .. s0 + sn - 1 (sn <= SG).  Lane = (slot, sigma): SG lanes
-// per slot, one sigma each; the 32/SG slots take every (32/SG)-th neighbour.
-// Neighbour ids come 32 at a time from one coalesced load and are broadcast by
-// shuffle; each lane keeps U key loads in flight.  log2(32/SG) butterfly steps
-// combine the slots.  Nodes go in `order` (heaviest first) when given, so the
-// longest rows start first.
+// Best (key, id) over the neighbours of one node for this lane's sigma: the
+// neighbour ids [beg, end) in 32-id chunks first, first + step, ... (step > 1 when
+// several warps share the row).  Lane = (slot, sigma): SG lanes per slot, one sigma
+// each; the 32/SG slots take every (32/SG)-th neighbour of a chunk.  Neighbour ids
+// come 32 at a time from one coalesced load and are broadcast by shuffle; each lane
+// keeps U key loads in flight.  log2(32/SG) butterfly steps combine the slots, so
+// lanes of slot 0 end with the warp's best.
 template <int SG>
-__global__ void __launch_bounds__(256) ggd_parent_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
+__device__ __forceinline__ void scan_row(int32_t n, const int32_t *__restrict__ col_idx,
+                                         const long long *__restrict__ K, int32_t S, int s, bool sok, int beg,
+                                         int end, int first, int step, long long &bk, int &best) {
+    constexpr int SLOTS = 32 / SG;
+    constexpr int U = 8;
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / SG;
+    for (int j0 = beg + 32 * first; j0 < end; j0 += 32 * step) {
+        const int cnt = min(32, end - j0);
+        const int myu = (lane < cnt) ? qcdev::checked_id(col_idx[j0 + lane], n, qcdev::DBG_GGD) : 0;
+        for (int m = 0; m < cnt; m += SLOTS * U) {
+            long long x[U];
+            int uu[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int t = m + k * SLOTS + slot;
+                uu[k] = __shfl_sync(FULL, myu, t & 31);
+                x[k] = (sok && t < cnt) ? K[(size_t)uu[k] * S + s] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int t = m + k * SLOTS + slot;
+                if (sok && t < cnt && better(x[k], uu[k], bk, best)) {
+                    bk = x[k];
+                    best = uu[k];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int off = SG; off < 32; off <<= 1) {
+        const long long ok = __shfl_xor_sync(FULL, bk, off);
+        const int ob = __shfl_xor_sync(FULL, best, off);
+        if (ob >= 0 && better(ok, ob, bk, best)) {
+            bk = ok;
+            best = ob;
+        }
+    }
+}
+
+// Parents for sigma values s0 .. s0 + sn - 1 (sn <= SG).  Nodes go in `order`
+// (heaviest first) when given: its first order[n] rows (degree >= 127) take a
+// whole block each, whose 8 warps split the row and meet in shared memory; every
+// other row takes one warp.
+template <int SG>
+__global__ void __launch_bounds__(256, 4) ggd_parent_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
                                                          const int32_t *__restrict__ col_idx,
                                                          const long long *__restrict__ K, int32_t S,
                                                          int32_t s0, int32_t sn,
                                                          const int32_t *__restrict__ order,
                                                          int32_t *__restrict__ parent) {
-    constexpr int SLOTS = 32 / SG;
-    constexpr int U = 8;
+    constexpr int WARPS = 8;
+    __shared__ long long red_k[WARPS][SG];
+    __shared__ int red_b[WARPS][SG];
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
     const int slot = lane / SG;
     const int sl = lane % SG;
     const bool sok = sl < sn;
     const int s = s0 + sl;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int i = warp; i < n; i += nwarps) {
-        const int v = order ? order[i] : i;
-        const int beg = row_ptr[v], end = row_ptr[v + 1];
+    const int heavy = order ? order[n] : 0;
+    for (int i = blockIdx.x; i < heavy; i += gridDim.x) {
+        const int v = order[i];
         long long bk = 0;
         int best = -1;
-        for (int j0 = beg; j0 < end; j0 += 32) {
-            const int cnt = min(32, end - j0);
-            const int myu = (lane < cnt) ? qcdev::checked_id(col_idx[j0 + lane], n, qcdev::DBG_GGD) : 0;
-            for (int m = 0; m < cnt; m += SLOTS * U) {
-                long long x[U];
-                int uu[U];
-#pragma unroll
-                for (int k = 0; k < U; ++k) {
-                    const int t = m + k * SLOTS + slot;
-                    uu[k] = __shfl_sync(FULL, myu, t & 31);
-                    x[k] = (sok && t < cnt) ? K[(size_t)uu[k] * S + s] : 0;
-                }
-#pragma unroll
-                for (int k = 0; k < U; ++k) {
-                    const int t = m + k * SLOTS + slot;
-                    if (sok && t < cnt && better(x[k], uu[k], bk, best)) {
-                        bk = x[k];
-                        best = uu[k];
-                    }
+        scan_row<SG>(n, col_idx, K, S, s, sok, row_ptr[v], row_ptr[v + 1], wib, WARPS, bk, best);
+        if (slot == 0) {
+            red_k[wib][sl] = bk;
+            red_b[wib][sl] = best;
+        }
+        __syncthreads();
+        if (wib == 0 && slot == 0 && sok) {
+            for (int w = 1; w < WARPS; ++w) {
+                const int ob = red_b[w][sl];
+                if (ob >= 0 && better(red_k[w][sl], ob, bk, best)) {
+                    bk = red_k[w][sl];
+                    best = ob;
                 }
             }
+            const long long own = K[(size_t)v * S + s];
+            parent[(size_t)s * n + v] = (best >= 0 && bk < own) ? best : v;
         }
-#pragma unroll
-        for (int off = SG; off < 32; off <<= 1) {
-            const long long ok = __shfl_xor_sync(FULL, bk, off);
-            const int ob = __shfl_xor_sync(FULL, best, off);
-            if (ob >= 0 && better(ok, ob, bk, best)) {
-                bk = ok;
-                best = ob;
-            }
-        }
+        __syncthreads();
+    }
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = heavy + warp; i < n; i += nwarps) {
+        const int v = order ? order[i] : i;
+        long long bk = 0;
+        int best = -1;
+        scan_row<SG>(n, col_idx, K, S, s, sok, row_ptr[v], row_ptr[v + 1], 0, 1, bk, best);
         if (slot == 0 && sok) {
             const long long own = K[(size_t)v * S + s];
             parent[(size_t)s * n + v] = (best >= 0 && bk < own) ? best : v;
