@@ -36,6 +36,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import faulthandler
 import hashlib
 import json
 import os
@@ -925,4 +926,6 @@ def main():
 
 
 if __name__ == "__main__":
+    # a crash in native code prints the Python stack of every thread to stderr
+    faulthandler.enable()
     main()

@@ -29,8 +29,10 @@
  *     scratch through the context's allocator (see qc_allocator).
  *   - An object made on a stream (a graph, a batch plan) allocates its memory
  *     stream-ordered on that stream and gives it back on the same stream when it
- *     is destroyed, so the stream must outlive the object.  Objects that own a
- *     stream (sweep plans, servers) give their memory back before destroying it.
+ *     is destroyed, so the stream must outlive the object.  Streams the library
+ *     makes itself (for sweep and batch plans and servers) belong to the context
+ *     and live until qc_context_destroy, so a graph that such a plan or server
+ *     prepared can be destroyed after it.
  *   - There is no CPU fallback: without a usable GPU every call that needs one
  *     returns QC_ERR_CUDA.
  */

@@ -392,7 +392,10 @@ struct qc_batch {
     ~qc_batch() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
-        if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (cap_stream) {
+            cudaStreamSynchronize(cap_stream);
+            qc_stream_release(ctx, cap_stream, 0);
+        }
     }
 };
 
@@ -678,7 +681,7 @@ qc_status qc_batch_create(qc_ctx *ctx, int32_t n_graphs, qc_graph *const *graphs
         b->c = cands[choice % 16].second;
         b->sparse_degree = SPARSE_CANDIDATES[choice / 16];
         // capture the batched solve
-        QC_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+        QC_CUDA_TRY(ctx, qc_stream_acquire(ctx, 0, &b->cap_stream));
         QC_CUDA_TRY(ctx, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
         qc_status st = batch_enqueue(b, b->cap_stream, b->threads, b->c, b->sparse_degree);
         cudaGraph_t graph = nullptr;

@@ -57,6 +57,35 @@ void qc_mem_free(qc_ctx *ctx, void *ptr, size_t bytes, cudaStream_t stream) {
 
 qc_ctx::~qc_ctx() {
     for (void *p : pinned_free) cudaFreeHost(p);
+    for (cudaStream_t s : all_streams) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+}
+
+cudaError_t qc_stream_acquire(qc_ctx *ctx, int priority, cudaStream_t *out) {
+    {
+        std::lock_guard<std::mutex> lk(ctx->streams_mu);
+        for (size_t i = 0; i < ctx->spare_streams.size(); ++i)
+            if (ctx->spare_streams[i].first == priority) {
+                *out = ctx->spare_streams[i].second;
+                ctx->spare_streams.erase(ctx->spare_streams.begin() + (std::ptrdiff_t)i);
+                return cudaSuccess;
+            }
+    }
+    cudaStream_t s = nullptr;
+    const cudaError_t e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, priority);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(ctx->streams_mu);
+    ctx->all_streams.push_back(s);
+    *out = s;
+    return cudaSuccess;
+}
+
+void qc_stream_release(qc_ctx *ctx, cudaStream_t s, int priority) {
+    if (!s) return;
+    std::lock_guard<std::mutex> lk(ctx->streams_mu);
+    ctx->spare_streams.emplace_back(priority, s);
 }
 
 qc_status qc_pinned::acquire() {
@@ -100,11 +129,13 @@ void qc_record_kernel(qc_ctx *ctx, const char *kernel, double ms, double model_b
 // width, while a row's gather reads R contiguous 16-byte segments per
 // neighbour, so wide chunks stay efficient after their bitsets leave L2.
 // Measured on GB300 (SBM graphs of mean degree 20, n = 2^15 .. 2^19), the
-// fastest width keeps the two bitset buffers near four times L2, between 64
+// fastest width keeps the two bitset buffers near eight times L2, between 64
 // and 256 words; below that the per-level fixed cost dominates (sizing the
-// buffers to half of L2 ran 2-3x slower at n >= 2^18).  The width is a
-// multiple of 64 words (whole 32-segment tiles) chosen so that the chunks
-// split the W words evenly.  QCGRAPH_CHUNK_WORDS overrides the choice (tests
+// buffers to half of L2 ran 2-3x slower at n >= 2^18).  With the two-hop
+// set-up, whose cost grows slowly with the width, n = 2^18 solves in 78.4 ms
+// at 256 words against 82.7 ms at 128 (four times L2) and 111 ms at 64.  The
+// width is a multiple of 64 words (whole 32-segment tiles) chosen so that the
+// chunks split the W words evenly.  QCGRAPH_CHUNK_WORDS overrides the choice (tests
 // use it to force many chunks).
 int32_t qc_bfs_chunk_words(const qc_ctx *ctx, int32_t n) {
     const int64_t W = ((int64_t)n + 63) / 64;
@@ -114,7 +145,7 @@ int32_t qc_bfs_chunk_words(const qc_ctx *ctx, int32_t n) {
         if (wc < 1) wc = 1;
     } else {
         const size_t l2 = ctx->l2_bytes ? ctx->l2_bytes : (size_t)96 << 20;
-        int64_t target = (int64_t)(4 * l2 / (2 * 8 * (size_t)(n > 0 ? n : 1)));
+        int64_t target = (int64_t)(8 * l2 / (2 * 8 * (size_t)(n > 0 ? n : 1)));
         target = std::min<int64_t>(std::max<int64_t>(target, 64), 256);
         const int64_t chunks = (W + target - 1) / target;
         wc = ((W + chunks - 1) / chunks + 63) / 64 * 64;
@@ -327,12 +358,14 @@ qc_status qc_potential(qc_graph *g, const double *sigmas, int32_t n_sigma, doubl
 }
 
 // Descent and roots queued on `stream`; roots per sigma counted into roots_dev.
+// keys: V's descent keys when the potential kernel wrote them, else null.
 static qc_status ggd_enqueue(qc_graph *g, const double *V, int32_t n_sigma, int32_t *labels_out,
-                             int32_t *roots_dev, cudaStream_t stream) {
+                             int32_t *roots_dev, cudaStream_t stream, const long long *keys = nullptr) {
     qc_ctx *ctx = g->ctx;
     QC_CUDA_TRY(ctx, cudaMemsetAsync(roots_dev, 0, sizeof(int32_t) * (size_t)n_sigma, stream));
     return qc_descend(ctx, g->n, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(),
-                      g->prepared ? g->order.as<int32_t>() : nullptr, V, n_sigma, labels_out, roots_dev, stream);
+                      g->prepared ? g->order.as<int32_t>() : nullptr, V, n_sigma, labels_out, roots_dev, stream,
+                      keys);
 }
 
 static qc_status read_roots(qc_ctx *ctx, const qc_buffer &roots, int32_t *n_clusters_out, cudaStream_t stream) {
@@ -382,20 +415,24 @@ qc_status qc_solve(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V
         V = Vtmp.as<double>();
     }
     QC_TRY(roots.allocate(ctx, sizeof(int32_t) * (size_t)n_sigma, stream));
+    // the potential kernel writes the descent's keys too
+    qc_buffer keys;
+    QC_TRY(keys.allocate(ctx, sizeof(long long) * (size_t)n_sigma * (size_t)g->n, stream));
+    long long *K = keys.as<long long>();
     qc_status st = QC_OK;
     if (!g->hist_valid) st = qc_bfs_enqueue(g, stream);
-    if (st == QC_OK) st = qc_potential_from_hist(g, sigmas, n_sigma, V, stream);
+    if (st == QC_OK) st = qc_potential_from_hist(g, sigmas, n_sigma, V, stream, K);
     if (st == QC_OK) {
         qc_range r2("qc.ggd");
-        st = ggd_enqueue(g, V, n_sigma, labels_out, roots.as<int32_t>(), stream);
+        st = ggd_enqueue(g, V, n_sigma, labels_out, roots.as<int32_t>(), stream, K);
     }
     bool redone = false;
     const qc_status settled = qc_bfs_settle(g, stream, &redone);
     if (st != QC_OK) return st;
     if (settled != QC_OK) return settled;
     if (redone) {
-        QC_TRY(qc_potential_from_hist(g, sigmas, n_sigma, V, stream));
-        QC_TRY(ggd_enqueue(g, V, n_sigma, labels_out, roots.as<int32_t>(), stream));
+        QC_TRY(qc_potential_from_hist(g, sigmas, n_sigma, V, stream, K));
+        QC_TRY(ggd_enqueue(g, V, n_sigma, labels_out, roots.as<int32_t>(), stream, K));
     }
     return read_roots(ctx, roots, n_clusters_out, stream);
 }
@@ -420,8 +457,9 @@ qc_status qc_cluster(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr
     QC_TRY(qc_graph_create(ctx, n, nnz, row_ptr, col_idx, flags, stream_, &g));
     std::unique_ptr<qc_graph, void (*)(qc_graph *)> hold(g, qc_graph_destroy);
     const size_t cells = (size_t)n_sigma * (size_t)n;
-    qc_buffer V, labels, roots;
+    qc_buffer V, labels, roots, keys;
     QC_TRY(V.allocate(ctx, sizeof(double) * cells, stream));
+    QC_TRY(keys.allocate(ctx, sizeof(long long) * cells, stream));
     QC_TRY(labels.allocate(ctx, sizeof(int32_t) * cells, stream));
     QC_TRY(roots.allocate(ctx, sizeof(int32_t) * (size_t)n_sigma, stream));
     qc_pinned pin(ctx);
@@ -429,10 +467,11 @@ qc_status qc_cluster(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr
     if (counts_pinned) QC_TRY(pin.acquire());
     // potentials, descent and both copies out, queued behind the BFS
     auto queue = [&]() -> qc_status {
-        QC_TRY(qc_potential_from_hist(g, sigmas, n_sigma, V.as<double>(), stream));
+        QC_TRY(qc_potential_from_hist(g, sigmas, n_sigma, V.as<double>(), stream, keys.as<long long>()));
         {
             qc_range r2("qc.ggd");
-            QC_TRY(ggd_enqueue(g, V.as<double>(), n_sigma, labels.as<int32_t>(), roots.as<int32_t>(), stream));
+            QC_TRY(ggd_enqueue(g, V.as<double>(), n_sigma, labels.as<int32_t>(), roots.as<int32_t>(), stream,
+                               keys.as<long long>()));
         }
         QC_CUDA_TRY(ctx, cudaMemcpyAsync(labels_out, labels.ptr, labels.bytes, cudaMemcpyDefault, stream));
         if (counts_pinned)

@@ -198,10 +198,13 @@ parent_fn pick_parent(int sn) {
 
 qc_status qc_descend_into(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                           const int32_t *order, const double *V, int32_t n_sigma, int32_t *labels,
-                          int32_t *n_roots_dev, int32_t *parent, long long *keys, cudaStream_t stream) {
-    key_transpose<<<dim3(qc_ceil_div(n, 32), qc_ceil_div(n_sigma, 32)), dim3(32, 8), 0, stream>>>(
-        n, n_sigma, V, keys);
-    QC_LAUNCHED(ctx);
+                          int32_t *n_roots_dev, int32_t *parent, long long *keys, cudaStream_t stream,
+                          bool keys_ready) {
+    if (!keys_ready) {
+        key_transpose<<<dim3(qc_ceil_div(n, 32), qc_ceil_div(n_sigma, 32)), dim3(32, 8), 0, stream>>>(
+            n, n_sigma, V, keys);
+        QC_LAUNCHED(ctx);
+    }
     const int wblocks = qc_ceil_div(n, 8) < 16 * ctx->num_sms ? qc_ceil_div(n, 8) : 16 * ctx->num_sms;
     for (int32_t s0 = 0; s0 < n_sigma; s0 += 16) {
         const int32_t sn = (n_sigma - s0) < 16 ? (n_sigma - s0) : 16;
@@ -216,10 +219,11 @@ qc_status qc_descend_into(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const 
 
 qc_status qc_descend(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                      const int32_t *order, const double *V, int32_t n_sigma, int32_t *labels,
-                     int32_t *n_roots_dev, cudaStream_t stream) {
-    qc_buffer parent, keys;
+                     int32_t *n_roots_dev, cudaStream_t stream, const long long *keys) {
+    qc_buffer parent, own_keys;
     QC_TRY(parent.allocate(ctx, sizeof(int32_t) * (size_t)n * (size_t)n_sigma, stream));
-    QC_TRY(keys.allocate(ctx, sizeof(long long) * (size_t)n * (size_t)n_sigma, stream));
+    if (!keys) QC_TRY(own_keys.allocate(ctx, sizeof(long long) * (size_t)n * (size_t)n_sigma, stream));
     return qc_descend_into(ctx, n, row_ptr, col_idx, order, V, n_sigma, labels, n_roots_dev,
-                           parent.as<int32_t>(), keys.as<long long>(), stream);
+                           parent.as<int32_t>(), keys ? const_cast<long long *>(keys) : own_keys.as<long long>(),
+                           stream, keys != nullptr);
 }

@@ -24,31 +24,67 @@ void qc_weight_table(double sigma, int32_t len, double *w, double *u) {
 
 namespace {
 
-// One thread per (sigma, node); hist is level-major so a warp reads 32
-// consecutive counts per level.  tables: w[s][d], u[s][d] for d = 0..D, den[s] = 2 sigma^2.
 // The largest distance: D, or (when the BFS that fills hist is still queued ahead
 // on the stream) the one the BFS recorded, D_dev[0] - 1, at most D.
 __device__ __forceinline__ int32_t distance_bound(int32_t D, const int32_t *D_dev) {
     return D_dev ? max(0, min(D, *D_dev - 1)) : D;
 }
 
-__global__ void potential_kernel(int32_t n, int32_t Dmax, const int32_t *D_dev, const int32_t *__restrict__ hist,
-                                 const double *__restrict__ w, const double *__restrict__ u,
-                                 const double *__restrict__ den, double *__restrict__ V) {
+// c as a double, built on the integer pipe (exact: c < 2^31 has at most 31
+// significant bits), so that GB300's narrow binary64 pipe only multiplies and adds.
+__device__ __forceinline__ double count_to_double(int c) {
+    if (c <= 0) return (double)c;                    // not in a valid histogram
+    const unsigned uc = (unsigned)c;
+    const int lz = __clz(uc);                        // c > 0: top bit at 31 - lz
+    const unsigned long long e = 1023ull + 31ull - (unsigned long long)lz;
+    const unsigned long long m = ((unsigned long long)uc << (21 + lz)) & ((1ull << 52) - 1ull);
+    return __longlong_as_double((long long)((e << 52) | m));
+}
+
+// The descent's order-preserving key of a potential (IEEE order, -0 equal to +0).
+__device__ __forceinline__ long long potential_key(double x) {
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+
+// V of one (sigma, node).  hist is level-major, so a warp reads 32 consecutive
+// counts per level.  Distance 0 (the node itself, h = 1 in every histogram) needs
+// no binary64 work: 1 * x = x and 0 + x = x exactly, so the sums start at
+// (u[0], w[0]); any other count there takes the general step.
+__device__ __forceinline__ double potential_of(int32_t n, int v, int32_t D, const int32_t *__restrict__ hist,
+                                              const double *us, const double *ws, double den) {
+    double sum1 = 0.0, sum2 = 0.0;
+    int d = 0;
+    if (hist[v] == 1) {
+        sum1 = us[0];
+        sum2 = ws[0];
+        d = 1;
+    }
+    for (; d <= D; ++d) {
+        const int c = hist[(size_t)d * n + v];
+        if (c == 0) continue;          // adds +0.0 to non-negative sums: no change
+        const double h = count_to_double(c);
+        sum1 = __dadd_rn(sum1, __dmul_rn(h, us[d]));
+        sum2 = __dadd_rn(sum2, __dmul_rn(h, ws[d]));
+    }
+    return __ddiv_rn(__ddiv_rn(sum1, sum2), den);
+}
+
+// One thread per (sigma, node).  tables: w[s][d], u[s][d] for d = 0..D, den[s] = 2 sigma^2.
+// K (optional): the keys of the descent, node-major K[v * S + s].
+__global__ void potential_kernel(int32_t n, int32_t Dmax, const int32_t *D_dev, int32_t S,
+                                 const int32_t *__restrict__ hist, const double *__restrict__ w,
+                                 const double *__restrict__ u, const double *__restrict__ den,
+                                 double *__restrict__ V, long long *__restrict__ K) {
     const int s = blockIdx.y;
     const double *ws = w + (size_t)s * (Dmax + 1);
     const double *us = u + (size_t)s * (Dmax + 1);
     const int32_t D = distance_bound(Dmax, D_dev);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        double sum1 = 0.0, sum2 = 0.0;
-        for (int d = 0; d <= D; ++d) {
-            const int c = hist[(size_t)d * n + v];
-            if (c == 0) continue;          // adds +0.0 to non-negative sums: no change
-            const double h = (double)c;
-            sum1 = __dadd_rn(sum1, __dmul_rn(h, us[d]));
-            sum2 = __dadd_rn(sum2, __dmul_rn(h, ws[d]));
-        }
-        V[(size_t)s * n + v] = __ddiv_rn(__ddiv_rn(sum1, sum2), den[s]);
+        const double x = potential_of(n, v, D, hist, us, ws, den[s]);
+        V[(size_t)s * n + v] = x;
+        if (K) K[(size_t)v * S + s] = potential_key(x);
     }
 }
 
@@ -61,7 +97,8 @@ struct InlineTables {
 
 __global__ void potential_kernel_inline(int32_t n, int32_t Dmax, const int32_t *D_dev, int32_t S,
                                         const int32_t *__restrict__ hist,
-                                        const __grid_constant__ InlineTables tab, double *__restrict__ V) {
+                                        const __grid_constant__ InlineTables tab, double *__restrict__ V,
+                                        long long *__restrict__ K) {
     const int s = blockIdx.y;
     const int L = Dmax + 1;
     const double *ws = tab.t + s * L;
@@ -69,15 +106,9 @@ __global__ void potential_kernel_inline(int32_t n, int32_t Dmax, const int32_t *
     const double den = tab.t[2 * S * L + s];
     const int32_t D = distance_bound(Dmax, D_dev);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        double sum1 = 0.0, sum2 = 0.0;
-        for (int d = 0; d <= D; ++d) {
-            const int c = hist[(size_t)d * n + v];
-            if (c == 0) continue;
-            const double h = (double)c;
-            sum1 = __dadd_rn(sum1, __dmul_rn(h, us[d]));
-            sum2 = __dadd_rn(sum2, __dmul_rn(h, ws[d]));
-        }
-        V[(size_t)s * n + v] = __ddiv_rn(__ddiv_rn(sum1, sum2), den);
+        const double x = potential_of(n, v, D, hist, us, ws, den);
+        V[(size_t)s * n + v] = x;
+        if (K) K[(size_t)v * S + s] = potential_key(x);
     }
 }
 
@@ -156,23 +187,23 @@ bool qc_potential_tables_inline(int32_t n_sigma, int32_t L) {
 
 qc_status qc_potential_launch(qc_ctx *ctx, int32_t n, const int32_t *hist, int32_t Dmax, const int32_t *D_dev,
                               int32_t n_sigma, const std::vector<double> &tab, const double *dtab, double *V,
-                              cudaStream_t stream) {
+                              long long *keys, cudaStream_t stream) {
     const int32_t L = Dmax + 1;
     dim3 grid(qc_ceil_div(n, 256) < 2 * ctx->num_sms ? qc_ceil_div(n, 256) : 2 * ctx->num_sms, n_sigma);
     if (qc_potential_tables_inline(n_sigma, L)) {
         InlineTables it;
         std::copy(tab.begin(), tab.end(), it.t);
-        potential_kernel_inline<<<grid, 256, 0, stream>>>(n, Dmax, D_dev, n_sigma, hist, it, V);
+        potential_kernel_inline<<<grid, 256, 0, stream>>>(n, Dmax, D_dev, n_sigma, hist, it, V, keys);
     } else {
-        potential_kernel<<<grid, 256, 0, stream>>>(n, Dmax, D_dev, hist, dtab, dtab + (size_t)n_sigma * L,
-                                                   dtab + 2 * (size_t)n_sigma * L, V);
+        potential_kernel<<<grid, 256, 0, stream>>>(n, Dmax, D_dev, n_sigma, hist, dtab, dtab + (size_t)n_sigma * L,
+                                                   dtab + 2 * (size_t)n_sigma * L, V, keys);
     }
     QC_LAUNCHED(ctx);
     return QC_OK;
 }
 
 qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V,
-                                 cudaStream_t stream) {
+                                 cudaStream_t stream, long long *keys) {
     qc_range range("qc.potential");
     qc_ctx *ctx = g->ctx;
     // while the BFS is still queued ahead, D is known on the device only: the
@@ -183,12 +214,13 @@ qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_si
     std::vector<double> tab;
     qc_potential_tables(sigmas, n_sigma, L, tab);
     if (qc_potential_tables_inline(n_sigma, L))
-        return qc_potential_launch(ctx, g->n, g->hist.as<int32_t>(), Dmax, D_dev, n_sigma, tab, nullptr, V, stream);
+        return qc_potential_launch(ctx, g->n, g->hist.as<int32_t>(), Dmax, D_dev, n_sigma, tab, nullptr, V, keys,
+                                   stream);
     qc_buffer dtab;
     QC_TRY(dtab.allocate(ctx, sizeof(double) * tab.size(), stream));
     QC_CUDA_TRY(ctx, cudaMemcpyAsync(dtab.ptr, tab.data(), dtab.bytes, cudaMemcpyHostToDevice, stream));
     // the host table must outlive the asynchronous copy
     QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
     return qc_potential_launch(ctx, g->n, g->hist.as<int32_t>(), Dmax, D_dev, n_sigma, tab, dtab.as<double>(), V,
-                               stream);
+                               keys, stream);
 }

@@ -47,8 +47,18 @@ struct qc_ctx {
     std::mutex pinned_mu;
     std::vector<void *> pinned_free;       // 64 KiB pinned host blocks ready for reuse
     std::atomic<float> coop_sm_share{1.0f};  // share of SMs the cooperative kernels fill
+    std::mutex streams_mu;
+    std::vector<std::pair<int, cudaStream_t>> spare_streams;   // (priority, stream) not in use
+    std::vector<cudaStream_t> all_streams;                       // every stream the context made
     ~qc_ctx();
 };
+
+// Streams the library makes (sweep and batch plans, servers) belong to the context
+// and live until it is destroyed: memory allocated stream-ordered on one of them (a
+// graph prepared by a plan, say) can be given back on it whenever its owner goes.
+// A released stream returns to the context's spares (non-blocking, by priority).
+cudaError_t qc_stream_acquire(qc_ctx *ctx, int priority, cudaStream_t *out);
+void qc_stream_release(qc_ctx *ctx, cudaStream_t s, int priority);
 
 // A pinned host block of QC_PINNED_BYTES for small device<->host transfers,
 // taken from the context's pool and given back on destruction.
@@ -237,9 +247,10 @@ qc_status qc_bfs_enqueue(qc_graph *g, cudaStream_t stream);
 // and *redone is set, so that work queued on the old rows must be queued again.
 qc_status qc_bfs_settle(qc_graph *g, cudaStream_t stream, bool *redone);
 
-// potential.cu: V[s][v] from the cached histogram.
+// potential.cu: V[s][v] from the cached histogram; keys (optional): the descent's
+// order-preserving keys of V, node-major int64[n][n_sigma], written alongside.
 qc_status qc_potential_from_hist(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V,
-                                 cudaStream_t stream);
+                                 cudaStream_t stream, long long *keys = nullptr);
 // Host weight tables for one sigma, d = 0..len-1 (identical expression to the
 // definition: w = exp(-d^2 / (2 sigma^2)), u = d^2 w).
 void qc_weight_table(double sigma, int32_t len, double *w, double *u);
@@ -252,20 +263,23 @@ void qc_potential_tables(const double *sigmas, int32_t n_sigma, int32_t L, std::
 bool qc_potential_tables_inline(int32_t n_sigma, int32_t L);
 // Queue the potential kernel over hist[Dmax+1][n] (D_dev: the BFS's outcome words
 // + 1 when D is known on the device only, else null); dtab: device copy of tab
-// when the tables do not travel inline.
+// when the tables do not travel inline; keys as for qc_potential_from_hist.
 qc_status qc_potential_launch(qc_ctx *ctx, int32_t n, const int32_t *hist, int32_t Dmax, const int32_t *D_dev,
                               int32_t n_sigma, const std::vector<double> &tab, const double *dtab, double *V,
-                              cudaStream_t stream);
+                              long long *keys, cudaStream_t stream);
 
 // ggd.cu: parents and roots.
 // order: nodes heaviest first (the graph's preparation) or NULL for 0..n-1.
+// keys (optional): V's keys already written by the potential kernel (V is then not read).
 qc_status qc_descend(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                      const int32_t *order, const double *V, int32_t n_sigma, int32_t *labels,
-                     int32_t *n_roots_dev, cudaStream_t stream);
-// The same with caller-provided scratch: parent int32[n_sigma][n], keys int64[n][n_sigma].
+                     int32_t *n_roots_dev, cudaStream_t stream, const long long *keys = nullptr);
+// The same with caller-provided scratch: parent int32[n_sigma][n], keys int64[n][n_sigma]
+// (filled from V here unless keys_ready).
 qc_status qc_descend_into(qc_ctx *ctx, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                           const int32_t *order, const double *V, int32_t n_sigma, int32_t *labels,
-                          int32_t *n_roots_dev, int32_t *parent, long long *keys, cudaStream_t stream);
+                          int32_t *n_roots_dev, int32_t *parent, long long *keys, cudaStream_t stream,
+                          bool keys_ready = false);
 
 // batch.cu: the graph-per-CTA kernel without a plan (used by the serving loop)
 struct qc_cta_launch;

@@ -114,6 +114,7 @@ struct qc_server {
     std::thread sched;
     std::vector<std::thread> large;
     std::vector<cudaStream_t> large_streams;
+    int prio_high = 0, prio_low = 0;   // priorities of the slot and worker streams (the context's)
     float saved_share = 1.0f;          // the context's SM share before the server set its own
     float large_share = 0.4f;          // SM share of the large-request path
     bool divide_share = false;         // split large_share among the large requests running
@@ -414,12 +415,12 @@ qc_status qc_server_create(qc_ctx *ctx, const qc_server_config *cfg, qc_server *
     // batched launches of small requests first: highest stream priority
     int prio_low = 0, prio_high = 0;
     QC_CUDA_TRY(ctx, cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+    s->prio_low = prio_low;
+    s->prio_high = prio_high;
     s->slots.resize(ns);
-    for (Slot &sl : s->slots)
-        QC_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, prio_high));
+    for (Slot &sl : s->slots) QC_CUDA_TRY(ctx, qc_stream_acquire(ctx, prio_high, &sl.stream));
     s->large_streams.resize(nl);
-    for (cudaStream_t &ls : s->large_streams)
-        QC_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&ls, cudaStreamNonBlocking, prio_low));
+    for (cudaStream_t &ls : s->large_streams) QC_CUDA_TRY(ctx, qc_stream_acquire(ctx, prio_low, &ls));
     qc_server *raw = s.get();
     s->sched = std::thread([raw] { raw->scheduler(); });
     for (int i = 0; i < (int)s->large_streams.size(); ++i)
@@ -560,8 +561,8 @@ void qc_server_destroy(qc_server *s) {
     if (s->sched.joinable()) s->sched.join();
     for (std::thread &t : s->large)
         if (t.joinable()) t.join();
-    // requests' memory is given back on the streams it was allocated on, so those
-    // streams go only after it
+    // requests' memory is given back on the streams it was allocated on; those stay
+    // with the context, which also keeps them for graphs the caller lent
     for (Slot &sl : s->slots)
         if (sl.stream) cudaStreamSynchronize(sl.stream);
     for (cudaStream_t ls : s->large_streams)
@@ -576,14 +577,14 @@ void qc_server_destroy(qc_server *s) {
         if (sl.launch) qc_cta_launch_free(sl.launch);
         if (sl.stream) {
             cudaStreamSynchronize(sl.stream);
-            cudaStreamDestroy(sl.stream);
+            qc_stream_release(s->ctx, sl.stream, s->prio_high);
         }
         if (sl.pinned) cudaFreeHost(sl.pinned);
     }
     for (cudaStream_t ls : s->large_streams)
         if (ls) {
             cudaStreamSynchronize(ls);
-            cudaStreamDestroy(ls);
+            qc_stream_release(s->ctx, ls, s->prio_low);
         }
     s->ctx->coop_sm_share = s->saved_share;
     delete s;

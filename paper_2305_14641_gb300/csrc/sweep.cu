@@ -61,11 +61,11 @@ qc_status queue_sweep(qc_sweep *p, cudaStream_t s) {
     qc_ctx *ctx = p->ctx;
     qc_graph *g = p->g;
     QC_TRY(qc_potential_launch(ctx, g->n, p->hist.as<int32_t>(), p->rows - 1, p->out.as<int32_t>() + 1, p->S, p->tab,
-                               p->dtab.as<double>(), p->V, s));
+                               p->dtab.as<double>(), p->V, p->keys.as<long long>(), s));
     QC_CUDA_TRY(ctx, cudaMemsetAsync(p->roots.ptr, 0, p->roots.bytes, s));
     QC_TRY(qc_descend_into(ctx, g->n, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(), g->order.as<int32_t>(),
                            p->V, p->S, p->labels, p->roots.as<int32_t>(), p->parent.as<int32_t>(),
-                           p->keys.as<long long>(), s));
+                           p->keys.as<long long>(), s, true));
     QC_CUDA_TRY(ctx, cudaMemcpyAsync(p->pinned + 8, p->roots.ptr, p->roots.bytes, cudaMemcpyDeviceToHost, s));
     return QC_OK;
 }
@@ -152,7 +152,7 @@ qc_sweep::~qc_sweep() {
     bs.release();
     if (cap) {
         cudaStreamSynchronize(cap);
-        cudaStreamDestroy(cap);
+        qc_stream_release(ctx, cap, 0);
     }
     if (pinned) cudaFreeHost(pinned);
 }
@@ -180,7 +180,7 @@ qc_status qc_sweep_create(qc_graph *g, const double *sigmas, int32_t n_sigma, do
         delete p;
         return st;
     };
-    if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
+    if (qc_stream_acquire(ctx, 0, &p->cap) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost((void **)&p->pinned, sizeof(int32_t) * (8 + (size_t)n_sigma)) != cudaSuccess) {
         qc_set_error(ctx, "qc_sweep_create: stream, event or pinned memory not available");

@@ -115,3 +115,20 @@ def test_plan_and_graph_agree(qc, ctx):
     assert torch.equal(lab, plan.labels)
     plan.close()
     G.close()
+
+def test_graph_outlives_its_plan(qc, ctx):
+    """A plan prepares the graph on a stream of its own; the graph's preparation is
+    given back on that stream when the graph is closed after the plan, so the
+    stream stays with the context (a plan of the same context reuses it)."""
+    graph = gg.planted_partition(20000, 20, 0.004, 0.0001, gg.rng(68))
+    ref = oracle.solve(graph, [1.4])
+    for _ in range(3):
+        G = qc.Graph.from_graph(ctx, graph)
+        plan = qc.SweepPlan(G, [1.4])
+        plan.run(counts=False)
+        assert np.array_equal(plan.labels.cpu().numpy(), ref.labels)
+        plan.close()
+        _, labels, counts = G.solve([1.4])
+        assert np.array_equal(labels.cpu().numpy(), ref.labels) and counts == ref.n_clusters
+        G.close()
+        torch.cuda.synchronize()
