@@ -4,8 +4,8 @@
 // real, so the potential of Algorithm 1 is summed pair by pair instead of
 // through integer distance bins.
 //
-// Shortest paths: sources are processed K at a time (K a multiple of 32, the
-// distance block near eight times L2).  dist[v][k] (node-major,
+// Shortest paths: sources are processed K at a time (K a multiple of 32; by
+// default all of them while the block stays within 4 GiB).  dist[v][k] (node-major,
 // binary64) holds the best length found from source s0 + k to v.  One
 // persistent cooperative launch relaxes, pass after pass,
 //     dist[v][k] = min(dist[v][k], min_{u in row v} dist[u][k] + w(v, u))
@@ -13,20 +13,17 @@
 // s0 + k along the arcs of row v and onwards; for an undirected graph that is
 // also the path from the source to v).  The potential of node v below sums over
 // its own row dist[v][.], i.e. over the lengths *from* v, as in the hop path.
-// A warp owns a node v.  It first checks whether any neighbour changed any
-// distance in the previous pass or so far in this one (chgv[u] = pass of u's
-// last change) and skips v if none did; otherwise, GU groups of 32 sources at a
-// time, it reads only the neighbours whose group changed since the previous
-// pass (chg[u][g]), NB such neighbours at a time, so a lane keeps up to GU x NB
-// distances in flight and quiet parts of the graph cost one int per neighbour
-// and pass.  Testing ">= previous pass" rather than "== previous pass" matters: a
+// A warp takes a node v and GU groups of 32 sources.  It reads only the
+// neighbours whose group changed since the previous pass (chg[u][g] = pass of
+// the group's last change), NB such neighbours at a time, so a lane keeps up to
+// GU x NB distances in flight and quiet parts of the graph cost one 16-byte load
+// per neighbour and pass.  Testing ">= previous pass" rather than "== previous pass" matters: a
 // neighbour that changes again in this pass must not hide its earlier change.  Updates are
 // in place: a value only ever falls to another path's length, every change is
 // seen by the neighbours in the next pass, and a pass without change ends the
 // launch (the last change of any (u, group) is read by u's neighbours in the
 // pass after it), so the result is the unique fixed point whatever the
 // interleaving:
-// each length is accumulated hop by hop as dist[u] + w, rounded in binary64,
 // exactly as Dijkstra's relaxation in the oracle.
 //
 // Potential: for node v, sum1 = sum_j d^2 e^{-d^2 / 2 sigma^2} and
@@ -48,19 +45,18 @@
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int GU = 4;              // source groups a warp relaxes together
+constexpr int GU = 4;              // source groups a warp relaxes together (a multiple of 4)
 constexpr int NB = 4;              // changed neighbours a warp reads together
+constexpr int GRAB = 4;            // items a warp takes per counter update
 
 struct SsspParams {
     int32_t n;
-    const int32_t *row_ptr;
     const int32_t *col_idx;
     const double *w;
-    const int32_t *order;          // nodes, heaviest degree bucket first
+    const int4 *oinfo;             // {node, row start, row end, 0}, heaviest degree bucket first
     double *dist;                  // [n][K]
-    int32_t *chg;                  // [n][KG] pass of the last change of each group
-    int32_t *chgv;                 // [n] pass of the last change of any group
-    int32_t K, KG, s0, ns;         // sources s0 .. s0 + ns - 1 (ns <= K)
+    int32_t *chg;                  // [n][KGp] pass of the last change of each group (-1: none yet)
+    int32_t K, KG, KGp, s0, ns;    // sources s0 .. s0 + ns - 1 (ns <= K); KGp = KG rounded up to GU
     int32_t max_pass;
     int32_t *status;               // [0] state, [1] passes run
     unsigned *bar;
@@ -76,6 +72,143 @@ struct SsspParams {
 __device__ __forceinline__ double as_double(unsigned long long b) { return __longlong_as_double((long long)b); }
 __device__ __forceinline__ unsigned long long bits_of(double x) { return (unsigned long long)__double_as_longlong(x); }
 
+// Most candidates that pass the integer compare still cannot improve: the
+// neighbour is closer to the source than v, but not by w.  GB300 runs binary64
+// adds at 1/64 of its single-precision rate, and these adds kept its binary64
+// pipe two-thirds busy, so a single-precision bound decides first:
+// f_down(x) <= x and f_up(x) >= x (the binary64 bits truncated to a float by
+// integer operations, clamped to [0, 2^127]), so if the sum of the lower
+// bounds of dist[u] and w, rounded down, is at or above the upper bound of the
+// best length, then dist[u] + w >= best exactly and so is its rounded binary64
+// value (rounding is monotone and best is a binary64 number): no binary64 add
+// is needed.  Only candidates within about 2^-22 of best, or below it, reach
+// the binary64 add, whose rounded result alone decides, so the lengths are
+// unchanged bit for bit.
+__device__ __forceinline__ float f_down(unsigned long long b) {   // b: a non-negative finite binary64
+    if (b >= 0x47e0000000000000ull) return 1.7014118346046923e38f;     // 2^127 <= x
+    if (b < 0x3810000000000000ull) return 0.0f;                         // x < 2^-126
+    return __int_as_float((int)((b >> 29) - (896ull << 23)));           // x truncated to 24 bits
+}
+__device__ __forceinline__ float f_up(unsigned long long b) {     // b: a non-negative binary64 or +inf
+    if (b >= 0x47e0000000000000ull) return __int_as_float(0x7f800000);  // +inf
+    if (b < 0x3810000000000000ull) return 1.1754943508222875e-38f;      // 2^-126 > x
+    return __int_as_float((int)((b >> 29) - (896ull << 23)) + 1);       // one float step above the truncation
+}
+
+// Values that other warps rewrite during a pass are read through L2 only
+// (ld.global.cg): L1 is not coherent across SMs, and a line cached there in
+// one pass could hand back a length another SM has since lowered.  Reading a
+// value that is about to fall is harmless (the change is seen in the next
+// pass); the grid barrier makes every write of a pass visible to the next.
+__device__ __forceinline__ unsigned long long load_len(const double *dist, size_t i) {
+    return (unsigned long long)__ldcg(reinterpret_cast<const long long *>(dist) + i);
+}
+
+// One (node, block of GU source groups) item.  The chain of dependent loads is
+// kept short: the row bounds come with the node in one 16-byte load, the
+// change words of a neighbour's GU groups in one 16-byte load each per 4
+// groups, and the item's own lengths only once some neighbour is fresh, issued
+// together with the first neighbours' lengths.
+__device__ __forceinline__ bool sssp_item(const SsspParams &p, const int pass, const int it, const int lane) {
+    constexpr unsigned long long INFB = 0x7ff0000000000000ull;
+    const int gb = it / p.n;
+    const int4 inf = __ldg(p.oinfo + (it - gb * p.n));
+    const int v = inf.x, beg = inf.y, end = inf.z;
+    const int g0 = gb * GU;
+    unsigned long long mine[GU], best[GU];
+    float fbest[GU];                                   // f_up(best)
+    bool loaded = false;
+    for (int e0 = beg; e0 < end; e0 += 32) {
+        const int e = e0 + lane;
+        int u = 0;
+        float wt = 0.0f;                               // f_down(w)
+        int cq[GU];
+#pragma unroll
+        for (int q = 0; q < GU; ++q) cq[q] = -1;
+        if (e < end) {
+            u = qcdev::checked_id(__ldg(p.col_idx + e), p.n, qcdev::DBG_WEIGHTED);
+            wt = f_down((unsigned long long)__double_as_longlong(__ldg(p.w + e)));
+            const int4 *cw = reinterpret_cast<const int4 *>(p.chg + (size_t)u * p.KGp + g0);
+#pragma unroll
+            for (int q4 = 0; q4 < GU / 4; ++q4) {
+                const int4 c = __ldcg(cw + q4);
+                cq[4 * q4] = c.x;
+                cq[4 * q4 + 1] = c.y;
+                cq[4 * q4 + 2] = c.z;
+                cq[4 * q4 + 3] = c.w;
+            }
+        }
+        unsigned fm[GU];
+        unsigned any_fresh = 0u;
+#pragma unroll
+        for (int q = 0; q < GU; ++q) {
+            fm[q] = __ballot_sync(FULL, cq[q] >= pass - 1);
+            any_fresh |= fm[q];
+        }
+        if (!any_fresh) continue;
+        if (!loaded) {
+#pragma unroll
+            for (int q = 0; q < GU; ++q) {
+                mine[q] = (g0 + q < p.KG) ? load_len(p.dist, (size_t)v * p.K + (g0 + q) * 32 + lane) : INFB;
+                best[q] = mine[q];
+                fbest[q] = f_up(mine[q]);
+            }
+            loaded = true;
+        }
+        // up to NB changed neighbours at a time, so that a lane has up to
+        // GU x NB lengths in flight
+        while (any_fresh) {
+            int ub[NB], bb[NB];
+            float wb[NB];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                bb[i] = -1;
+                if (any_fresh) {
+                    bb[i] = __ffs(any_fresh) - 1;
+                    any_fresh &= any_fresh - 1;
+                }
+                const int src = bb[i] < 0 ? 0 : bb[i];
+                ub[i] = __shfl_sync(FULL, u, src);
+                wb[i] = __shfl_sync(FULL, wt, src);
+            }
+            unsigned long long db[NB][GU];
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+#pragma unroll
+                for (int q = 0; q < GU; ++q)
+                    db[i][q] = (bb[i] >= 0 && ((fm[q] >> bb[i]) & 1u))
+                                   ? load_len(p.dist, (size_t)ub[i] * p.K + (g0 + q) * 32 + lane)
+                                   : INFB;
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+#pragma unroll
+                for (int q = 0; q < GU; ++q) {
+                    if (db[i][q] >= best[q]) continue;   // w > 0: no shorter path through u
+                    if (__fadd_rd(f_down(db[i][q]), wb[i]) >= fbest[q]) continue;   // dist[u] + w >= best
+                    const double wv = __ldg(p.w + e0 + bb[i]);
+                    const unsigned long long c = bits_of(__dadd_rn(as_double(db[i][q]), wv));
+                    if (c < best[q]) {
+                        best[q] = c;
+                        fbest[q] = f_up(c);
+                    }
+                }
+        }
+    }
+    if (!loaded) return false;
+    bool v_fell = false;
+#pragma unroll
+    for (int q = 0; q < GU; ++q) {
+        if (g0 + q >= p.KG) break;
+        const bool fell = best[q] < mine[q];
+        if (fell) __stcg(reinterpret_cast<long long *>(p.dist) + (size_t)v * p.K + (g0 + q) * 32 + lane, (long long)best[q]);
+        if (__any_sync(FULL, fell)) {
+            v_fell = true;
+            if (lane == 0) __stcg(p.chg + (size_t)v * p.KGp + g0 + q, pass);
+        }
+    }
+    return v_fell;
+}
+
 // Three blocks per SM (80 registers, a few spills) beat two blocks without
 // spills (104 registers): 68 against 81-90 ms for the DC-SBM of N = 16384.
 __global__ void __launch_bounds__(256, 3) sssp_persistent(const SsspParams p) {
@@ -87,115 +220,32 @@ __global__ void __launch_bounds__(256, 3) sssp_persistent(const SsspParams p) {
         const int v = (int)(i / p.K), k = (int)(i - (long long)v * p.K);
         p.dist[i] = (k < p.ns && v == p.s0 + k) ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
     }
-    for (long long i = tid; i < (long long)p.n * p.KG; i += nthreads) {
-        const int v = (int)(i / p.KG), g = (int)(i - (long long)v * p.KG);
+    for (long long i = tid; i < (long long)p.n * p.KGp; i += nthreads) {
+        const int v = (int)(i / p.KGp), g = (int)(i - (long long)v * p.KGp);
         const int k = v - p.s0;
         p.chg[i] = (k >= 0 && k < p.ns && (k >> 5) == g) ? 0 : -1;
     }
-    for (int v = tid; v < p.n; v += nthreads) p.chgv[v] = (v >= p.s0 && v < p.s0 + p.ns) ? 0 : -1;
     if (!qcdev::grid_barrier(p.bar, p.status)) return;
-    // an item is (node, block of GU source groups), heaviest nodes first, so that
-    // no pass ends waiting on one warp that took a hub late
-    const int NGB = (p.KG + GU - 1) / GU;
-    const int items = p.n * NGB;
+    // An item is (node, block of GU source groups), taken tile-major: every node
+    // of one group block (heaviest first, so that no pass ends waiting on a warp
+    // that took a hub late) before the next block.  The warps in flight then
+    // gather from one block's column of dist (n x GU x 32 x 8 bytes, 16 MiB for
+    // n = 16384), which stays in L2 however many sources a launch holds.  A warp
+    // takes GRAB consecutive items per counter update and reserves its next
+    // GRAB while it works on these.
+    const int items = p.n * (p.KGp / GU);
     int pass = 1;
     for (; pass <= p.max_pass; ++pass) {
         bool any = false;
-        while (true) {
-            int it = 0;
-            if (lane == 0) it = atomicAdd(p.pass_ctr + pass, 1);
-            it = __shfl_sync(FULL, it, 0);
-            if (it >= items) break;
-            const int oi = it / NGB;
-            const int v = p.order[oi];
-            const int gb = it - oi * NGB;
-            const int beg = p.row_ptr[v], end = p.row_ptr[v + 1];
-            bool stirred = false;
-            for (int e = beg + lane; e < end && !stirred; e += 32)
-                stirred = *(volatile int32_t *)(p.chgv + qcdev::checked_id(p.col_idx[e], p.n, qcdev::DBG_WEIGHTED)) >= pass - 1;
-            if (!__any_sync(FULL, stirred)) continue;
-            bool v_fell = false;
-            // GU source groups at a time, and up to NB changed neighbours at a time,
-            // so that a lane has up to GU x NB distances in flight
-            {
-                const int g0 = gb * GU;
-                const unsigned long long *dist = reinterpret_cast<const unsigned long long *>(p.dist);
-                constexpr unsigned long long INFB = 0x7ff0000000000000ull;
-                unsigned long long mine[GU], best[GU];
-#pragma unroll
-                for (int q = 0; q < GU; ++q) {
-                    mine[q] = (g0 + q < p.KG) ? *(volatile const unsigned long long *)(dist + (size_t)v * p.K +
-                                                                                      (g0 + q) * 32 + lane)
-                                              : INFB;
-                    best[q] = mine[q];
-                }
-                for (int e0 = beg; e0 < end; e0 += 32) {
-                    const int e = e0 + lane;
-                    int u = 0;
-                    unsigned long long wt = 0ull;
-                    if (e < end) {
-                        u = qcdev::checked_id(p.col_idx[e], p.n, qcdev::DBG_WEIGHTED);
-                        wt = (unsigned long long)__double_as_longlong(p.w[e]);
-                    }
-                    unsigned fm[GU];
-                    unsigned any_fresh = 0u;
-#pragma unroll
-                    for (int q = 0; q < GU; ++q) {
-                        const bool fresh = e < end && g0 + q < p.KG &&
-                                           *(volatile const int32_t *)(p.chg + (size_t)u * p.KG + g0 + q) >= pass - 1;
-                        fm[q] = __ballot_sync(FULL, fresh);
-                        any_fresh |= fm[q];
-                    }
-                    while (any_fresh) {
-                        int ub[NB], bb[NB];
-                        unsigned long long wb[NB];
-#pragma unroll
-                        for (int i = 0; i < NB; ++i) {
-                            bb[i] = -1;
-                            if (any_fresh) {
-                                bb[i] = __ffs(any_fresh) - 1;
-                                any_fresh &= any_fresh - 1;
-                            }
-                            const int src = bb[i] < 0 ? 0 : bb[i];
-                            ub[i] = __shfl_sync(FULL, u, src);
-                            wb[i] = __shfl_sync(FULL, wt, src);
-                        }
-                        unsigned long long db[NB][GU];
-#pragma unroll
-                        for (int i = 0; i < NB; ++i)
-#pragma unroll
-                            for (int q = 0; q < GU; ++q)
-                                db[i][q] = (bb[i] >= 0 && ((fm[q] >> bb[i]) & 1u))
-                                               ? *(volatile const unsigned long long *)(dist + (size_t)ub[i] * p.K +
-                                                                                        (g0 + q) * 32 + lane)
-                                               : INFB;
-#pragma unroll
-                        for (int i = 0; i < NB; ++i)
-#pragma unroll
-                            for (int q = 0; q < GU; ++q) {
-                                if (db[i][q] >= best[q]) continue;   // w > 0: no shorter path through u
-                                const unsigned long long c = bits_of(__dadd_rn(as_double(db[i][q]), as_double(wb[i])));
-                                if (c < best[q]) best[q] = c;
-                            }
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < GU; ++q) {
-                    if (g0 + q >= p.KG) break;
-                    const bool fell = best[q] < mine[q];
-                    if (fell)
-                        *(volatile unsigned long long *)(reinterpret_cast<unsigned long long *>(p.dist) +
-                                                         (size_t)v * p.K + (g0 + q) * 32 + lane) = best[q];
-                    if (__any_sync(FULL, fell)) {
-                        v_fell = true;
-                        if (lane == 0) *(volatile int32_t *)(p.chg + (size_t)v * p.KG + g0 + q) = pass;
-                    }
-                }
-            }
-            if (v_fell) {
-                any = true;
-                if (lane == 0) *(volatile int32_t *)(p.chgv + v) = pass;
-            }
+        int base = 0;
+        if (lane == 0) base = atomicAdd(p.pass_ctr + pass, GRAB);
+        base = __shfl_sync(FULL, base, 0);
+        while (base < items) {
+            int next = 0;
+            if (lane == 0) next = atomicAdd(p.pass_ctr + pass, GRAB);
+            for (int j = 0; j < GRAB && base + j < items; ++j)
+                any |= sssp_item(p, pass, base + j, lane);
+            base = __shfl_sync(FULL, next, 0);
         }
         if (__syncthreads_or(any) && threadIdx.x == 0) p.pass_new[pass] = 1;
         if (!qcdev::grid_barrier(p.bar, p.status)) return;
@@ -417,12 +467,10 @@ __global__ void check_weights(int32_t n, const int32_t *row_ptr, const int32_t *
 }
 
 // Sources per shortest-path launch.  Each pass of a launch ends at a grid
-// barrier whose cost does not grow with K, so wide blocks win even after the
-// distance block leaves L2: measured on GB300 (the DC-SBM of N = 16384), the
-// shortest paths took 126 ms with K = 512 (half of L2), 110 ms with 1024 and
-// 103 ms from 4096 up.  K is sized for a distance block near eight times L2 and
-// split evenly over the n sources, a multiple of 32.  QCGRAPH_SSSP_SOURCES
-// overrides it.
+// barrier whose cost does not grow with K, and the tile-major item order keeps
+// the gathers in L2 whatever K is, so a launch takes every source while the
+// distance block stays within 4 GiB (n <= 23170), else an even split of them
+// into blocks below that.  QCGRAPH_SSSP_SOURCES overrides it.
 // The exponential's tables, from the C library's exp in extended precision
 // (long double), each rounded once.
 void fill_exp_tables(ExpTables &T) {
@@ -439,19 +487,20 @@ __global__ void exp_neg_kernel(int64_t n, const double *t, double *out, const __
         out[i] = exp_neg(t[i], T);
 }
 
-int32_t sources_per_batch(const qc_ctx *ctx, int32_t n) {
+int32_t sources_per_batch(int32_t n) {
     const int64_t cover = ((int64_t)n + 31) / 32 * 32;
     int64_t K;
     if (const char *env = getenv("QCGRAPH_SSSP_SOURCES")) {
         K = atoll(env) / 32 * 32;
     } else {
-        const size_t l2 = ctx->l2_bytes ? ctx->l2_bytes : (size_t)96 << 20;
-        const int64_t target = std::max<int64_t>((int64_t)(8 * l2 / (8 * (size_t)std::max(n, 1))), 32);
+        const int64_t target = std::max<int64_t>((int64_t)(((size_t)4 << 30) / (8 * (size_t)std::max(n, 1))), 32);
         const int64_t batches = (cover + target - 1) / target;
         K = ((cover + batches - 1) / batches + 31) / 32 * 32;
     }
     if (K < 32) K = 32;
-    return (int32_t)std::min<int64_t>(K, cover);
+    // the items of a pass, n x ceil(K / 128), stay below 2^30
+    const int64_t k_items = std::max<int64_t>((((int64_t)1 << 30) / std::max(n, 1)) / GU * 32 * GU, 32);
+    return (int32_t)std::min<int64_t>(std::min<int64_t>(K, k_items), cover);
 }
 
 }  // namespace
@@ -513,18 +562,18 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
     cudaStream_t stream = qc_stream(stream_);
     QC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     const int32_t n = g->n;
-    const int32_t K = sources_per_batch(ctx, n);
+    const int32_t K = sources_per_batch(n);
     const int32_t KG = K / 32;
+    const int32_t KGp = (KG + GU - 1) / GU * GU;
     QC_TRY(qc_graph_prepare(g, stream));     // the degree order of the nodes
     const int32_t max_pass = n + 1;     // a lightest path has at most n - 1 arcs
     std::vector<double> den(n_sigma);
     for (int32_t s = 0; s < n_sigma; ++s) den[s] = 2.0 * (sigmas[s] * sigmas[s]);
     ExpTables etab;
     fill_exp_tables(etab);
-    qc_buffer dist, chg, chgv, ctl, acc, dden;
+    qc_buffer dist, chg, ctl, acc, dden;
     QC_TRY(dist.allocate(ctx, sizeof(double) * (size_t)n * K, stream));
-    QC_TRY(chg.allocate(ctx, sizeof(int32_t) * (size_t)n * KG, stream));
-    QC_TRY(chgv.allocate(ctx, sizeof(int32_t) * (size_t)n, stream));
+    QC_TRY(chg.allocate(ctx, sizeof(int32_t) * (size_t)n * KGp, stream));
     QC_TRY(ctl.allocate(ctx, sizeof(int32_t) * (8 + 2 * ((size_t)max_pass + 1)), stream));
     QC_TRY(acc.allocate(ctx, sizeof(double2) * (size_t)n_sigma * n, stream));
     QC_CUDA_TRY(ctx, cudaMemsetAsync(acc.ptr, 0, acc.bytes, stream));
@@ -538,7 +587,7 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
         return QC_ERR_CUDA;
     }
     int blocks = per_sm * qc_coop_sms(ctx);
-    const int want = qc_ceil_div((int64_t)n * ((KG + GU - 1) / GU), 8);
+    const int want = qc_ceil_div((int64_t)n * (KGp / GU), 8);
     if (blocks > want) blocks = want;
     if (blocks < 1) blocks = 1;
     qc_pinned pin(ctx);
@@ -548,15 +597,14 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
     for (int32_t s0 = 0; s0 < n; s0 += K) {
         SsspParams p;
         p.n = n;
-        p.row_ptr = g->row_ptr.as<int32_t>();
         p.col_idx = g->col_idx.as<int32_t>();
         p.w = g->weights.as<double>();
-        p.order = g->order.as<int32_t>();
+        p.oinfo = g->oinfo.as<int4>();
         p.dist = dist.as<double>();
         p.chg = chg.as<int32_t>();
-        p.chgv = chgv.as<int32_t>();
         p.K = K;
         p.KG = KG;
+        p.KGp = KGp;
         p.s0 = s0;
         p.ns = std::min(K, n - s0);
         p.max_pass = max_pass;

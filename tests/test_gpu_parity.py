@@ -447,12 +447,19 @@ def test_histogram_checkpoint(qc, ctx):
     g3.close()
 
 
-def assert_weighted_matches(qc, ctx, graph, w, sigmas):
+_WEIGHTED_REF = {}
+
+
+def assert_weighted_matches(qc, ctx, graph, w, sigmas, cache_key=None):
     G = qc.Graph.from_graph(ctx, graph)
     G.set_weights(w)
     V = G.potential_weighted(sigmas)
     Vh = V.cpu().numpy()
-    ref = oracle.potential_weighted(graph, w, sigmas, threads=oracle.default_threads())
+    ref = _WEIGHTED_REF.get(cache_key) if cache_key is not None else None
+    if ref is None:
+        ref = oracle.potential_weighted(graph, w, sigmas, threads=oracle.default_threads())
+        if cache_key is not None:
+            _WEIGHTED_REF[cache_key] = ref
     rel = np.abs(Vh - ref) / np.maximum(np.abs(ref), np.finfo(np.float64).tiny)
     assert np.all(rel <= 1e-12), (graph.name, float(rel.max()))
     labels, counts = G.ggd_labels(V)
@@ -483,6 +490,19 @@ def test_weighted_batches_and_unit_weights(qc, ctx, monkeypatch):
     Vw = assert_weighted_matches(qc, ctx, graph, np.ones(graph.nnz), [0.9, 1.8])
     hop = oracle.solve(graph, [0.9, 1.8]).V
     assert np.allclose(Vw, hop, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("sources", [None, "2048", "16384"])
+def test_weighted_dcsbm16384_full(qc, ctx, sources, monkeypatch):
+    """The weighted workload at full size: the DC-SBM of N = 16384 with weights
+    U(0.5, 2), in the default source blocks, in 8 blocks and in one block of all
+    sources; V within 1e-12 of the oracle's Dijkstra-based sums at the two ends of
+    the sigma sweep, labels exact on the same V."""
+    if sources is not None:
+        monkeypatch.setenv("QCGRAPH_SSSP_SOURCES", sources)
+    graph, sweep = gg.dcsbm16384()
+    w = gg.edge_weights(graph, 0.5, 2.0, gg.rng(7, 1))
+    assert_weighted_matches(qc, ctx, graph, w, [sweep[0], sweep[-1]], cache_key="dcsbm-16384 U(0.5, 2)")
 
 
 def test_exp_neg_accuracy(qc, ctx):
