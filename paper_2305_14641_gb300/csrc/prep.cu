@@ -191,14 +191,21 @@ __global__ void __launch_bounds__(256) prep_fused(const PrepParams p) {
             p.info[i] = make_int4(v, p.row_ptr[v], p.row_ptr[v + 1], 0);
         }
     if (!qcdev::grid_barrier(bar, p.ctl)) return;
-    // E
+    // E: a warp tests 32 consecutive nodes with one load and walks, lanes
+    // across the row, the rows of those outside that component (a warp per
+    // node, one label load after another, made this the longest phase)
     const int giant = *(volatile int32_t *)(p.ctl + 4);
     const int lane = threadIdx.x & 31;
-    for (int v = tid >> 5; v < n; v += nthreads >> 5) {
-        if (*(volatile int32_t *)(p.L + v) == giant) continue;
-        const int end = p.row_ptr[v + 1];
-        for (int e = p.row_ptr[v] + 2 + lane; e < end; e += 32)
-            uf_link(p.L, v, qcdev::checked_id(p.col_idx[e], n, qcdev::DBG_PREP));
+    for (int v0 = tid - lane; v0 < n; v0 += nthreads) {
+        const int vl = v0 + lane;
+        unsigned rest = __ballot_sync(0xffffffffu, vl < n && *(volatile int32_t *)(p.L + vl) != giant);
+        while (rest) {
+            const int v = v0 + __ffs(rest) - 1;
+            rest &= rest - 1;
+            const int end = p.row_ptr[v + 1];
+            for (int e = p.row_ptr[v] + 2 + lane; e < end; e += 32)
+                uf_link(p.L, v, qcdev::checked_id(p.col_idx[e], n, qcdev::DBG_PREP));
+        }
     }
     if (!qcdev::grid_barrier(bar, p.ctl)) return;
     // F
