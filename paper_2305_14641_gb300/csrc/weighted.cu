@@ -290,6 +290,7 @@ struct ExpTables {
     double hi[746];                // exp(-a), a = 0 .. 745
     double lo[64];                 // exp(-b / 64), b = 0 .. 63 (binary64 form)
     unsigned long long fx[1024];   // exp(-b / 1024) in Q1.63, b = 0 .. 1023
+    unsigned long long fa[64];     // exp(-a) in Q1.63, a = 0 .. 63 (fixed-point sums)
 };
 
 // binary64 form: t = a + b/64 + r, exp(-r) by its Taylor series to degree 6
@@ -317,8 +318,10 @@ __device__ __forceinline__ void load_exp_tables(ExpTables &dst, const ExpTables 
     __syncthreads();
 }
 
-// exp(-t) from Tf = floor(t 2^53), t < 708.
-__device__ __forceinline__ double exp_neg_fixed(unsigned long long Tf, const ExpTables &T) {
+// exp(-t) from Tf = floor(t 2^53), t < 708; *fix (if given) receives
+// exp(-t) 2^62 rounded down to an integer (within 2 units), 0 from t = 64 on.
+__device__ __forceinline__ double exp_neg_fixed(unsigned long long Tf, const ExpTables &T,
+                                                unsigned long long *fix = nullptr) {
     constexpr unsigned long long ONE = 1ull << 63;        // 1.0 in Q1.63
     constexpr unsigned long long THIRD = 0x5555555555555555ull;   // floor(2^64 / 3)
     const int a = (int)(Tf >> 53);
@@ -330,6 +333,7 @@ __device__ __forceinline__ double exp_neg_fixed(unsigned long long Tf, const Exp
     w = ONE - __umul64hi(rq, w);                                     // exp(-r)
     const unsigned long long L = T.fx[b];
     const unsigned long long M = (__umul64hi(L, w) << 1) | ((L * w) >> 63);   // Q1.63, in (0.36, 1]
+    if (fix) *fix = a < 64 ? __umul64hi(T.fa[a], M) : 0ull;                  // Q1.63 x Q1.63 -> Q2.62
     // exp(-a) M: the mantissa product (hi:lo, below 2^127) rounded once to 53 bits
     constexpr unsigned long long MANT = (1ull << 52) - 1;
     const unsigned long long hb = (unsigned long long)__double_as_longlong(T.hi[a]);   // normal for a <= 707
@@ -376,6 +380,35 @@ __device__ __forceinline__ double exp_neg_product(unsigned long long d2b, unsign
     const unsigned long long Tf = r >= 64 ? (hi >> (r - 64)) : ((hi << (64 - r)) | (lo >> r));
     if (Tf >= (708ull << 53)) return exp_neg(__dmul_rn(__longlong_as_double((long long)d2b), inv), T);
     return exp_neg_fixed(Tf, T);
+}
+
+// exp_neg_product, and fix = exp(-d2 x inv) 2^62 rounded down as exp_neg_fixed
+// gives it: 2^62 where the result is 1, 0 from t = 256 on (the binary64
+// route), and for a subnormal d2 (rare) the binary64 result scaled and truncated.
+__device__ __forceinline__ double exp_neg_product_fix(unsigned long long d2b, unsigned long long mi, int ri,
+                                                      double inv, const ExpTables &T, unsigned long long &fix) {
+    constexpr unsigned long long ONE62 = 1ull << 62;
+    fix = ONE62;
+    if (d2b == 0) return 1.0;
+    const int ed = (int)(d2b >> 52);
+    const int r = ri - ed;
+    if (ed == 0) {
+        const double e = exp_neg(__dmul_rn(__longlong_as_double((long long)d2b), inv), T);
+        fix = (unsigned long long)(e * 4611686018427387904.0);   // e 2^62 (exact), truncated
+        return e;
+    }
+    fix = 0ull;
+    if (r < 44) return exp_neg(__dmul_rn(__longlong_as_double((long long)d2b), inv), T);
+    fix = ONE62;
+    if (r >= 128) return 1.0;
+    const unsigned long long md = (d2b & ((1ull << 52) - 1)) | (1ull << 52);
+    const unsigned long long hi = __umul64hi(md, mi), lo = md * mi;
+    const unsigned long long Tf = r >= 64 ? (hi >> (r - 64)) : ((hi << (64 - r)) | (lo >> r));
+    if (Tf >= (708ull << 53)) {
+        fix = 0ull;
+        return exp_neg(__dmul_rn(__longlong_as_double((long long)d2b), inv), T);
+    }
+    return exp_neg_fixed(Tf, T, &fix);
 }
 
 // acc[s][v] += (sum1, sum2) over the batch's sources for node v: a warp per node,
@@ -439,6 +472,180 @@ __global__ void __launch_bounds__(256, 3) wpot_accumulate(int32_t n, int32_t K, 
     }
 }
 
+// (hi:lo) += b, 128-bit unsigned
+__device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi, unsigned long long b) {
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(b));
+}
+// (hi 2^64 + lo) 2^-q as binary64: the product is exact, the sum rounds once
+__device__ __forceinline__ double fixed_to_double(unsigned long long lo, unsigned long long hi, double scale) {
+    return __dmul_rn(__fma_rn(__ull2double_rn(hi), 18446744073709551616.0, __ull2double_rn(lo)), scale);
+}
+
+// Symmetric pair sums, for undirected graphs whose sources a launch holds all
+// at once: the length from v to j and the one from j to v are the same
+// shortest-path length (accumulated from opposite ends, so they may differ in
+// the last bits), and each unordered pair's exponential is evaluated once for
+// both nodes' sums.  Work: strips of 32 rows (4 per warp) against segments of
+// SYM_SEG columns at or right of the strip's first node, lanes across the
+// columns.  A pair (v, j) with v in the strip adds to v's row sums; when j lies
+// right of the strip it also adds to j's column sums.  Node v's sums are then
+// its strip's row sums (columns from the strip's first node on) plus the
+// column sums of the strips left of it, which covers every j once.
+//   rows: butterfly over the lanes of d^2 e (binary64) and of e 2^57 (integer),
+//         added into per-row shared accumulators, written per (item, row);
+//   columns: per lane over the warp's 4 rows, a fused multiply-add for sum1 and
+//         e 2^61 in integers for sum2, then the 8 warps in order through shared
+//         memory, written per (strip, column).
+// sum2 in integers is exact but for the truncation of each term (2^-57 or
+// 2^-61); with sum2 >= 1 (the self term) that is within n 2^-57 relative.  The
+// partial sums are reduced in a fixed order (wpot_sym_reduce), so the result is
+// the same on every run.  GB300's binary64 pipe does about one operation per
+// ordered pair and sigma instead of two, and the exponential half as often.
+constexpr int SYM_ROWS = 32;
+constexpr int SYM_SEG = 1024;
+constexpr int SYM_SG = 4;          // sigmas per launch
+
+__global__ void __launch_bounds__(256, 2) wpot_sym(int32_t n, int32_t K, const double *dist, int32_t S,
+                                                   const double *den, int32_t nsegm, int32_t items,
+                                                   int32_t *item_ctr, double2 *prow, double2 *pcol,
+                                                   const __grid_constant__ ExpTables Tp) {
+    constexpr int RW = SYM_ROWS / 8;   // rows per warp
+    __shared__ ExpTables T;
+    __shared__ double cs1w[8][32][SYM_SG];
+    __shared__ unsigned long long cs2w[8][32][SYM_SG];
+    __shared__ int s_item;
+    __shared__ double s_inv[SYM_SG];                 // 1 / (2 sigma^2), for the rare binary64 route
+    if (threadIdx.x < SYM_SG) s_inv[threadIdx.x] = ((int)threadIdx.x < S) ? 1.0 / den[threadIdx.x] : 1.0;
+    load_exp_tables(T, Tp);                          // (its barrier publishes s_inv too)
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    unsigned long long im[SYM_SG];
+    int ir[SYM_SG];
+#pragma unroll
+    for (int s = 0; s < SYM_SG; ++s) {
+        const unsigned long long ib = (unsigned long long)__double_as_longlong(s_inv[s]);
+        im[s] = (ib & ((1ull << 52) - 1)) | (1ull << 52);
+        ir[s] = 2097 - (int)(ib >> 52);
+    }
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(item_ctr, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= items) break;
+        const int strip = it / nsegm, c = it - strip * nsegm;
+        const int i0 = strip * SYM_ROWS;
+        const int jb = i0 + c * SYM_SEG;
+        if (jb >= n) continue;
+        const int je = min(n, jb + SYM_SEG);
+        // this lane's part of the warp's rows over the item's columns: sum1 by
+        // fused multiply-adds, sum2 as e 2^57 in integers (at most 32 chunks of
+        // one term each: below 2^62)
+        double rs1[RW][SYM_SG];
+        unsigned long long rs2[RW][SYM_SG];
+#pragma unroll
+        for (int rr = 0; rr < RW; ++rr)
+#pragma unroll
+            for (int s = 0; s < SYM_SG; ++s) {
+                rs1[rr][s] = 0.0;
+                rs2[rr][s] = 0ull;
+            }
+        for (int j0 = jb; j0 < je; j0 += 32) {
+            const bool diag = j0 == i0;                  // the strip's own columns: rows only
+            const int j = j0 + lane;
+            const bool jok = j < je;
+            double cs1[SYM_SG];
+            unsigned long long cs2[SYM_SG];
+#pragma unroll
+            for (int s = 0; s < SYM_SG; ++s) {
+                cs1[s] = 0.0;
+                cs2[s] = 0ull;
+            }
+#pragma unroll
+            for (int rr = 0; rr < RW; ++rr) {
+                const int v = i0 + warp * RW + rr;
+                const double d = (v < n && jok) ? dist[(size_t)v * K + j] : __longlong_as_double(0x7ff0000000000000ll);
+                if (!(d < 1e308)) continue;              // unreachable, or outside the item
+                const double d2 = __dmul_rn(d, d);
+                const unsigned long long d2b = (unsigned long long)__double_as_longlong(d2);
+#pragma unroll
+                for (int s = 0; s < SYM_SG; ++s) {
+                    if (s >= S) continue;
+                    unsigned long long fx;
+                    const double e = exp_neg_product_fix(d2b, im[s], ir[s], s_inv[s], T, fx);
+                    rs1[rr][s] = fma(d2, e, rs1[rr][s]);
+                    rs2[rr][s] += fx >> 5;
+                    if (!diag) {
+                        cs1[s] = fma(d2, e, cs1[s]);
+                        cs2[s] += fx >> 1;                   // the warp's rows: at most 2^63
+                    }
+                }
+            }
+            if (!diag) {
+#pragma unroll
+                for (int s = 0; s < SYM_SG; ++s) {
+                    cs1w[warp][lane][s] = cs1[s];
+                    cs2w[warp][lane][s] = cs2[s];
+                }
+                __syncthreads();
+                for (int i = threadIdx.x; i < 32 * SYM_SG; i += blockDim.x) {
+                    const int l = i / SYM_SG, s = i - l * SYM_SG;
+                    double a = 0.0;
+                    unsigned long long lo = 0ull, hi = 0ull;
+                    for (int w = 0; w < 8; ++w) {
+                        a = __dadd_rn(a, cs1w[w][l][s]);
+                        add128(lo, hi, cs2w[w][l][s]);
+                    }
+                    if (j0 + l < je)
+                        pcol[((size_t)strip * n + j0 + l) * SYM_SG + s] = make_double2(a, fixed_to_double(lo, hi, 0x1p-61));
+                }
+                __syncthreads();
+            }
+        }
+        // the rows' totals over the lanes (every lane ends with the same sums)
+#pragma unroll
+        for (int rr = 0; rr < RW; ++rr)
+#pragma unroll
+            for (int s = 0; s < SYM_SG; ++s) {
+                double x = rs1[rr][s];
+                unsigned long long lo = rs2[rr][s], hi = 0ull;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    x = __dadd_rn(x, __shfl_xor_sync(FULL, x, off));
+                    const unsigned long long olo = __shfl_xor_sync(FULL, lo, off), ohi = __shfl_xor_sync(FULL, hi, off);
+                    add128(lo, hi, olo);
+                    hi += ohi;
+                }
+                if (lane == 0)
+                    prow[((size_t)it * SYM_ROWS + warp * RW + rr) * SYM_SG + s] =
+                        make_double2(x, fixed_to_double(lo, hi, 0x1p-57));
+            }
+    }
+}
+
+// acc[s][v] = node v's row sums over its strip's segments, then the column
+// sums of every strip left of it, in that order.
+__global__ void wpot_sym_reduce(int32_t n, int32_t S, int32_t nsegm, const double2 *prow, const double2 *pcol,
+                                double2 *acc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * SYM_SG; i += gridDim.x * blockDim.x) {
+        const int v = i / SYM_SG, s = i - v * SYM_SG;
+        if (s >= S) continue;
+        const int strip = v / SYM_ROWS, r = v - strip * SYM_ROWS;
+        double a1 = 0.0, a2 = 0.0;
+        for (int c = 0; c < nsegm && strip * SYM_ROWS + c * SYM_SEG < n; ++c) {
+            const double2 x = prow[((size_t)(strip * nsegm + c) * SYM_ROWS + r) * SYM_SG + s];
+            a1 = __dadd_rn(a1, x.x);
+            a2 = __dadd_rn(a2, x.y);
+        }
+        for (int I = 0; I < strip; ++I) {
+            const double2 x = pcol[((size_t)I * n + v) * SYM_SG + s];
+            a1 = __dadd_rn(a1, x.x);
+            a2 = __dadd_rn(a2, x.y);
+        }
+        acc[(size_t)s * n + v] = make_double2(a1, a2);
+    }
+}
+
 __global__ void wpot_final(int32_t n, int32_t S, const double *den, const double2 *acc, double *V) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S * n; i += gridDim.x * blockDim.x) {
         const int s = i / n;
@@ -489,6 +696,8 @@ void fill_exp_tables(ExpTables &T) {
     for (int b = 0; b < 64; ++b) T.lo[b] = (double)std::exp(-(long double)b / 64.0L);
     for (int b = 0; b < 1024; ++b)   // <= 2^63, rounded to the nearest integer
         T.fx[b] = (unsigned long long)(std::ldexp(std::exp(-(long double)b / 1024.0L), 63) + 0.5L);
+    for (int a = 0; a < 64; ++a)     // <= 2^63, rounded to the nearest integer
+        T.fa[a] = (unsigned long long)(std::ldexp(std::exp(-(long double)a), 63) + 0.5L);
 }
 
 __global__ void exp_neg_kernel(int64_t n, const double *t, double *out, const __grid_constant__ ExpTables Tp) {
@@ -512,6 +721,36 @@ int32_t sources_per_batch(int32_t n) {
     // the items of a pass, n x ceil(K / 128), stay below 2^30
     const int64_t k_items = std::max<int64_t>((((int64_t)1 << 30) / std::max(n, 1)) / GU * 32 * GU, 32);
     return (int32_t)std::min<int64_t>(std::min<int64_t>(K, k_items), cover);
+}
+
+// The symmetric pair sums (wpot_sym) of a distance block that holds every
+// source, SYM_SG sigmas per launch, into acc[s][v].
+qc_status wpot_symmetric(qc_ctx *ctx, int32_t n, int32_t K, const double *dist, int32_t n_sigma, const double *dden,
+                         double2 *acc, const ExpTables &etab, cudaStream_t stream) {
+    const int32_t strips = qc_ceil_div(n, SYM_ROWS);
+    const int32_t nsegm = qc_ceil_div(n, SYM_SEG);
+    const int32_t items = strips * nsegm;
+    const int32_t groups = qc_ceil_div(n_sigma, SYM_SG);
+    qc_buffer prow, pcol, ctr;
+    QC_TRY(prow.allocate(ctx, sizeof(double2) * (size_t)items * SYM_ROWS * SYM_SG, stream));
+    QC_TRY(pcol.allocate(ctx, sizeof(double2) * (size_t)strips * n * SYM_SG, stream));
+    QC_TRY(ctr.allocate(ctx, sizeof(int32_t) * (size_t)groups, stream));
+    QC_CUDA_TRY(ctx, cudaMemsetAsync(ctr.ptr, 0, ctr.bytes, stream));
+    int per_sm = 0;
+    QC_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)wpot_sym, 256, 0));
+    const int blocks = std::max(1, std::min(std::max(per_sm, 1) * ctx->num_sms, items));
+    const int rb = std::max(1, std::min(qc_ceil_div((int64_t)n * SYM_SG, 256), 4 * ctx->num_sms));
+    for (int32_t gi = 0; gi < groups; ++gi) {
+        const int32_t s0 = gi * SYM_SG;
+        const int32_t S = std::min(SYM_SG, n_sigma - s0);
+        wpot_sym<<<blocks, 256, 0, stream>>>(n, K, dist, S, dden + s0, nsegm, items, ctr.as<int32_t>() + gi,
+                                             prow.as<double2>(), pcol.as<double2>(), etab);
+        QC_LAUNCHED(ctx);
+        wpot_sym_reduce<<<rb, 256, 0, stream>>>(n, S, nsegm, prow.as<double2>(), pcol.as<double2>(),
+                                                acc + (size_t)s0 * n);
+        QC_LAUNCHED(ctx);
+    }
+    return QC_OK;
 }
 
 }  // namespace
@@ -606,6 +845,10 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
     QC_TRY(pin.acquire());
     int32_t *h = static_cast<int32_t *>(pin.ptr);
     const int pblocks = std::max(1, std::min(qc_ceil_div(n, 8), 8 * ctx->num_sms));
+    // an undirected graph whose sources all fit one block takes the symmetric
+    // pair sums (QCGRAPH_WPOT_SYM=0 keeps the per-node form)
+    const char *sym_env = getenv("QCGRAPH_WPOT_SYM");
+    const bool sym = !g->directed && K >= n && !(sym_env && sym_env[0] == '0');
     for (int32_t s0 = 0; s0 < n; s0 += K) {
         SsspParams p;
         p.n = n;
@@ -640,9 +883,14 @@ extern "C" qc_status qc_potential_weighted(qc_graph *g, const double *sigmas, in
             qc_set_error(ctx, "shortest paths did not settle within %d passes", max_pass);
             return QC_ERR_CUDA;
         }
-        wpot_accumulate<<<pblocks, 256, 0, stream>>>(n, K, p.ns, dist.as<double>(), n_sigma, dden.as<double>(),
-                                                     acc.as<double2>(), etab);
-        QC_LAUNCHED(ctx);
+        if (sym) {
+            QC_TRY(wpot_symmetric(ctx, n, K, dist.as<double>(), n_sigma, dden.as<double>(), acc.as<double2>(), etab,
+                                  stream));
+        } else {
+            wpot_accumulate<<<pblocks, 256, 0, stream>>>(n, K, p.ns, dist.as<double>(), n_sigma,
+                                                         dden.as<double>(), acc.as<double2>(), etab);
+            QC_LAUNCHED(ctx);
+        }
     }
     const int fb = std::max(1, std::min(qc_ceil_div((int64_t)n_sigma * n, 256), 2 * ctx->num_sms));
     wpot_final<<<fb, 256, 0, stream>>>(n, n_sigma, dden.as<double>(), acc.as<double2>(), V_out);
