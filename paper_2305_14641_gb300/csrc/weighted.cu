@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(256, 3) wpot_accumulate(int32_t n, int32_t K, 
             }
             for (int k = lane; k < ns; k += 32) {
                 const double d = row[k];
-                if (!(d < 1e308)) continue;                        // unreachable (+inf)
+                if (__double_as_longlong(d) >= 0x7ff0000000000000ll) continue;   // unreachable (+inf)
                 const double d2 = __dmul_rn(d, d);
                 const unsigned long long d2b = (unsigned long long)__double_as_longlong(d2);
 #pragma unroll
@@ -565,7 +565,9 @@ __global__ void __launch_bounds__(256, 2) wpot_sym(int32_t n, int32_t K, const d
             for (int rr = 0; rr < RW; ++rr) {
                 const int v = i0 + warp * RW + rr;
                 const double d = (v < n && jok) ? dist[(size_t)v * K + j] : __longlong_as_double(0x7ff0000000000000ll);
-                if (!(d < 1e308)) continue;              // unreachable, or outside the item
+                // unreachable (+inf), or outside the item; an integer compare keeps
+                // it off the binary64 pipe
+                if (__double_as_longlong(d) >= 0x7ff0000000000000ll) continue;
                 const double d2 = __dmul_rn(d, d);
                 const unsigned long long d2b = (unsigned long long)__double_as_longlong(d2);
 #pragma unroll
@@ -590,9 +592,9 @@ __global__ void __launch_bounds__(256, 2) wpot_sym(int32_t n, int32_t K, const d
                 __syncthreads();
                 for (int i = threadIdx.x; i < 32 * SYM_SG; i += blockDim.x) {
                     const int l = i / SYM_SG, s = i - l * SYM_SG;
-                    double a = 0.0;
-                    unsigned long long lo = 0ull, hi = 0ull;
-                    for (int w = 0; w < 8; ++w) {
+                    double a = cs1w[0][l][s];
+                    unsigned long long lo = cs2w[0][l][s], hi = 0ull;
+                    for (int w = 1; w < 8; ++w) {
                         a = __dadd_rn(a, cs1w[w][l][s]);
                         add128(lo, hi, cs2w[w][l][s]);
                     }
