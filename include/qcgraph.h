@@ -245,8 +245,11 @@ qc_status qc_solve(qc_graph *g, const double *sigmas, int32_t n_sigma, double *V
  * to labels_out: int32[n_sigma][n], host or device memory (any address the CUDA
  * copy engines can write).  n_clusters_out: host int32[n_sigma] or NULL.  The
  * work after the upload is queued back to back and the call waits once at the
- * end (and, with QC_VALIDATE, once for the validation's verdict), so on return
- * labels_out holds the result and the library holds nothing of the graph.
+ * end, so on return labels_out holds the result and the library holds nothing
+ * of the graph.  QC_VALIDATE's check is queued too, ahead of the rest: if it
+ * fails, the work behind it runs on the graph with every row emptied (so it
+ * stays inside the arrays), the call returns QC_ERR_INVALID_GRAPH, and
+ * labels_out and n_clusters_out then hold nothing meaningful.
  * Errors: those of qc_graph_create and qc_solve. */
 qc_status qc_cluster(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
                      uint32_t flags, const double *sigmas, int32_t n_sigma, int32_t *labels_out,

@@ -12,6 +12,7 @@ and streams; every step of the method runs in the library's CUDA kernels.
 from __future__ import annotations
 
 import ctypes
+import weakref
 from typing import Sequence
 
 import numpy as np
@@ -72,6 +73,14 @@ class Context:
         native.check(self._lib.qc_context_create(self.device, int(mem_budget_bytes), alloc_ptr,
                                                  ctypes.byref(h)))
         self.handle = h
+        # graphs and plans made on this context (weakly held): the C library requires
+        # the context to outlive them, so close() closes any still open first
+        self._children = []
+
+    def _adopt(self, obj, rank: int) -> None:
+        if len(self._children) >= 64:
+            self._children = [c for c in self._children if c[1]() is not None]
+        self._children.append((rank, weakref.ref(obj)))
 
     def set_timing(self, enable: bool) -> None:
         self.check(self._lib.qc_context_set_timing(self.handle, int(bool(enable))))
@@ -134,6 +143,12 @@ class Context:
 
     def close(self) -> None:
         if getattr(self, "handle", None):
+            # plans before graphs (a plan holds its graphs), both before the context
+            for _, ref in sorted(getattr(self, "_children", []), key=lambda c: c[0]):
+                obj = ref()
+                if obj is not None:
+                    obj.close()
+            self._children = []
             self._lib.qc_context_destroy(self.handle)
             self.handle = None
 
@@ -177,6 +192,7 @@ class Graph:
                                            _stream_handle(stream), ctypes.byref(h)))
         del keep
         self.handle = h
+        ctx._adopt(self, 1)
         self.n = n
         self.nnz = nnz
 
@@ -327,6 +343,7 @@ class SweepPlan:
         ctx.check(ctx._lib.qc_sweep_create(graph.handle, sig, S, V.data_ptr() if V is not None else None,
                                            self.labels.data_ptr(), _stream_handle(stream), ctypes.byref(h)))
         self.handle = h
+        ctx._adopt(self, 0)
 
     def run(self, reuse_histogram: bool = False, counts: bool = False, stream=None):
         """One run; returns the clusters per sigma (host ints) when counts, else None."""
@@ -377,6 +394,7 @@ class BatchPlan:
         ctx.check(ctx._lib.qc_batch_create(ctx.handle, len(graphs), arr, sig, self.labels.data_ptr(), off,
                                            _stream_handle(stream), ctypes.byref(h)))
         self.handle = h
+        ctx._adopt(self, 0)
 
     def run(self, stream=None, counts: bool = True):
         """Run the plan; returns the clusters per graph (host ints) or None."""

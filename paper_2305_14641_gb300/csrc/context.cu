@@ -454,8 +454,18 @@ qc_status qc_cluster(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr
         }
     cudaStream_t stream = qc_stream(stream_);
     qc_graph *g = nullptr;
-    QC_TRY(qc_graph_create(ctx, n, nnz, row_ptr, col_idx, flags, stream_, &g));
+    // the upload, then the validation queued without a wait: the work behind it
+    // runs on an emptied CSR if the check fails, and the verdict is read with the
+    // results
+    QC_TRY(qc_graph_create(ctx, n, nnz, row_ptr, col_idx, flags & ~(uint32_t)QC_VALIDATE, stream_, &g));
     std::unique_ptr<qc_graph, void (*)(qc_graph *)> hold(g, qc_graph_destroy);
+    const bool validate = (flags & QC_VALIDATE) != 0;
+    qc_buffer verdict;
+    if (validate) {
+        QC_TRY(verdict.allocate(ctx, sizeof(int32_t), stream));
+        QC_TRY(qc_validate_csr_queue(ctx, n, nnz, g->row_ptr.as<int32_t>(), g->col_idx.as<int32_t>(), !g->directed,
+                                     verdict.as<int32_t>(), stream));
+    }
     const size_t cells = (size_t)n_sigma * (size_t)n;
     qc_buffer V, labels, roots, keys;
     QC_TRY(V.allocate(ctx, sizeof(double) * cells, stream));
@@ -463,8 +473,11 @@ qc_status qc_cluster(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr
     QC_TRY(labels.allocate(ctx, sizeof(int32_t) * cells, stream));
     QC_TRY(roots.allocate(ctx, sizeof(int32_t) * (size_t)n_sigma, stream));
     qc_pinned pin(ctx);
-    const bool counts_pinned = n_clusters_out && sizeof(int32_t) * (size_t)n_sigma <= QC_PINNED_BYTES;
-    if (counts_pinned) QC_TRY(pin.acquire());
+    QC_TRY(pin.acquire());
+    // the pinned block: the verdict in its first word, the cluster counts after it
+    int32_t *h_verdict = static_cast<int32_t *>(pin.ptr);
+    int32_t *h_counts = h_verdict + 4;
+    const bool counts_pinned = n_clusters_out && sizeof(int32_t) * ((size_t)n_sigma + 4) <= QC_PINNED_BYTES;
     // potentials, descent and both copies out, queued behind the BFS
     auto queue = [&]() -> qc_status {
         QC_TRY(qc_potential_from_hist(g, sigmas, n_sigma, V.as<double>(), stream, keys.as<long long>()));
@@ -475,21 +488,30 @@ qc_status qc_cluster(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr
         }
         QC_CUDA_TRY(ctx, cudaMemcpyAsync(labels_out, labels.ptr, labels.bytes, cudaMemcpyDefault, stream));
         if (counts_pinned)
-            QC_CUDA_TRY(ctx, cudaMemcpyAsync(pin.ptr, roots.ptr, roots.bytes, cudaMemcpyDeviceToHost, stream));
+            QC_CUDA_TRY(ctx, cudaMemcpyAsync(h_counts, roots.ptr, roots.bytes, cudaMemcpyDeviceToHost, stream));
         return QC_OK;
     };
+    h_verdict[0] = 0;
     qc_status st = qc_bfs_enqueue(g, stream);
     if (st == QC_OK) st = queue();
+    if (st == QC_OK && validate)
+        st = cudaMemcpyAsync(h_verdict, verdict.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream) == cudaSuccess
+                 ? QC_OK
+                 : QC_ERR_CUDA;
     bool redone = false;
-    const qc_status settled = qc_bfs_settle(g, stream, &redone);
+    const qc_status settled = qc_bfs_settle(g, stream, &redone);   // waits for all of the above
     if (st != QC_OK) return st;
+    if (validate) {
+        QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));   // returns at once where the settle has waited
+        QC_TRY(qc_csr_verdict(ctx, h_verdict[0]));
+    }
     if (settled != QC_OK) return settled;
     if (redone) QC_TRY(queue());
     if (n_clusters_out && !counts_pinned)
         QC_CUDA_TRY(ctx, cudaMemcpyAsync(n_clusters_out, roots.ptr, roots.bytes, cudaMemcpyDeviceToHost, stream));
     QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
     QC_TRY(qc_debug_take(ctx));
-    if (counts_pinned) memcpy(n_clusters_out, pin.ptr, roots.bytes);
+    if (counts_pinned) memcpy(n_clusters_out, h_counts, roots.bytes);
     return QC_OK;
 }
 

@@ -296,6 +296,13 @@ void qc_cta_launch_free(qc_cta_launch *L);
 // One launch checks the whole CSR (row_ptr included) and waits for the verdict.
 qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
                           const int32_t *col_idx_dev, bool symmetric, cudaStream_t stream);
+// The same check queued without waiting: err (device int32) receives its flags,
+// and if it found anything every row of row_ptr_dev is then made empty, so that
+// the work queued behind it stays inside the arrays; the caller reads err once
+// its work has finished and reports qc_csr_verdict of it.
+qc_status qc_validate_csr_queue(qc_ctx *ctx, int32_t n, int64_t nnz, int32_t *row_ptr_dev,
+                                const int32_t *col_idx_dev, bool symmetric, int32_t *err, cudaStream_t stream);
+qc_status qc_csr_verdict(qc_ctx *ctx, int32_t flags);
 qc_status qc_validate_hist(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr_dev,
                            const int32_t *hist_dev, int32_t D, cudaStream_t stream);
 

@@ -55,6 +55,15 @@ __global__ void check_csr(int32_t n, int64_t nnz, const int32_t *row_ptr, const 
     if (lane == 0 && bad) atomicOr(err, bad);
 }
 
+// After a queued check (qc_validate_csr_queue): if it found anything, every row
+// is made empty, so the kernels queued behind it read no column id and no row
+// bound outside the arrays; the caller discards their results and reports the
+// verdict.
+__global__ void empty_rows_if_bad(int32_t n, int32_t *row_ptr, const int32_t *err) {
+    if (*(volatile const int32_t *)err == 0) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) row_ptr[i] = 0;
+}
+
 enum : int32_t {
     BAD_H0 = 1,         // h(0, v) != 1
     BAD_H1 = 2,         // h(1, v) != out-degree
@@ -112,6 +121,29 @@ qc_status qc_validate_hist(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *r
     return QC_OK;
 }
 
+qc_status qc_csr_verdict(qc_ctx *ctx, int32_t flags) {
+    if (!flags) return QC_OK;
+    qc_set_error(ctx, "invalid CSR (flags 0x%x):%s%s%s%s%s", flags,
+                 (flags & BAD_ROW_PTR) ? " row_ptr not 0-based, non-decreasing and ending at nnz;" : "",
+                 (flags & BAD_COLUMN) ? " column id out of range;" : "",
+                 (flags & BAD_ORDER) ? " row not strictly ascending;" : "",
+                 (flags & BAD_SELF_LOOP) ? " self-loop;" : "",
+                 (flags & BAD_ASYMMETRIC) ? " not symmetric;" : "");
+    return QC_ERR_INVALID_GRAPH;
+}
+
+qc_status qc_validate_csr_queue(qc_ctx *ctx, int32_t n, int64_t nnz, int32_t *row_ptr, const int32_t *col_idx,
+                                bool symmetric, int32_t *err, cudaStream_t stream) {
+    QC_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, sizeof(int32_t), stream));
+    const int wblocks = qc_ceil_div(n, 8) < 8 * ctx->num_sms ? qc_ceil_div(n, 8) : 8 * ctx->num_sms;
+    check_csr<<<wblocks, 256, 0, stream>>>(n, nnz, row_ptr, col_idx, symmetric, err);
+    QC_LAUNCHED(ctx);
+    const int eb = qc_ceil_div(n + 1, 256) < 2 * ctx->num_sms ? qc_ceil_div(n + 1, 256) : 2 * ctx->num_sms;
+    empty_rows_if_bad<<<eb, 256, 0, stream>>>(n, row_ptr, err);
+    QC_LAUNCHED(ctx);
+    return QC_OK;
+}
+
 qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
                           const int32_t *col_idx, bool symmetric, cudaStream_t stream) {
     qc_buffer err;
@@ -125,14 +157,5 @@ qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *ro
     QC_LAUNCHED(ctx);
     QC_CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
     QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
-    if (h_err) {
-        qc_set_error(ctx, "invalid CSR (flags 0x%x):%s%s%s%s%s", h_err,
-                     (h_err & BAD_ROW_PTR) ? " row_ptr not 0-based, non-decreasing and ending at nnz;" : "",
-                     (h_err & BAD_COLUMN) ? " column id out of range;" : "",
-                     (h_err & BAD_ORDER) ? " row not strictly ascending;" : "",
-                     (h_err & BAD_SELF_LOOP) ? " self-loop;" : "",
-                     (h_err & BAD_ASYMMETRIC) ? " not symmetric;" : "");
-        return QC_ERR_INVALID_GRAPH;
-    }
-    return QC_OK;
+    return qc_csr_verdict(ctx, h_err);
 }

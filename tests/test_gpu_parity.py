@@ -237,6 +237,11 @@ def test_invalid_inputs(qc, ctx):
         with pytest.raises(qc.QCError) as e:
             qc.Graph(ctx, r, c)
         assert e.value.status_name == "QC_ERR_INVALID_GRAPH", name
+        # the one-call form queues its check ahead of the solve, which then runs on
+        # emptied rows; the verdict comes with the results
+        with pytest.raises(qc.QCError) as e:
+            qc.cluster(ctx, r, c, [1.0, 2.0])
+        assert e.value.status_name == "QC_ERR_INVALID_GRAPH", name
     # row_ptr itself: decreasing, not starting at 0, ending past or before nnz,
     # negative and huge entries; the device check reads every row bound before it
     # indexes through it, so none of these reads outside the arrays
@@ -255,6 +260,11 @@ def test_invalid_inputs(qc, ctx):
         with pytest.raises(qc.QCError) as e:
             qc.Graph(ctx, *dev_bad)
         assert e.value.status_name == "QC_ERR_INVALID_GRAPH", bad_rp
+        for args in ((bad_rp, ci), dev_bad):
+            with pytest.raises(qc.QCError) as e:
+                qc.cluster(ctx, *args, [1.0])
+            assert e.value.status_name == "QC_ERR_INVALID_GRAPH", bad_rp
+            assert "row_ptr" in str(e.value), str(e.value)
     # the context is still usable
     assert_solution_matches(qc, ctx, graph, [1.0])
 

@@ -132,3 +132,26 @@ def test_graph_outlives_its_plan(qc, ctx):
         assert np.array_equal(labels.cpu().numpy(), ref.labels) and counts == ref.n_clusters
         G.close()
         torch.cuda.synchronize()
+
+
+def test_context_closes_what_is_left_open(qc):
+    """The library requires a context to outlive its graphs and plans; the binding
+    closes any left open when the context closes (plans first), so dropping them
+    afterwards is harmless."""
+    graph = gg.planted_partition(700, 5, 0.04, 0.003, gg.rng(69))
+    ref = oracle.solve(graph, [1.2])
+    c = qc.Context(0, allocator="cuda")
+    G = qc.Graph.from_graph(c, graph)
+    plan = qc.SweepPlan(G, [1.2])
+    plan.run(counts=False)
+    assert np.array_equal(plan.labels.cpu().numpy(), ref.labels)
+    bp = qc.BatchPlan(c, [G], [1.2])
+    bp.run(counts=False)
+    assert np.array_equal(bp.labels.cpu().numpy(), ref.labels[0])
+    c.close()
+    assert G.handle is None and plan.handle is None and bp.handle is None
+    del plan, bp, G
+    torch.cuda.synchronize()
+    with qc.Context(0, allocator="cuda") as c2:       # the device is still usable
+        lab, _ = qc.cluster(c2, graph.row_ptr, graph.col_idx, [1.2])
+        assert np.array_equal(lab, ref.labels)
