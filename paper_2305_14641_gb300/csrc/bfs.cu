@@ -800,8 +800,13 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
 // MASKS: the variant that keeps change masks (G = 32 only), for graphs whose
 // early frontiers are sparse; the plain variant reads every segment of every
 // neighbour.
+// Blocks per SM: four (64 registers) for the short-row variants and the
+// change-mask one, three (80 registers) for the plain tiled one.  Measured on
+// GB300: four blocks took the plain variant on dcsbm-16384 from 0.359 to 0.412
+// ms per launch (its spills), and the mask variant on sbm-262144 from 79.1 to
+// 77.6 ms per solve.
 template <int G, bool MASKS>
-__global__ void __launch_bounds__(256, G == 32 ? 3 : 4) bfs_persistent(const BfsParams p) {
+__global__ void __launch_bounds__(256, (G == 32 && !MASKS) ? 3 : 4) bfs_persistent(const BfsParams p) {
     __shared__ ulonglong2 red[WARPS][32];
     if (threadIdx.x == 0) {
         block_found = 0u;
