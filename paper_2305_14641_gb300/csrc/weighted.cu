@@ -503,9 +503,9 @@ __device__ __forceinline__ double fixed_to_double(unsigned long long lo, unsigne
 // ordered pair and sigma instead of two, and the exponential half as often.
 constexpr int SYM_ROWS = 32;
 constexpr int SYM_SEG = 1024;
-constexpr int SYM_SG = 4;          // sigmas per launch
+constexpr int SYM_SG = 2;          // sigmas per launch
 
-__global__ void __launch_bounds__(256, 2) wpot_sym(int32_t n, int32_t K, const double *dist, int32_t S,
+__global__ void __launch_bounds__(256, 3) wpot_sym(int32_t n, int32_t K, const double *dist, int32_t S,
                                                    const double *den, int32_t nsegm, int32_t items,
                                                    int32_t *item_ctr, double2 *prow, double2 *pcol,
                                                    const __grid_constant__ ExpTables Tp) {
