@@ -164,9 +164,21 @@ __global__ void __launch_bounds__(256) prep_fused(const PrepParams p) {
     if (!qcdev::grid_barrier(bar, p.ctl)) return;
     // C
     uf_compress(p.L, n, tid, nthreads);
-    if (p.order)
-        for (int v = tid; v < n; v += nthreads)
-            p.order[atomicAdd(&p.bins[32 + degree_bucket(p.row_ptr[v + 1] - p.row_ptr[v])], 1)] = v;
+    if (p.order) {
+        // one counter update per bucket and warp (most nodes share a few buckets,
+        // and a counter update per node serialised on them)
+        const int lane_c = threadIdx.x & 31;
+        for (int v0 = tid - lane_c; v0 < n; v0 += nthreads) {
+            const int v = v0 + lane_c;
+            const int b = v < n ? degree_bucket(p.row_ptr[v + 1] - p.row_ptr[v]) : 32;
+            const unsigned same = __match_any_sync(0xffffffffu, b);
+            const int leader = __ffs(same) - 1;
+            int at = 0;
+            if (b < 32 && lane_c == leader) at = atomicAdd(&p.bins[32 + b], __popc(same));
+            at = __shfl_sync(0xffffffffu, at, leader);
+            if (b < 32) p.order[at + __popc(same & ((1u << lane_c) - 1u))] = v;
+        }
+    }
     if (!qcdev::grid_barrier(bar, p.ctl)) return;
     // D
     if (blockIdx.x == 0) {
