@@ -13,46 +13,73 @@ enum : int32_t {
     BAD_ASYMMETRIC = 16,
 };
 
-// One warp per row.  Every row bound is checked before it is used, so the scan
-// stays inside row_ptr[0..n] and col_idx[0..nnz) whatever the arrays hold:
-// row v's warp checks 0 <= row_ptr[v] <= row_ptr[v+1] <= nnz (which, over all v,
-// makes row_ptr non-decreasing within [0, nnz]); thread 0 checks the two ends.
-__global__ void check_csr(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx, bool symmetric,
-                          int32_t *err) {
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+// Two kernels, neither of which reads outside row_ptr[0..n] and col_idx[0..nnz)
+// whatever the arrays hold.
+// check_rows, one thread per row: 0 <= row_ptr[v] <= row_ptr[v+1] <= nnz (which,
+// over all v, makes row_ptr non-decreasing within [0, nnz]); thread 0 checks the
+// two ends.
+__global__ void check_rows(int32_t n, int64_t nnz, const int32_t *row_ptr, int32_t *err) {
     int bad = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz)) bad |= BAD_ROW_PTR;
-    for (int v = warp; v < n; v += nwarps) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[n] != nnz)) bad |= BAD_ROW_PTR;
+    for (int v = tid; v < n; v += gridDim.x * blockDim.x) {
         const int beg = row_ptr[v], end = row_ptr[v + 1];
-        if (beg < 0 || beg > end || (int64_t)end > nnz) {
-            bad |= BAD_ROW_PTR;
-            continue;
-        }
-        for (int e = beg + lane; e < end; e += 32) {
-            const int u = col_idx[e];
-            if (u < 0 || u >= n) { bad |= BAD_COLUMN; continue; }
-            if (u == v) bad |= BAD_SELF_LOOP;
-            if (e > beg && col_idx[e - 1] >= u) bad |= BAD_ORDER;
-            if (!symmetric) continue;
-            // symmetric: v must appear in row u (binary search; rows may be unsorted
-            // only if BAD_ORDER is also reported)
-            const int64_t ulo = row_ptr[u], uend = row_ptr[u + 1];
-            if (ulo < 0 || uend < ulo || uend > nnz) { bad |= BAD_ROW_PTR; continue; }
-            int lo = (int)ulo, hi = (int)uend - 1;
-            bool found = false;
-            while (lo <= hi) {
-                const int mid = lo + ((hi - lo) >> 1);
-                const int x = col_idx[mid];
-                if (x == v) { found = true; break; }
-                if (x < v) lo = mid + 1; else hi = mid - 1;
-            }
-            if (!found) bad |= BAD_ASYMMETRIC;
-        }
+        if (beg < 0 || beg > end || (int64_t)end > nnz) bad |= BAD_ROW_PTR;
     }
     bad = __reduce_or_sync(0xffffffffu, bad);
-    if (lane == 0 && bad) atomicOr(err, bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicOr(err, bad);
+}
+
+// check_edges, one thread per edge (so a hub's row costs no more than others):
+// the edge's row v is found by binary search in row_ptr (within [0, n) whatever
+// row_ptr holds; where row_ptr is invalid the row may be wrong, and then
+// check_rows has already flagged it), then its column is in range, not v, above
+// the previous column of the row, and (symmetric) v appears in the column's row,
+// by binary search between that row's bounds once they are checked.
+__global__ void check_edges(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx, bool symmetric,
+                            int32_t *err) {
+    int bad = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n - 1;                      // the last v with row_ptr[v] <= e
+        while (lo < hi) {
+            const int mid = lo + ((hi - lo + 1) >> 1);
+            if ((int64_t)row_ptr[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const int v = lo;
+        const int u = col_idx[e];
+        if (u < 0 || u >= n) { bad |= BAD_COLUMN; continue; }
+        if (u == v) bad |= BAD_SELF_LOOP;
+        if (e > 0 && e > (int64_t)row_ptr[v] && col_idx[e - 1] >= u) bad |= BAD_ORDER;
+        if (!symmetric) continue;
+        const int64_t ulo = row_ptr[u], uend = row_ptr[u + 1];
+        if (ulo < 0 || uend < ulo || uend > nnz) { bad |= BAD_ROW_PTR; continue; }
+        int a = (int)ulo, b = (int)uend - 1;
+        bool found = false;
+        while (a <= b) {
+            const int mid = a + ((b - a) >> 1);
+            const int x = col_idx[mid];
+            if (x == v) { found = true; break; }
+            if (x < v) a = mid + 1; else b = mid - 1;
+        }
+        if (!found) bad |= BAD_ASYMMETRIC;
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicOr(err, bad);
+}
+
+// Both checks into err (zeroed by the caller).
+qc_status launch_csr_checks(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                            bool symmetric, int32_t *err, cudaStream_t stream) {
+    const int rb = qc_ceil_div(n, 256) < 2 * ctx->num_sms ? qc_ceil_div(n, 256) : 2 * ctx->num_sms;
+    check_rows<<<rb, 256, 0, stream>>>(n, nnz, row_ptr, err);
+    QC_LAUNCHED(ctx);
+    if (nnz > 0) {
+        const int64_t eb64 = (nnz + 255) / 256;
+        const int eb = eb64 < 8 * (int64_t)ctx->num_sms ? (int)eb64 : 8 * ctx->num_sms;
+        check_edges<<<eb, 256, 0, stream>>>(n, nnz, row_ptr, col_idx, symmetric, err);
+        QC_LAUNCHED(ctx);
+    }
+    return QC_OK;
 }
 
 // After a queued check (qc_validate_csr_queue): if it found anything, every row
@@ -135,9 +162,7 @@ qc_status qc_csr_verdict(qc_ctx *ctx, int32_t flags) {
 qc_status qc_validate_csr_queue(qc_ctx *ctx, int32_t n, int64_t nnz, int32_t *row_ptr, const int32_t *col_idx,
                                 bool symmetric, int32_t *err, cudaStream_t stream) {
     QC_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, sizeof(int32_t), stream));
-    const int wblocks = qc_ceil_div(n, 8) < 8 * ctx->num_sms ? qc_ceil_div(n, 8) : 8 * ctx->num_sms;
-    check_csr<<<wblocks, 256, 0, stream>>>(n, nnz, row_ptr, col_idx, symmetric, err);
-    QC_LAUNCHED(ctx);
+    QC_TRY(launch_csr_checks(ctx, n, nnz, row_ptr, col_idx, symmetric, err, stream));
     const int eb = qc_ceil_div(n + 1, 256) < 2 * ctx->num_sms ? qc_ceil_div(n + 1, 256) : 2 * ctx->num_sms;
     empty_rows_if_bad<<<eb, 256, 0, stream>>>(n, row_ptr, err);
     QC_LAUNCHED(ctx);
@@ -152,9 +177,7 @@ qc_status qc_validate_csr(qc_ctx *ctx, int32_t n, int64_t nnz, const int32_t *ro
     qc_pinned pin(ctx);
     QC_TRY(pin.acquire());
     int32_t &h_err = *static_cast<int32_t *>(pin.ptr);
-    const int wblocks = qc_ceil_div(n, 8) < 8 * ctx->num_sms ? qc_ceil_div(n, 8) : 8 * ctx->num_sms;
-    check_csr<<<wblocks, 256, 0, stream>>>(n, nnz, row_ptr, col_idx, symmetric, err.as<int32_t>());
-    QC_LAUNCHED(ctx);
+    QC_TRY(launch_csr_checks(ctx, n, nnz, row_ptr, col_idx, symmetric, err.as<int32_t>(), stream));
     QC_CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
     QC_CUDA_TRY(ctx, cudaStreamSynchronize(stream));
     return qc_csr_verdict(ctx, h_err);
