@@ -28,8 +28,8 @@
 // Work: items are (node, tile of 32 segments) taken in the graph's order
 // (heaviest degree bucket first; sat is indexed in that order).  Items of rows
 // with degree >= 127 are heavy: all warps of a block share one, splitting its
-// neighbour list.  Other items go one warp each, GRAB list positions per counter
-// update: the first pull level lists every light item, and each level appends
+// neighbour list.  Other items go one warp each, 4 list positions per counter
+// update (8 with change masks): the first pull level lists every light item, and each level appends
 // the items it pulled (still open, or saturated just now and owed one copy of
 // ones) to the next level's worklist, so late levels touch only what is left.
 // A warp reads its positions' sat words with one load per lane and runs the
@@ -67,7 +67,12 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint64_t ONES = ~0ull;
 constexpr int NOT_SAT = 0x7fffffff;
 constexpr int WARPS = 8;               // warps per block
-constexpr int GRAB = 4;                // light list positions taken per counter update
+// light list positions taken per counter update: four in the plain variant,
+// eight in the change-mask one (measured on GB300: eight took dcsbm-16384's launch
+// from 0.359 to 0.473 ms, its scanning levels' tails grew, and sbm-262144's solve
+// from 76.8 to 74.2 ms, a quarter as many updates of a counter a million items share)
+template <bool MASKS>
+__host__ __device__ constexpr int grab_of() { return MASKS ? 8 : 4; }
 constexpr int LIST_AFTER = 2;          // pull levels of a launch that scan every item
 constexpr int TH_WORDS = 256;          // longest chunk row the two-hop set-up builds in shared memory
 constexpr int TH_U = 8;                // neighbour-of-neighbour ids each lane has in flight
@@ -671,7 +676,7 @@ __device__ void heavy_items(const BfsParams &p, const int level, const bool mask
     }
 }
 
-// Light items: a warp takes GRAB list positions, one sat word per lane, and
+// Light items: a warp takes grab_of<MASKS>() list positions, one sat word per lane, and
 // runs the items a ballot marks (copy-ones items first, then pull items); the
 // pull items go to the next level's worklist.  The first pull level of a
 // launch lists every light item in order; later levels read the worklist.
@@ -690,6 +695,7 @@ __device__ __forceinline__ void light_items(const BfsParams &p, const int level,
     const int count = from_list ? *(volatile int32_t *)(p.wl_count + level) : p.n * p.T - first;
     int32_t *ctr = p.light_ctr + level;
     int base = 0;
+    constexpr int GRAB = grab_of<MASKS>();
     if (lane == 0) base = atomicAdd(ctr, GRAB);
     base = __shfl_sync(FULL, base, 0);
     while (base < count) {
