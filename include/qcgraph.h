@@ -223,9 +223,10 @@ qc_status qc_ggd_labels(qc_graph *g, const double *V, int32_t n_sigma, int32_t *
  * (2 sigma^2) with d = dist(i, j) the lightest-path length from i (along arcs
  * for a directed graph), j over the nodes i reaches, i itself included.  All-
  * source shortest paths run on the device in blocks of sources; the sums use
- * binary64 with the device's exp, so V agrees with a sequential host
- * evaluation to rounding (relative 1e-13 or better) and is the same on every
- * run.  V_out: device double[n_sigma * n].  Descent: qc_ggd_labels on V_out.
+ * binary64 with the device's exp (for an undirected graph each pair's terms
+ * once for both nodes, and the e^{...} sum exactly in integers but for one
+ * truncation per term), so V agrees with a sequential host evaluation to
+ * within 1e-12 relative and is the same on every run.  V_out: device double[n_sigma * n].  Descent: qc_ggd_labels on V_out.
  * Errors: QC_ERR_INVALID_ARG (no weights, bad sigma), QC_ERR_BUDGET,
  * QC_ERR_OOM, QC_ERR_CUDA (including weights that let lengths fall without
  * end), QC_ERR_TIMEOUT. */
